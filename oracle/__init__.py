@@ -1,0 +1,176 @@
+"""CPU oracle for the algebraic-signature equi-join -- TEST INFRASTRUCTURE ONLY.
+
+Only tests/, the smoke check in __graft_entry__ and bench.py's CPU-baseline /
+reference arm may import this package.  The product path (the CUDA library and
+its binding) never does, and this package never imports the product.
+
+It wraps oracle.c, a plain C statement of:
+  * GF(2^16) arithmetic with log/antilog tables and a shift-and-add product
+    (Section 3.1 of the paper);
+  * the 4-component algebraic signature sig^k(P) = sum_i p_i x^(k i), once by
+    the table definition and once by Horner's rule (Section 3.1);
+  * the exact equi-join T = {(r.id, s.id) : key(r) == key(s)} by a nested loop,
+    a simple hash join on full strings and a Grace (partitioned) hash join
+    (Section 2; Figure 2 without the signature shortcut, since the result must
+    be exact).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SO = os.path.join(_HERE, "_build", "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+POLY = 0x1100B          # x^16 + x^12 + x^3 + x + 1
+ORDER = 65535
+
+
+def _build_lib() -> None:
+    os.makedirs(os.path.dirname(_SO), exist_ok=True)
+    tmp = _SO + f".tmp{os.getpid()}"
+    subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-pthread", "-o", tmp,
+                           os.path.join(_HERE, "oracle.c")])
+    os.replace(tmp, _SO)
+
+
+def build() -> str:
+    with _lock:
+        _build_lib()
+    return _SO
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        src = os.path.join(_HERE, "oracle.c")
+        if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+            _build_lib()
+        lib = ctypes.CDLL(_SO)
+        P, U64, U16 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint16
+        lib.or_gf_init.restype = ctypes.c_int
+        lib.or_gf_tables.argtypes = [P, P]
+        lib.or_gf_mul_tab.argtypes = [U16, U16]
+        lib.or_gf_mul_tab.restype = U16
+        lib.or_gf_mul_shift.argtypes = [U16, U16]
+        lib.or_gf_mul_shift.restype = U16
+        lib.or_gf_pow_x.argtypes = [U64]
+        lib.or_gf_pow_x.restype = U16
+        lib.or_sig_tables.argtypes = [P, U64]
+        lib.or_sig_tables.restype = U64
+        lib.or_sig_horner.argtypes = [P, U64]
+        lib.or_sig_horner.restype = U64
+        lib.or_sig_batch.argtypes = [P, P, U64, P, ctypes.c_int, ctypes.c_int]
+        for f in (lib.or_join_nested, lib.or_join_simple):
+            f.argtypes = [P, P, P, U64, P, P, P, U64, P, U64]
+            f.restype = U64
+        lib.or_join_grace.argtypes = [P, P, P, U64, P, P, P, U64, P, U64, ctypes.c_int, ctypes.c_int]
+        lib.or_join_grace.restype = U64
+        if not lib.or_gf_init():
+            raise RuntimeError("oracle: x is not primitive under the field polynomial")
+        _lib = lib
+        return lib
+
+
+def _buf(b: bytes):
+    a = np.frombuffer(bytes(b) + b"\0", dtype=np.uint8)
+    return a, a.ctypes.data
+
+
+# ---------------------------------------------------------------- GF(2^16)
+
+def gf_tables():
+    """(log[65536], antilog[65535]) as uint16 arrays."""
+    lib = _load()
+    log = np.zeros(65536, dtype=np.uint16)
+    alog = np.zeros(65535, dtype=np.uint16)
+    lib.or_gf_tables(log.ctypes.data, alog.ctypes.data)
+    return log, alog
+
+
+def gf_mul_tab(a: int, b: int) -> int:
+    return int(_load().or_gf_mul_tab(a, b))
+
+
+def gf_mul_shift(a: int, b: int) -> int:
+    return int(_load().or_gf_mul_shift(a, b))
+
+
+def gf_pow_x(e: int) -> int:
+    return int(_load().or_gf_pow_x(e))
+
+
+# ---------------------------------------------------------------- signatures
+
+def sig(key: bytes, method: str = "tables") -> int:
+    """Packed 64-bit signature of one key: component k (1..4) in bits [16(k-1), 16k)."""
+    lib = _load()
+    arr, p = _buf(key)
+    f = lib.or_sig_tables if method == "tables" else lib.or_sig_horner
+    return int(f(p, len(key)))
+
+
+def components(s: int):
+    return tuple((s >> (16 * k)) & 0xFFFF for k in range(4))
+
+
+def sig_batch(arena: np.ndarray, off: np.ndarray, method: str = "tables", nthreads: int = 1) -> np.ndarray:
+    lib = _load()
+    n = off.shape[0] - 1
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    arena = np.ascontiguousarray(arena)
+    off = np.ascontiguousarray(off, dtype=np.uint64)
+    lib.or_sig_batch(arena.ctypes.data, off.ctypes.data, n, out.ctypes.data,
+                     0 if method == "tables" else 1, nthreads)
+    return out[:n]
+
+
+# ---------------------------------------------------------------- joins
+
+def _rel_ptrs(rel):
+    arena = np.ascontiguousarray(rel.arena)
+    off = np.ascontiguousarray(rel.off, dtype=np.uint64)
+    ids = np.ascontiguousarray(rel.ids, dtype=np.uint32)
+    return (arena, off, ids), (arena.ctypes.data, off.ctypes.data, ids.ctypes.data, off.shape[0] - 1)
+
+
+def _run_join(fn, R, S, extra=(), cap_hint=None):
+    keepR, pr = _rel_ptrs(R)
+    keepS, ps = _rel_ptrs(S)
+    cap = cap_hint if cap_hint is not None else max(1024, ps[3])
+    while True:
+        out = np.zeros(2 * max(cap, 1), dtype=np.uint32)
+        cnt = int(fn(*pr, *ps, out.ctypes.data, cap, *extra))
+        if cnt <= cap:
+            return sort_pairs(out[:2 * cnt].reshape(-1, 2))
+        cap = cnt
+
+
+def sort_pairs(pairs: np.ndarray) -> np.ndarray:
+    """Sort (r_id, s_id) rows ascending, lexicographically, as uint32."""
+    pairs = np.asarray(pairs, dtype=np.uint32).reshape(-1, 2)
+    if pairs.shape[0] == 0:
+        return pairs
+    key = (pairs[:, 0].astype(np.uint64) << np.uint64(32)) | pairs[:, 1].astype(np.uint64)
+    order = np.argsort(key, kind="stable")
+    return pairs[order]
+
+
+def join_nested(R, S) -> np.ndarray:
+    return _run_join(_load().or_join_nested, R, S)
+
+
+def join_simple(R, S) -> np.ndarray:
+    return _run_join(_load().or_join_simple, R, S)
+
+
+def join_grace(R, S, log2_parts: int = 8, nthreads: int = 4) -> np.ndarray:
+    return _run_join(_load().or_join_grace, R, S, extra=(log2_parts, nthreads))

@@ -1,0 +1,100 @@
+"""Pins of the oracle's joins: nested loop (brute force) = simple hash join =
+Grace hash join (Section 2), plus the ground truth of the input generator."""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from cases import edge_keys, five_symbol_collision
+
+
+def brute(rkeys, skeys, rids=None, sids=None):
+    rids = rids if rids is not None else list(range(len(rkeys)))
+    sids = sids if sids is not None else list(range(len(skeys)))
+    out = [(rids[r], sids[s]) for r in range(len(rkeys)) for s in range(len(skeys)) if rkeys[r] == skeys[s]]
+    return np.array(sorted(out), dtype=np.uint32).reshape(-1, 2)
+
+
+def run_all(R, S):
+    a = oracle.join_nested(R, S)
+    b = oracle.join_simple(R, S)
+    c = oracle.join_grace(R, S, log2_parts=3, nthreads=3)
+    assert np.array_equal(a, b) and np.array_equal(b, c)
+    return a
+
+
+def test_edge_keys_join():
+    keys = edge_keys()
+    R = workloads.relation_from_keys(keys)
+    S = workloads.relation_from_keys(list(reversed(keys)))
+    got = run_all(R, S)
+    assert np.array_equal(got, brute(keys, list(reversed(keys))))
+    # "A" and "A\0" share a signature but are different keys
+    ia, ia0 = keys.index(b"A"), keys.index(b"A\0")
+    assert oracle.sig(keys[ia]) == oracle.sig(keys[ia0])
+    pairs = {tuple(p) for p in got.tolist()}
+    rev = list(reversed(keys))
+    assert (ia, rev.index(b"A\0")) not in pairs
+
+
+def test_collision_pair_does_not_join():
+    a, b = five_symbol_collision()
+    R = workloads.relation_from_keys([a])
+    S = workloads.relation_from_keys([b, a])
+    got = run_all(R, S)
+    assert got.tolist() == [[0, 1]]
+
+
+def test_random_small_with_duplicates_and_ids():
+    rng = random.Random(10)
+    pool = [bytes(rng.randrange(3) for _ in range(rng.randrange(0, 5))) for _ in range(30)]
+    rkeys = [rng.choice(pool) for _ in range(300)]
+    skeys = [rng.choice(pool) for _ in range(500)]
+    rids = [rng.randrange(2 ** 32) for _ in rkeys]
+    sids = [rng.randrange(2 ** 32) for _ in skeys]
+    R = workloads.relation_from_keys(rkeys, rids)
+    S = workloads.relation_from_keys(skeys, sids)
+    got = run_all(R, S)
+    assert np.array_equal(got, brute(rkeys, skeys, rids, sids))
+
+
+def test_empty_relations():
+    R = workloads.relation_from_keys([])
+    S = workloads.relation_from_keys([b"x"])
+    assert run_all(R, S).shape == (0, 2)
+    assert run_all(S, R).shape == (0, 2)
+
+
+def test_plain_workload_ground_truth():
+    wl = workloads.generate(workloads.CONFIGS["plain"])
+    got = oracle.join_simple(wl.R, wl.S)
+    assert len(got) == wl.expected_pairs() == 30_000
+    g2 = oracle.join_grace(wl.R, wl.S, log2_parts=6, nthreads=4)
+    assert np.array_equal(got, g2)
+    # every pair is an exact copy made by the generator
+    src = wl.s_src[got[:, 1]]
+    assert np.array_equal(src, got[:, 0].astype(np.int64))
+
+
+def test_collision_workload_ground_truth():
+    spec = workloads.CONFIGS["collision"].scaled(500, 5_000)
+    wl = workloads.generate(spec)
+    got = oracle.join_simple(wl.R, wl.S)
+    assert len(got) == wl.expected_pairs() == int((wl.s_kind == 1).sum()) == 2_000
+    assert set(wl.s_kind[got[:, 1]].tolist()) == {1}
+    # near-duplicates exist, share no signature with their source (<= 6 byte changes
+    # touch <= 6 symbols; equal signatures would need a 2^-64 event) and do not join
+    near = np.nonzero(wl.s_kind == 2)[0][:200]
+    sS = oracle.sig_batch(wl.S.arena, wl.S.off)
+    sR = oracle.sig_batch(wl.R.arena, wl.R.off)
+    assert len(near) == 200 and not np.any(sS[near] == sR[wl.s_src[near]])
+
+
+def test_large_workload_ground_truth_scaled():
+    spec = workloads.CONFIGS["large"].scaled(20_000, 200_000)
+    wl = workloads.generate(spec)
+    got = oracle.join_grace(wl.R, wl.S, log2_parts=8, nthreads=4)
+    assert len(got) == wl.expected_pairs()
+    assert (wl.r_mult > 1).any()
