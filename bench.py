@@ -1,0 +1,407 @@
+"""Benchmark of the GB300 algebraic-signature equi-join.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload large] [--impl reference]
+
+One step = one whole signature hash join T = Join(R, S) on device-resident
+inputs: signatures of R, build of the signature hash table, probe with every
+S key (S signature, table walk, byte-exact verification, output compaction).
+The workload is synthetic (workloads.CONFIGS).  Rank 0 prints one JSON line.
+
+Multi-GPU: the join does not shard here (replicas only): every rank runs its
+own copy of the workload and the value is the sum of S tuples over ranks
+divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import workloads  # noqa: E402
+
+METRIC = "probe tuples/s"
+UNIT = "tuples/s"
+L2_BYTES = 126 * 2 ** 20
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def workload_desc(name: str, spec) -> str:
+    return (f"{name}: |R|={spec.m:,} x |S|={spec.n:,}, key length {spec.r_len[0]}-{spec.r_len[1]} B "
+            f"{spec.alphabet}, {int(spec.frac_copy * 100)}% S copies"
+            + (f" (Zipf {spec.zipf_s})" if spec.zipf_s else "")
+            + (f", {int(spec.frac_near * 100)}% near-duplicates" if spec.frac_near else "")
+            + (f", {spec.dup_frac:.0%} of R keys duplicated {spec.dup[0]}-{spec.dup[1]}x" if spec.dup_frac else ""))
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm, smax, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = max(smax, float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def pct(xs, q):
+    xs = sorted(xs)
+    if not xs:
+        return None
+    k = min(len(xs) - 1, max(0, int(round(q / 100.0 * (len(xs) - 1)))))
+    return xs[k]
+
+
+# --------------------------------------------------------------------------- reference arm (the CPU oracle)
+
+def cpu_oracle_run(wl, n_s: int, cores: int) -> float:
+    """Oracle on the host: signatures of all of R and of the first n_s S keys,
+    then the exact Grace hash join of R with those S keys.  Returns seconds."""
+    import oracle
+    from workloads import Relation
+    S = wl.S
+    Ss = Relation(S.arena, S.off[: n_s + 1].copy(), S.ids[:n_s].copy())
+    t0 = time.perf_counter()
+    oracle.sig_batch(wl.R.arena, wl.R.off, nthreads=cores)
+    oracle.sig_batch(Ss.arena, Ss.off, nthreads=cores)
+    oracle.join_grace(wl.R, Ss, log2_parts=10, nthreads=cores)
+    return time.perf_counter() - t0
+
+
+class CpuModel:
+    """Time of the oracle as a + b * n_s (fixed R work + per-S-key work), fitted
+    from two sample sizes; value = |S| / (a + b |S|) S tuples per second."""
+
+    def __init__(self, wl, cores: int, budget_s: float = 12.0):
+        self.wl, self.cores = wl, cores
+        n = wl.S.n
+        self.n1 = max(1, min(n, max(2000, n // 50)))
+        t1 = cpu_oracle_run(wl, self.n1, cores)
+        t1b = cpu_oracle_run(wl, self.n1, cores)
+        t1 = min(t1, t1b)
+        if self.n1 >= n:
+            self.a, self.b, self.n2, self.t2 = 0.0, t1 / n, n, t1
+            return
+        per = t1 / self.n1
+        self.n2 = int(min(n, max(2 * self.n1, budget_s / max(per, 1e-12))))
+        self.t2 = cpu_oracle_run(wl, self.n2, cores)
+        self.b = max(1e-12, (self.t2 - t1) / (self.n2 - self.n1))
+        self.a = max(0.0, t1 - self.b * self.n1)
+
+    def value_from(self, t: float, n_s: int) -> float:
+        """S tuples/s of the whole join, extrapolating one run of n_s S keys."""
+        n = self.wl.S.n
+        per = max(1e-12, (t - self.a) / n_s)
+        return n / (self.a + per * n)
+
+    def sample_text(self) -> str:
+        return (f"all {self.wl.R.n:,} R keys with the first {self.n1:,} and {self.n2:,} of {self.wl.S.n:,} S keys "
+                f"(signatures + Grace join); time fitted as fixed + per-S-key and extrapolated to all of S")
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    spec = workloads.CONFIGS[args.workload]
+    wl = workloads.generate(spec)
+    cores = os.cpu_count() or 1
+    model = CpuModel(wl, cores, budget_s=max(4.0, 60.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_oracle_run(wl, model.n2, cores)
+    vals = []
+    for _ in range(args.steps):
+        vals.append(model.value_from(cpu_oracle_run(wl, model.n2, cores), model.n2))
+    value = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.S.n / value * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic", "config": {"workload": workload_desc(args.workload, spec)},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": model.sample_text()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# --------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import paper_2411_18183_gb300 as ag
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world != args.gpus:
+        raise SystemExit(f"--gpus {args.gpus} but WORLD_SIZE={world}")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(x: float) -> float:
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    spec = workloads.CONFIGS[args.workload]
+    t_gen = time.perf_counter()
+    # inputs live in pinned host memory (for the end-to-end leg) and are copied once
+    # to device memory (for the device-resident leg)
+    pinned = []
+
+    def alloc(nbytes):
+        t = torch.empty(nbytes, dtype=torch.uint8, pin_memory=True)
+        pinned.append(t)
+        return t.numpy()
+
+    wl = workloads.generate(spec, alloc=alloc)
+    t_gen = time.perf_counter() - t_gen
+    m, n = wl.R.n, wl.S.n
+    key_bytes = wl.R.nbytes + wl.S.nbytes
+
+    def host_rel(rel):
+        return (torch.from_numpy(rel.arena), torch.from_numpy(rel.off.view(np.int64)).pin_memory(),
+                torch.from_numpy(rel.ids.view(np.int32)).pin_memory())
+
+    hR, hS = host_rel(wl.R), host_rel(wl.S)
+    dR = ag.DeviceRelation(hR[0].cuda(), hR[1].cuda(), hR[2].cuda())
+    dS = ag.DeviceRelation(hS[0].cuda(), hS[1].cuda(), hS[2].cuda())
+    lf = args.load_factor
+    ws = ag.alloc_ws(ag.join_ws_bytes(m, lf))
+    tb = ag.join_table_bytes(m, lf)
+    cap = int(max(1024, wl.expected_pairs() * 1.25 + 1024))
+    pairs = torch.empty(2 * cap, dtype=torch.int32, device="cuda")
+    count = ws[tb:tb + 8].view(torch.int64)
+    stream = torch.cuda.current_stream()
+
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+
+    def step(evs=None):
+        if evs:
+            evs[0].record(stream)
+        t = ag.join_build(dR, ws[:tb], lf, stream=stream)
+        if evs:
+            evs[1].record(stream)
+        ag.join_probe(t, dS, pairs, count, sync=False, stream=stream)
+        if evs:
+            evs[2].record(stream)
+
+    # correctness of the timed configuration: total pairs = the generator's ground truth
+    step()
+    torch.cuda.synchronize()
+    total_pairs = int(count.item())
+    expected = wl.expected_pairs()
+    if total_pairs != expected:
+        raise SystemExit(f"pair count {total_pairs} != expected {expected}")
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    t0.record(stream)
+    for k in range(args.steps):
+        step(ev[k])
+    t1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    total_ms = t0.elapsed_time(t1)
+    build_ms = [e[0].elapsed_time(e[1]) for e in ev]
+    probe_ms = [e[1].elapsed_time(e[2]) for e in ev]
+    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    total_ms = max_over_ranks(total_ms)
+    ms_per_step = total_ms / args.steps
+    value = world * n / (ms_per_step * 1e-3)
+
+    # signature kernel alone on S (key GB/s against HBM)
+    sig_out = torch.empty(n, dtype=torch.int64, device="cuda")
+    for _ in range(2):
+        ag.sig_compute(dS, sig_out, stream=stream)
+    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    s0.record(stream)
+    for _ in range(reps):
+        ag.sig_compute(dS, sig_out, stream=stream)
+    s1.record(stream)
+    torch.cuda.synchronize()
+    sig_ms = s0.elapsed_time(s1) / reps
+    hbm, peak_kind = peaks()
+    sig_gbps = (wl.S.nbytes + 16 * n) / (sig_ms * 1e-3) / 1e9
+
+    # end to end through the C ABI from pinned host buffers: H2D of R and S,
+    # the join, D2H of the count and the pairs
+    def e2e_step():
+        dR.arena.copy_(hR[0], non_blocking=True)
+        dR.off.copy_(hR[1], non_blocking=True)
+        dR.ids.copy_(hR[2], non_blocking=True)
+        dS.arena.copy_(hS[0], non_blocking=True)
+        dS.off.copy_(hS[1], non_blocking=True)
+        dS.ids.copy_(hS[2], non_blocking=True)
+        st, cnt = ag.join_into(dR, dS, ws, pairs, count, lf, sync=True, stream=stream)
+        out = pairs[: 2 * cnt].cpu()
+        return cnt, out.numel() * 4
+
+    h2d = sum(int(t.numel() * t.element_size()) for t in (*hR, *hS))
+    e2e_steps = max(2, min(args.steps, 5))
+    e2e_step()
+    barrier()
+    te = time.perf_counter()
+    d2h = 0
+    for _ in range(e2e_steps):
+        cnt, nb = e2e_step()
+        d2h = nb + 8
+    barrier()
+    e2e_s = max_over_ranks((time.perf_counter() - te) / e2e_steps)
+    e2e_value = world * n / e2e_s
+
+    # roofline of the dominant kernel: the probe (S signatures + probe + verify + compaction)
+    probe_avg = statistics.mean(probe_ms)
+    lens = np.diff(wl.S.off)
+    src = wl.s_src[wl.s_kind == 1]
+    verified_bytes = int((wl.r_mult[src].astype(np.int64) * lens[wl.s_kind == 1].astype(np.int64)).sum())
+    probe_alg = (wl.S.nbytes + 8 * (n + 1) + 4 * n          # S keys, offsets, ids
+                 + 8 * n                                     # one slot read per S key
+                 + total_pairs * (8 + 16 + 4)                # sigR, offR pair, idR per verified candidate
+                 + verified_bytes                            # R key bytes compared
+                 + 8 * total_pairs)                          # output pairs
+    achieved = probe_alg / (probe_avg * 1e-3) / 1e9
+    traffic = None
+    tp = os.path.join(ROOT, "profiles", "probe_traffic.json")
+    if os.path.exists(tp):
+        with open(tp) as f:
+            d = json.load(f)
+        if d.get("workload") == args.workload and d.get("kernel_rev") == KERNEL_REV:
+            traffic = d.get("bytes_per_launch")
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cores = os.cpu_count() or 1
+        model = CpuModel(wl, cores)
+        cpu = {"value": model.value_from(model.t2, model.n2), "unit": UNIT, "cores": cores, "kind": "oracle",
+               "sample": model.sample_text()}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": workload_desc(args.workload, spec), "load_factor": lf,
+                   "l2": f"inputs larger than L2 ({key_bytes / 1e9:.2f} GB of keys), no flush",
+                   "parallelism": f"replicas{world}"},
+        "p50_ms": pct(step_ms, 50), "p99_ms": pct(step_ms, 99),
+        "build_ms": statistics.mean(build_ms), "probe_ms": probe_avg,
+        "probe_only_tuples_per_s": n / (probe_avg * 1e-3),
+        "key_gbps": key_bytes / (ms_per_step * 1e-3) / 1e9,
+        "sig_kernel": {"gbps": sig_gbps, "frac_hbm": sig_gbps / hbm, "ms": sig_ms},
+        "pairs": total_pairs,
+        "clocks": clk,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": 3 * args.steps,
+        "roofline": {"bound": "hbm", "kernel": "probe_kernel", "achieved": achieved, "peak": hbm,
+                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
+                     "algorithmic_bytes": probe_alg},
+        "cpu_baseline": cpu,
+        "gen_s": t_gen,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+KERNEL_REV = "v1"
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--workload", default="large", choices=sorted(workloads.CONFIGS))
+    ap.add_argument("--load-factor", type=float, default=0.5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,212 @@
+"""Python binding of libalgsig.so, the GB300 algebraic-signature equi-join.
+
+Argument marshalling only: every step of the join runs in the library's CUDA
+kernels.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if the compiled library is missing, every call raises.
+
+    import paper_2411_18183_gb300 as ag
+    R = ag.DeviceRelation.from_host(arena, off, ids)      # or .from_tensors(...)
+    sig = ag.sig_compute(R)                                # uint64 signatures (torch.int64 bits)
+    pairs = ag.join(R, S)                                  # (cnt, 2) uint32 pairs as torch.int32 bits
+"""
+from __future__ import annotations
+
+import ctypes
+import dataclasses
+import os
+import threading
+
+import torch
+
+from . import build as _build_mod
+
+LIB_PATH = _build_mod.LIB
+
+AS_OK = 0
+AS_ERR_INVALID = 1
+AS_ERR_NOMEM = 2
+AS_ERR_CAPACITY = 3
+AS_ERR_TABLE_FULL = 4
+AS_ERR_CUDA = 5
+AS_ERR_UNSUPPORTED = 6
+
+EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_join_table_bytes",
+           "as_join_build", "as_join_probe", "as_join_ws_bytes", "as_join")
+
+
+class AlgsigError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+class Table(ctypes.Structure):
+    """as_table of algsig.h: description of a built signature hash table."""
+    _fields_ = [("slots", ctypes.c_void_p), ("sigR", ctypes.c_void_p), ("arenaR", ctypes.c_void_p),
+                ("offR", ctypes.c_void_p), ("idR", ctypes.c_void_p), ("flags", ctypes.c_void_p),
+                ("m", ctypes.c_uint64), ("cap", ctypes.c_uint64), ("log2cap", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32)]
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libalgsig.so (built by __graft_entry__.build() or paper_2411_18183_gb300.build)."""
+    global _lib
+    with _lock:
+        if _lib is not None and path is None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise RuntimeError(f"libalgsig.so not built ({p}); run python -m paper_2411_18183_gb300.build")
+        lib = ctypes.CDLL(p)
+        P, U64, SZ, F, S = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_float, ctypes.c_int
+        lib.as_last_error.restype = ctypes.c_char_p
+        lib.as_status_string.restype = ctypes.c_char_p
+        lib.as_status_string.argtypes = [S]
+        lib.as_version.restype = S
+        lib.as_sig_compute.argtypes = [P, P, U64, P, P]
+        lib.as_sig_compute.restype = S
+        lib.as_join_table_bytes.argtypes = [U64, F]
+        lib.as_join_table_bytes.restype = SZ
+        lib.as_join_ws_bytes.argtypes = [U64, F]
+        lib.as_join_ws_bytes.restype = SZ
+        lib.as_join_build.argtypes = [P, SZ, P, P, P, U64, P, F, ctypes.POINTER(Table), P]
+        lib.as_join_build.restype = S
+        lib.as_join_probe.argtypes = [ctypes.POINTER(Table), P, P, P, U64, P, P, U64, P, P, P]
+        lib.as_join_probe.restype = S
+        lib.as_join.argtypes = [P, P, P, U64, P, P, P, U64, F, P, SZ, P, U64, P, P, P]
+        lib.as_join.restype = S
+        if path is None:
+            _lib = lib
+        return lib
+
+
+def _check(st: int, allow=()):
+    if st != AS_OK and st not in allow:
+        lib = load()
+        raise AlgsigError(st, f"{lib.as_status_string(st).decode()}: {lib.as_last_error().decode()}")
+    return st
+
+
+def _ptr(t: torch.Tensor | None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int | None:
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+@dataclasses.dataclass
+class DeviceRelation:
+    """A relation resident in device memory: key i = arena[off[i]:off[i+1]].
+
+    arena: uint8 (16-byte aligned, readable to the next 16-byte boundary past
+    the last key byte); off: int64 tensor holding the uint64 offsets (n+1);
+    ids: int32 tensor holding uint32 ids, or None for ids = row numbers."""
+    arena: torch.Tensor
+    off: torch.Tensor
+    ids: torch.Tensor | None = None
+
+    @property
+    def n(self) -> int:
+        return int(self.off.numel() - 1)
+
+    @staticmethod
+    def from_host(arena, off, ids=None, device="cuda", non_blocking=False) -> "DeviceRelation":
+        """Copy numpy / torch host arrays to the device (allocating with torch)."""
+        a = torch.as_tensor(arena).view(torch.uint8)
+        o = torch.as_tensor(off).view(torch.int64)
+        i = None if ids is None else torch.as_tensor(ids).view(torch.int32)
+        pad = (-a.numel()) % 16
+        if pad:
+            a = torch.cat([a, torch.zeros(pad, dtype=torch.uint8)])
+        return DeviceRelation(a.to(device, non_blocking=non_blocking), o.to(device, non_blocking=non_blocking),
+                              None if i is None else i.to(device, non_blocking=non_blocking))
+
+
+def version() -> int:
+    return int(load().as_version())
+
+
+def sig_compute(rel: DeviceRelation, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """as_sig_compute: uint64 signature of every key (returned as int64 bits)."""
+    lib = load()
+    n = rel.n
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int64, device=rel.arena.device)
+    _check(lib.as_sig_compute(_ptr(rel.arena), _ptr(rel.off), n, _ptr(out), _stream(stream)))
+    return out
+
+
+def join_table_bytes(m: int, load_factor: float = 0.5) -> int:
+    return int(load().as_join_table_bytes(m, load_factor))
+
+
+def join_ws_bytes(m: int, load_factor: float = 0.5) -> int:
+    return int(load().as_join_ws_bytes(m, load_factor))
+
+
+def alloc_ws(nbytes: int, device="cuda") -> torch.Tensor:
+    """Workspace buffer (256-byte aligned: torch's allocator aligns to 512)."""
+    return torch.empty(max(nbytes, 256), dtype=torch.uint8, device=device)
+
+
+def join_build(R: DeviceRelation, ws: torch.Tensor, load_factor: float = 0.5, sigR: torch.Tensor | None = None,
+               stream=None) -> Table:
+    lib = load()
+    t = Table()
+    _check(lib.as_join_build(_ptr(ws), ws.numel(), _ptr(R.arena), _ptr(R.off), _ptr(R.ids), R.n, _ptr(sigR),
+                             load_factor, ctypes.byref(t), _stream(stream)))
+    return t
+
+
+def join_probe(t: Table, S: DeviceRelation, pairs: torch.Tensor, count: torch.Tensor,
+               sigS_out: torch.Tensor | None = None, sync: bool = True, stream=None) -> int | None:
+    """as_join_probe.  pairs: int32 tensor of 2*cap entries; count: int64 device scalar.
+    With sync=True returns the pair count (raises AlgsigError on capacity overflow)."""
+    lib = load()
+    cap = pairs.numel() // 2
+    h = ctypes.c_uint64(0)
+    _check(lib.as_join_probe(ctypes.byref(t), _ptr(S.arena), _ptr(S.off), _ptr(S.ids), S.n, _ptr(sigS_out),
+                             _ptr(pairs), cap, _ptr(count), ctypes.byref(h) if sync else None, _stream(stream)))
+    return int(h.value) if sync else None
+
+
+def join_into(R: DeviceRelation, S: DeviceRelation, ws: torch.Tensor, pairs: torch.Tensor, count: torch.Tensor,
+              load_factor: float = 0.5, sync: bool = True, stream=None, allow_capacity: bool = False):
+    """as_join into caller buffers.  Returns (status, count) when sync, else (status, None)."""
+    lib = load()
+    cap = pairs.numel() // 2
+    h = ctypes.c_uint64(0)
+    st = lib.as_join(_ptr(R.arena), _ptr(R.off), _ptr(R.ids), R.n, _ptr(S.arena), _ptr(S.off), _ptr(S.ids), S.n,
+                     load_factor, _ptr(ws), ws.numel(), _ptr(pairs), cap, _ptr(count),
+                     ctypes.byref(h) if sync else None, _stream(stream))
+    _check(st, allow=(AS_ERR_CAPACITY,) if allow_capacity else ())
+    return st, (int(h.value) if sync else None)
+
+
+def join(R: DeviceRelation, S: DeviceRelation, load_factor: float = 0.5, cap_pairs: int | None = None,
+         stream=None) -> torch.Tensor:
+    """The whole signature join.  Returns a (cnt, 2) int32 tensor of (r_id, s_id)
+    pairs (uint32 bits) in unspecified order, retrying once with the exact
+    size if the first guess of the capacity was too small."""
+    dev = R.arena.device
+    ws = alloc_ws(join_ws_bytes(R.n, load_factor), dev)
+    cap = cap_pairs if cap_pairs is not None else max(1024, S.n)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    while True:
+        pairs = torch.empty(2 * max(cap, 1), dtype=torch.int32, device=dev)
+        st, cnt = join_into(R, S, ws, pairs, count, load_factor, sync=True, stream=stream, allow_capacity=True)
+        if st == AS_OK:
+            return pairs[:2 * cnt].view(-1, 2)
+        cap = cnt

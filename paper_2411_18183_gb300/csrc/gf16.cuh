@@ -1,0 +1,116 @@
+// gf16.cuh -- GF(2^16) arithmetic and the algebraic-signature inner loop for
+// sm_103a.
+//
+// Signature (Section 3.1 of the paper): for a key of l 16-bit symbols p_i,
+//     sig^k = sum_{i=0}^{l-1} p_i * x^(k*i)  in GF(2^16) = GF(2)[x] / P(x),
+// P(x) = x^16 + x^12 + x^3 + x + 1, k = 1..4, sums are XOR.
+//
+// Evaluation here is Horner's rule over 16-byte chunks (8 symbols), run from
+// the last chunk to the first, with delayed reduction: the accumulator of
+// component k is kept as an unreduced GF(2) polynomial in a 32-bit register,
+// shifted by 8k bits per chunk and reduced back to 16 bits only when it would
+// overflow.  A reduction clears the bits above 16 with two byte-indexed table
+// lookups (bits 16..23 and 24..31), each entry holding b*x^16 (or b*x^24)
+// mod P together with b shifted into the cleared byte, so that one XOR both
+// removes the high byte and adds its residue.  The tables live in shared
+// memory, replicated once per bank so that the 32 lanes of a warp never
+// conflict.
+#pragma once
+#include <cstdint>
+
+namespace algsig {
+
+constexpr uint32_t kPoly = 0x1100Bu;   // x^16 + x^12 + x^3 + x + 1
+constexpr uint32_t kOrder = 65535u;    // order of x (x is primitive for this P)
+
+// Shared-memory reduction tables: 2 tables x 256 entries x 32 replicas.
+constexpr int kRedWords = 2 * 256 * 32;
+constexpr int kRedBytes = kRedWords * 4;
+
+__host__ __device__ __forceinline__ uint32_t gf_times_x(uint32_t a) {
+  a <<= 1;
+  return (a & 0x10000u) ? (a ^ kPoly) : a;
+}
+
+// Fill the replicated reduction tables.  `tmp` is 512 words of scratch shared
+// memory.  Must be called by the whole block; ends with __syncthreads().
+__device__ __forceinline__ void init_red_tables(uint32_t* red, uint32_t* tmp) {
+  for (int e = threadIdx.x; e < 512; e += blockDim.x) {
+    const int tbl = e >> 8;            // 0: bits 16..23, 1: bits 24..31
+    const uint32_t b = (uint32_t)(e & 255);
+    uint32_t v = b;
+    const int steps = 16 + 8 * tbl;    // b * x^16 or b * x^24
+    for (int i = 0; i < steps; i++) v = gf_times_x(v);
+    tmp[e] = v ^ (b << (16 + 8 * tbl));
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kRedWords; i += blockDim.x) red[i] = tmp[i >> 5];
+  __syncthreads();
+}
+
+// 32-bit unreduced value -> 16-bit residue mod P.  `redl` = red + lane.
+__device__ __forceinline__ uint32_t red32(uint32_t u, const uint32_t* __restrict__ redl) {
+  const uint32_t b2 = (u >> 16) & 0xFFu;
+  const uint32_t b3 = u >> 24;
+  return u ^ redl[b2 << 5] ^ redl[(256u + b3) << 5];
+}
+
+// value < 2^24 -> 16-bit residue (only bits 16..23 to clear)
+__device__ __forceinline__ uint32_t red24(uint32_t u, const uint32_t* __restrict__ redl) {
+  return u ^ redl[(u >> 16) << 5];
+}
+
+// One Horner step over a 16-byte chunk: acc_k <- acc_k * x^(8k) + sum_j q_j x^(kj),
+// where q_{2t} = low half of word t and q_{2t+1} = high half of word t.
+// Accumulators enter and leave reduced (< 2^16).
+__device__ __forceinline__ void horner_chunk(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
+                                             uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& a4,
+                                             const uint32_t* __restrict__ redl) {
+  const uint32_t l0 = v0 & 0xFFFFu, h0 = v0 >> 16;
+  const uint32_t l1 = v1 & 0xFFFFu, h1 = v1 >> 16;
+  const uint32_t l2 = v2 & 0xFFFFu, h2 = v2 >> 16;
+  const uint32_t l3 = v3 & 0xFFFFu, h3 = v3 >> 16;
+  uint32_t u;
+  // k = 1: 8 symbols, growth 8 bits
+  u = (a1 << 8) ^ l0 ^ (h0 << 1) ^ (l1 << 2) ^ (h1 << 3) ^ (l2 << 4) ^ (h2 << 5) ^ (l3 << 6) ^ (h3 << 7);
+  a1 = red24(u, redl);
+  // k = 2: 8 symbols, growth 16 bits
+  u = (a2 << 16) ^ l0 ^ (h0 << 2) ^ (l1 << 4) ^ (h1 << 6) ^ (l2 << 8) ^ (h2 << 10) ^ (l3 << 12) ^ (h3 << 14);
+  a2 = red32(u, redl);
+  // k = 3: two halves of 4 symbols, growth 12 bits each (upper half first)
+  u = (a3 << 12) ^ l2 ^ (h2 << 3) ^ (l3 << 6) ^ (h3 << 9);
+  a3 = red32(u, redl);
+  u = (a3 << 12) ^ l0 ^ (h0 << 3) ^ (l1 << 6) ^ (h1 << 9);
+  a3 = red32(u, redl);
+  // k = 4: two halves of 4 symbols, growth 16 bits each
+  u = (a4 << 16) ^ l2 ^ (h2 << 4) ^ (l3 << 8) ^ (h3 << 12);
+  a4 = red32(u, redl);
+  u = (a4 << 16) ^ l0 ^ (h0 << 4) ^ (l1 << 8) ^ (h1 << 12);
+  a4 = red32(u, redl);
+}
+
+// Mask of bytes [b0, b1) of a 16-byte chunk, for its 32-bit word j.
+__device__ __forceinline__ uint32_t byte_range_mask(int b0, int b1, int j) {
+  int lo = b0 - 4 * j, hi = b1 - 4 * j;
+  lo = lo < 0 ? 0 : (lo > 4 ? 4 : lo);
+  hi = hi < 0 ? 0 : (hi > 4 ? 4 : hi);
+  const uint32_t mhi = hi >= 4 ? 0xFFFFFFFFu : ((1u << (8 * hi)) - 1u);
+  const uint32_t mlo = lo >= 4 ? 0xFFFFFFFFu : ((1u << (8 * lo)) - 1u);
+  return mhi & ~mlo;
+}
+
+// Murmur3 64-bit finaliser: bucket hash of (signature, length).
+__device__ __forceinline__ uint64_t fmix64(uint64_t h) {
+  h ^= h >> 33;
+  h *= 0xff51afd7ed558ccdull;
+  h ^= h >> 33;
+  h *= 0xc4ceb9fe1a85ec53ull;
+  h ^= h >> 33;
+  return h;
+}
+
+__device__ __forceinline__ uint64_t sig_hash(uint64_t sig, uint64_t len) {
+  return fmix64(sig ^ (len * 0x9E3779B97F4A7C15ull));
+}
+
+}  // namespace algsig

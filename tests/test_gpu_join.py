@@ -1,0 +1,124 @@
+"""GPU signature join (as_join / as_join_build / as_join_probe through the C
+ABI) against the CPU oracle: sorted (r_id, s_id) pairs, bit-exact."""
+import random
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+from cases import edge_keys, five_symbol_collision
+from packing import relation_garbage_tail
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(ag, rel):
+    return ag.DeviceRelation.from_host(rel.arena, rel.off, rel.ids)
+
+
+def gpu_join(ag, R, S, lf=0.5):
+    pairs = ag.join(dev(ag, R), dev(ag, S), load_factor=lf)
+    return oracle.sort_pairs(pairs.cpu().numpy().view(np.uint32))
+
+
+def check(ag, R, S, lf=0.5):
+    got = gpu_join(ag, R, S, lf)
+    want = oracle.join_simple(R, S)
+    assert got.shape == want.shape, (got.shape, want.shape)
+    assert np.array_equal(got, want)
+    return want
+
+
+def test_edge_keys(cuda):
+    keys = edge_keys()
+    R = relation_garbage_tail(keys, seed=1)
+    S = relation_garbage_tail(list(reversed(keys)) + keys, seed=2)
+    check(cuda, R, S)
+
+
+def test_collision_pair_and_padding_twins(cuda):
+    a, b = five_symbol_collision()
+    R = relation_garbage_tail([a, b"A", b"\0"], seed=3)
+    S = relation_garbage_tail([b, b"A\0", b"", b"\0\0", a], seed=4)
+    got = check(cuda, R, S)
+    assert got.tolist() == [[0, 4]]
+
+
+def test_random_small_duplicates_ids_and_load_factors(cuda):
+    rng = random.Random(5)
+    pool = [bytes(rng.randrange(4) for _ in range(rng.randrange(0, 40))) for _ in range(60)]
+    rkeys = [rng.choice(pool) for _ in range(1000)]
+    skeys = [rng.choice(pool) for _ in range(3000)]
+    R = relation_garbage_tail(rkeys, seed=6, ids=[rng.randrange(2 ** 32) for _ in rkeys])
+    S = relation_garbage_tail(skeys, seed=7, ids=[rng.randrange(2 ** 32) for _ in skeys])
+    for lf in (1.0, 0.5, 0.25):
+        check(cuda, R, S, lf)
+
+
+def test_full_table_load_factor_one(cuda):
+    # m = cap = 64: every slot used, probes of absent keys walk the whole table
+    rng = random.Random(8)
+    rkeys = [bytes(rng.randrange(256) for _ in range(20)) for _ in range(64)]
+    skeys = [rng.choice(rkeys) for _ in range(100)] + [b"absent"] * 10
+    check(cuda, workloads.relation_from_keys(rkeys), workloads.relation_from_keys(skeys), lf=1.0)
+
+
+def test_empty_relations(cuda):
+    E = workloads.relation_from_keys([])
+    X = workloads.relation_from_keys([b"x", b""])
+    for R, S in ((E, X), (X, E), (E, E)):
+        got = gpu_join(cuda, R, S)
+        assert got.shape == (0, 2)
+    got = gpu_join(cuda, X, X)
+    assert got.tolist() == [[0, 0], [1, 1]]
+
+
+def test_capacity_overflow_reports_exact_count(cuda):
+    ag = cuda
+    wl = workloads.generate(workloads.CONFIGS["plain"].scaled(1000, 10_000))
+    R, S = dev(ag, wl.R), dev(ag, wl.S)
+    ws = ag.alloc_ws(ag.join_ws_bytes(R.n, 0.5))
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    pairs = torch.full((2 * 100,), -1, dtype=torch.int32, device="cuda")
+    st, cnt = ag.join_into(R, S, ws, pairs, count, 0.5, sync=True, allow_capacity=True)
+    want = oracle.join_simple(wl.R, wl.S)
+    assert st == ag.AS_ERR_CAPACITY and cnt == len(want) == 3000
+    part = pairs.cpu().numpy().view(np.uint32).reshape(-1, 2)
+    wantset = {tuple(p) for p in want.tolist()}
+    assert all(tuple(p) in wantset for p in part.tolist())
+
+
+def test_build_probe_split_and_signature_output(cuda):
+    ag = cuda
+    wl = workloads.generate(workloads.CONFIGS["plain"].scaled(3000, 30_000))
+    R, S = dev(ag, wl.R), dev(ag, wl.S)
+    ws = ag.alloc_ws(ag.join_table_bytes(R.n, 0.5))
+    sigR = ag.sig_compute(R)
+    t = ag.join_build(R, ws, 0.5, sigR=sigR)
+    pairs = torch.empty(2 * 20_000, dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sigS = torch.empty(S.n, dtype=torch.int64, device="cuda")
+    cnt = ag.join_probe(t, S, pairs, count, sigS_out=sigS)
+    got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
+    assert np.array_equal(got, oracle.join_simple(wl.R, wl.S))
+    assert np.array_equal(sigS.cpu().numpy().view(np.uint64), oracle.sig_batch(wl.S.arena, wl.S.off, nthreads=8))
+
+
+def test_plain_config_full(cuda):
+    wl = workloads.generate(workloads.CONFIGS["plain"])
+    want = check(cuda, wl.R, wl.S)
+    assert len(want) == 30_000
+
+
+def test_collision_config_scaled(cuda):
+    wl = workloads.generate(workloads.CONFIGS["collision"].scaled(2_000, 20_000))
+    want = check(cuda, wl.R, wl.S)
+    assert len(want) == 8_000
+
+
+def test_large_config_scaled(cuda):
+    wl = workloads.generate(workloads.CONFIGS["large"].scaled(20_000, 200_000))
+    want = check(cuda, wl.R, wl.S)
+    assert len(want) == wl.expected_pairs()

@@ -1,0 +1,75 @@
+"""GPU signatures (as_sig_compute through the C ABI) against the CPU oracle,
+element by element, bit-exact."""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from cases import edge_keys
+from packing import interleave_gaps, relation_garbage_tail
+
+pytestmark = pytest.mark.gpu
+
+
+def gpu_sigs(ag, rel):
+    R = ag.DeviceRelation.from_host(rel.arena, rel.off, rel.ids)
+    return ag.sig_compute(R).cpu().numpy().view(np.uint64)
+
+
+def check(ag, rel, nthreads=8):
+    got = gpu_sigs(ag, rel)
+    want = oracle.sig_batch(rel.arena, rel.off, nthreads=nthreads)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, f"{bad.size} mismatches, first at key {bad[:5].tolist()}"
+
+
+def test_edge_keys_every_alignment(cuda):
+    keys = edge_keys()
+    for shift in range(16):
+        check(cuda, relation_garbage_tail([b"#" * shift] + interleave_gaps(keys, seed=shift), seed=shift))
+
+
+def test_all_short_lengths_all_alignments(cuda):
+    rng = random.Random(11)
+    keys = []
+    for n in range(0, 80):
+        for _ in range(16):
+            keys.append(bytes(rng.randrange(256) for _ in range(n)))
+    rng.shuffle(keys)
+    check(cuda, relation_garbage_tail(interleave_gaps(keys, seed=1), seed=2))
+
+
+def test_tile_boundaries(cuda):
+    # lengths around multiples of the per-lane tile and of 32 tiles per round
+    rng = random.Random(12)
+    keys = []
+    for base in (256, 512, 768, 8192, 8192 + 256):
+        for d in (-17, -2, -1, 0, 1, 2, 15, 16, 17):
+            keys.append(bytes(rng.randrange(256) for _ in range(base + d)))
+    rng.shuffle(keys)
+    check(cuda, relation_garbage_tail(interleave_gaps(keys, seed=3), seed=4))
+
+
+def test_long_keys_many_rounds_and_exponent_wrap(cuda):
+    rng = np.random.default_rng(13)
+    keys = [rng.integers(0, 256, n, dtype=np.uint8).tobytes() for n in (1, 70_000, 131_069, 131_070, 131_071,
+                                                                          200_001, 300_000)]
+    check(cuda, relation_garbage_tail(interleave_gaps(keys, seed=5), seed=6), nthreads=8)
+
+
+def test_plain_config_full(cuda):
+    wl = workloads.generate(workloads.CONFIGS["plain"])
+    check(cuda, wl.R)
+    check(cuda, wl.S)
+
+
+def test_collision_config_scaled(cuda):
+    wl = workloads.generate(workloads.CONFIGS["collision"].scaled(1_000, 10_000))
+    check(cuda, wl.S)
+
+
+def test_large_config_scaled(cuda):
+    wl = workloads.generate(workloads.CONFIGS["large"].scaled(10_000, 100_000))
+    check(cuda, wl.S)

@@ -73,6 +73,8 @@ CONFIGS = {
     "collision": JoinSpec(m=100_000, n=1_000_000, r_len=(2048, 8192), s_len=(2048, 8192), alphabet="acgt",
                           frac_copy=0.40, frac_near=0.40, near=(1, 6), seed=20083),
 }
+# Profiling case: the shape of "large" at one fifth of the size (still larger than L2).
+CONFIGS["medium"] = dataclasses.replace(CONFIGS["large"], m=200_000, n=2_000_000)
 
 
 def _build_lib() -> None:
