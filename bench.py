@@ -385,7 +385,7 @@ def run_gpu(args):
     return 0
 
 
-KERNEL_REV = "v1"
+KERNEL_REV = "v3"
 
 
 def main():

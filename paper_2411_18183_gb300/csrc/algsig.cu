@@ -1,29 +1,13 @@
 // algsig.cu -- sm_103a kernels and C ABI of the algebraic-signature equi-join.
 //
 // Pipeline of one join T = Join(R, S) (Figure 2 of the paper):
-//   1. signatures of R         sig_tiles_kernel          (Section 3.1)
-//   2. build H_sign on R       build_kernel              (Figure 2, formula 3)
-//   3. probe with S            probe_kernel: S signatures, table walk,
-//                              byte-exact verification, warp-aggregated
-//                              output compaction         (Figure 2, formulas 4-5)
-//
-// Work decomposition of the signature stage.  A key is cut into tiles of
-// kTile bytes counted from the key's first byte.  A warp owns a contiguous
-// range of keys and walks their tiles in rounds of 32 (one tile per lane).
-// Each lane computes the signature of its tile relative to the tile start
-// (Horner over 16-byte chunks, see gf16.cuh), then shifts it to the tile's
-// position in the key by multiplying with x^(k * symbol offset) through
-// log / antilog tables.  Tiles of the same key sit in consecutive lanes; a
-// segmented XOR reduction gathers them in the key's first lane, and a key
-// that continues into the next round carries its partial signature.  Every
-// key's signature is thus written by exactly one lane, with no atomics and no
-// zero-initialisation.
-//
-// Alignment.  Keys start at any byte.  A lane reads the 16-byte aligned
-// chunks that cover its tile and, for an odd start, funnel-shifts the stream
-// by one byte so that symbols sit on 16-bit boundaries.  The remaining even
-// offset lo inside the first chunk only moves every symbol up by lo/2 slots;
-// it is undone by the same x^(k * offset) multiply (offset - lo/2).
+//   1. signatures of R      sig_kernel     (Section 3.1)
+//   2. build H_sign on R    build_kernel   (Figure 2, formula 3)
+//   3. probe with S         probe_kernel: S signatures, table walk, byte-exact
+//                           verification, output compaction (formulas 4-5)
+// The signature work of 1 and 3 is the warp tile walk of rounds.cuh: each
+// warp streams its share of the arena through shared memory with cp.async,
+// one round (32 tiles of kTile bytes) ahead of the arithmetic.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -36,206 +20,70 @@
 #include "gf16.cuh"
 
 namespace algsig {
-
-constexpr int kTile = 256;           // bytes of key per lane per round
-constexpr int kThreads = 256;        // threads per block of the signature / probe kernels
-constexpr int kKeysPerTask = 64;     // keys handed to a warp at a time
-constexpr uint64_t kEmpty = ~0ull;   // empty hash slot
-constexpr uint32_t kFlagTableFull = 1u;
-constexpr int kMaxDevices = 64;
-
 // GF(2^16) logarithm / antilogarithm of x, set up once per device.
 __device__ uint16_t g_log[65536];
 __device__ uint16_t g_alog[65536];
+}  // namespace algsig
 
-// ----------------------------------------------------------------------------
-// Device helpers
-// ----------------------------------------------------------------------------
+#include "rounds.cuh"
 
-__device__ __forceinline__ uint4 ldg16(const uint4* p) { return __ldg(p); }
+namespace algsig {
 
-__device__ __forceinline__ uint32_t lanemask_lt() {
-  uint32_t m;
-  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
+constexpr int kWarpsPerBlock = 16;
+constexpr int kThreads = 32 * kWarpsPerBlock;   // one block per SM
+constexpr int kPairBuf = 64;                    // verified pairs staged per warp before one atomic
+constexpr uint64_t kEmpty = ~0ull;              // empty hash slot
+constexpr uint32_t kFlagTableFull = 1u;
+constexpr int kMaxDevices = 64;
 
-// x^(e) * a for a 16-bit residue a and 0 <= e < 65535, through log/antilog.
-__device__ __forceinline__ uint32_t gf_shift(uint32_t a, uint32_t e) {
-  if (a == 0) return 0;
-  uint32_t t = (uint32_t)__ldg(&g_log[a]) + e;
-  if (t >= kOrder) t -= kOrder;
-  return __ldg(&g_alog[t]);
-}
-
-// Signature contribution of one tile: the bytes [tstart, tstart + tlen) of
-// the arena, which hold the key's symbols from symbol offset sym_off on.
-// Returns sum_k x^(k*sym_off) * sum_i p_(sym_off+i) x^(k*i), packed.
-__device__ __forceinline__ uint64_t tile_sig(const uint8_t* __restrict__ arena, uint64_t tstart, uint32_t tlen,
-                                             uint64_t sym_off, const uint32_t* __restrict__ redl) {
-  if (tlen == 0) return 0;
-  const uint32_t a = (uint32_t)(tstart & 15u);
-  const uint32_t odd = a & 1u;
-  const int lo = (int)(a - odd);              // even start inside the first realigned chunk
-  const int end = lo + (int)tlen;             // realigned end position
-  const int C = (end + 15) >> 4;              // realigned chunks
-  const uint4* base = reinterpret_cast<const uint4*>(arena + (tstart - a));
-  const uint32_t sh = odd * 8u;
-  uint32_t a1 = 0, a2 = 0, a3 = 0, a4 = 0;
-  uint32_t nxt0 = 0;                          // first word of the aligned chunk after the current one
-  if (odd && (end & 15) == 0) nxt0 = ldg16(base + C).x;
-  int c = C - 1;
-  if (c >= 1) {                               // last chunk: clear bytes past the tile end
-    const uint4 w = ldg16(base + c);
-    const int e = end - 16 * c;
-    uint32_t v0 = __funnelshift_r(w.x, w.y, sh) & byte_range_mask(0, e, 0);
-    uint32_t v1 = __funnelshift_r(w.y, w.z, sh) & byte_range_mask(0, e, 1);
-    uint32_t v2 = __funnelshift_r(w.z, w.w, sh) & byte_range_mask(0, e, 2);
-    uint32_t v3 = __funnelshift_r(w.w, nxt0, sh) & byte_range_mask(0, e, 3);
-    horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, redl);
-    nxt0 = w.x;
-    --c;
-  }
-  for (; c >= 1; --c) {                       // whole chunks
-    const uint4 w = ldg16(base + c);
-    const uint32_t v0 = __funnelshift_r(w.x, w.y, sh);
-    const uint32_t v1 = __funnelshift_r(w.y, w.z, sh);
-    const uint32_t v2 = __funnelshift_r(w.z, w.w, sh);
-    const uint32_t v3 = __funnelshift_r(w.w, nxt0, sh);
-    horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, redl);
-    nxt0 = w.x;
-  }
-  {                                           // first chunk: clear bytes before the tile start
-    const uint4 w = ldg16(base);
-    const int e = end < 16 ? end : 16;
-    uint32_t v0 = __funnelshift_r(w.x, w.y, sh) & byte_range_mask(lo, e, 0);
-    uint32_t v1 = __funnelshift_r(w.y, w.z, sh) & byte_range_mask(lo, e, 1);
-    uint32_t v2 = __funnelshift_r(w.z, w.w, sh) & byte_range_mask(lo, e, 2);
-    uint32_t v3 = __funnelshift_r(w.w, nxt0, sh) & byte_range_mask(lo, e, 3);
-    horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, redl);
-  }
-  // a_k = sum over slots t of q_t x^(k t), slot t = symbol (sym_off + t - lo/2) of the key.
-  const uint32_t eb = (uint32_t)((sym_off % kOrder + kOrder - (uint32_t)(lo >> 1)) % kOrder);
-  uint32_t e2 = eb * 2u; if (e2 >= kOrder) e2 -= kOrder;
-  uint32_t e3 = e2 + eb; if (e3 >= kOrder) e3 -= kOrder;
-  uint32_t e4 = e2 * 2u; if (e4 >= kOrder) e4 -= kOrder;
-  const uint64_t s1 = gf_shift(a1, eb), s2 = gf_shift(a2, e2), s3 = gf_shift(a3, e3), s4 = gf_shift(a4, e4);
-  return s1 | (s2 << 16) | (s3 << 32) | (s4 << 48);
-}
-
-// One round of the tile walk of a warp.  State (kc, tc, carry) is warp-uniform.
-// On return, lanes with `complete` hold the finished signature of key `key`
-// (whose arena start / length are `kstart` / `klen`); the state is advanced.
-struct RoundOut {
-  bool complete;
-  uint64_t key, sig, kstart, klen;
-};
-
-__device__ __forceinline__ RoundOut sig_round(const uint8_t* __restrict__ arena, const uint64_t* __restrict__ off,
-                                              uint64_t& kc, uint64_t k_end, uint64_t& tc, uint64_t& carry,
-                                              const uint32_t* __restrict__ redl) {
-  const uint32_t FULL = 0xFFFFFFFFu;
-  const int lane = threadIdx.x & 31;
-  const uint64_t kl = kc + (uint64_t)lane;
-  uint64_t sl = 0, ll = 0;
-  uint32_t rc = 0;                                 // tiles of key-lane left, clamped to 33
-  if (kl < k_end) {
-    sl = off[kl];
-    ll = off[kl + 1] - sl;
-    uint64_t nt = ll == 0 ? 1 : (ll + kTile - 1) / kTile;
-    if (lane == 0) nt -= tc;
-    rc = nt > 33 ? 33u : (uint32_t)nt;
-  }
-  uint32_t cum = rc;                               // inclusive scan over lanes
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint32_t t = __shfl_up_sync(FULL, cum, d);
-    if (lane >= d) cum += t;
-  }
-  const uint32_t total = __shfl_sync(FULL, cum, 31);
-  int q = 0;                                       // key-lane of slot `lane`: first q with cum[q] > lane
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) {
-    const uint32_t cv = __shfl_sync(FULL, cum, q + d - 1);
-    if (cv <= (uint32_t)lane) q += d;
-  }
-  const bool active = (uint32_t)lane < total;
-  const uint32_t cq = __shfl_sync(FULL, cum, q);
-  const uint32_t rq = __shfl_sync(FULL, rc, q);
-  const uint64_t sq = __shfl_sync(FULL, sl, q);
-  const uint64_t lq = __shfl_sync(FULL, ll, q);
-  const uint32_t slot0 = cq - rq;                  // first slot of key-lane q in this round
-  const uint64_t tile = (uint64_t)((uint32_t)lane - slot0) + (q == 0 ? tc : 0);
-  uint64_t contrib = 0;
-  if (active) {
-    const uint64_t toff = tile * (uint64_t)kTile;
-    const uint64_t rest = lq > toff ? lq - toff : 0;
-    const uint32_t tlen = rest < (uint64_t)kTile ? (uint32_t)rest : (uint32_t)kTile;
-    contrib = tile_sig(arena, sq + toff, tlen, toff >> 1, redl);
-  }
-  // segmented XOR towards the first lane of each key group
-  const int g = active ? q : 32 + lane;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint64_t o = __shfl_down_sync(FULL, contrib, d);
-    const int og = __shfl_down_sync(FULL, g, d);
-    if (lane + d < 32 && og == g) contrib ^= o;
-  }
-  const bool head = active && (uint32_t)lane == slot0;
-  if (head && q == 0) contrib ^= carry;
-  RoundOut r;
-  r.complete = head && (slot0 + rq <= 32u);
-  r.key = kc + (uint64_t)q;
-  r.sig = contrib;
-  r.kstart = sq;
-  r.klen = lq;
-  // advance the walk
-  if (total <= 32u) {
-    const uint64_t loaded = k_end - kc < 32 ? k_end - kc : 32;
-    kc += loaded;
-    tc = 0;
-    carry = 0;
-  } else {
-    const int q31 = __shfl_sync(FULL, q, 31);
-    const uint32_t s31 = __shfl_sync(FULL, slot0, 31);
-    const uint32_t c31 = __shfl_sync(FULL, cq, 31);
-    const uint64_t part = __shfl_sync(FULL, contrib, (int)s31);
-    if (c31 == 32u) {                              // key of slot 31 ends exactly at the round end
-      kc += (uint64_t)q31 + 1;
-      tc = 0;
-      carry = 0;
-    } else {
-      tc = (q31 == 0 ? tc : 0) + (uint64_t)(32u - s31);
-      kc += (uint64_t)q31;
-      carry = part;
-    }
-  }
-  return r;
-}
+// shared memory: reduction tables | their scratch | per-warp double buffers | per-warp pair buffers
+constexpr size_t kSmemTables = (size_t)kRedBytes + 512 * 4;
+constexpr size_t kSmemBufs = (size_t)kWarpsPerBlock * 2 * kBufBytes;
+constexpr size_t kSmemSig = kSmemTables + kSmemBufs;
+constexpr size_t kSmemProbe = kSmemSig + (size_t)kWarpsPerBlock * kPairBuf * 8;
 
 // ----------------------------------------------------------------------------
 // Signature kernel
 // ----------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kThreads) sig_tiles_kernel(const uint8_t* __restrict__ arena,
-                                                             const uint64_t* __restrict__ off, uint64_t n,
-                                                             uint64_t* __restrict__ sig_out) {
-  extern __shared__ uint32_t smem[];
-  init_red_tables(smem, smem + kRedWords);
+__global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restrict__ arena,
+                                                          const uint64_t* __restrict__ off, uint64_t n,
+                                                          uint64_t* __restrict__ sig_out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  init_red_tables(red, red + kRedWords);
   const int lane = threadIdx.x & 31;
-  const uint32_t* redl = smem + lane;
-  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const uint64_t ntasks = (n + kKeysPerTask - 1) / kKeysPerTask;
-  for (uint64_t task = warp; task < ntasks; task += nwarps) {
-    uint64_t kc = task * kKeysPerTask;
-    const uint64_t k_end = kc + kKeysPerTask < n ? kc + kKeysPerTask : n;
-    uint64_t tc = 0, carry = 0;
-    while (kc < k_end) {
-      const RoundOut r = sig_round(arena, off, kc, k_end, tc, carry, redl);
-      if (r.complete) sig_out[r.key] = r.sig;
-    }
+  const int wib = threadIdx.x >> 5;
+  const uint32_t* redl = red + lane;
+  uint8_t* bufs = smem + kSmemTables + (size_t)wib * 2 * kBufBytes;
+  const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
+  uint64_t k_lo, k_hi;
+  warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
+  // rounds r and r+1 are in flight before round r is computed
+  Plan cur = plan_round(plan_load(off, k_lo, k_hi), k_lo, k_hi, 0);
+  issue_span(bufs, arena, cur);
+  Plan nxt = plan_round(plan_load(off, cur.kc_next, k_hi), cur.kc_next, k_hi, cur.tc_next);
+  issue_span(bufs + kBufBytes, arena, nxt);
+  uint64_t carry = 0;
+  for (int r = 0; cur.valid; ++r) {
+    const PlanLoad ahead = plan_load(off, nxt.kc_next, k_hi);
+    cp_async_wait_prev();
+    __syncwarp();
+    uint8_t* buf = bufs + (r & 1) * kBufBytes;
+    uint32_t a1, a2, a3, a4;
+    tile_accumulate(buf, cur.span_lo, cur, redl, a1, a2, a3, a4);
+    const TileVals tv = tile_logs(cur, a1, a2, a3, a4);
+    __syncwarp();                                   // buf is free: refill it with round r+2
+    const Plan nn = plan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
+    issue_span(buf, arena, nn);
+    bool complete;
+    const uint64_t s = combine_round(cur, tv, carry, complete);
+    if (complete) sig_out[cur.kc + (uint64_t)cur.q] = s;
+    cur = nxt;
+    nxt = nn;
   }
+  cp_async_wait_all();
 }
 
 // ----------------------------------------------------------------------------
@@ -286,99 +134,137 @@ struct ProbeParams {
   unsigned long long* count;
 };
 
-// the `need` (1..8) bytes starting at p, little-endian in the low bytes; reads
-// only aligned 8-byte words that hold at least one of them
-__device__ __forceinline__ uint64_t ld_bytes8(const uint8_t* p, uint32_t need) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(p);
-  const uint64_t* q = reinterpret_cast<const uint64_t*>(a & ~(uintptr_t)7);
-  const uint32_t o = (uint32_t)(a & 7u);
-  uint64_t v = __ldg(q) >> (8 * o);
-  if (o != 0 && o + need > 8) v |= __ldg(q + 1) << (64 - 8 * o);
-  return v;
-}
-
-__device__ bool bytes_equal(const uint8_t* r, const uint8_t* s, uint64_t len) {
-  uint64_t i = 0;
-  for (; i + 8 <= len; i += 8)
-    if (ld_bytes8(r + i, 8) != ld_bytes8(s + i, 8)) return false;
-  const uint32_t rest = (uint32_t)(len - i);
-  if (rest == 0) return true;
-  const uint64_t mk = (1ull << (8 * rest)) - 1ull;
-  return ((ld_bytes8(r + i, rest) ^ ld_bytes8(s + i, rest)) & mk) == 0;
-}
-
-// Walk the table for the keys whose lanes have `live` set; emit verified pairs.
-// Called by the whole warp.
-__device__ __forceinline__ void probe_keys(bool live, uint64_t srow, uint64_t sig, uint64_t sstart, uint64_t slen,
-                                           const ProbeParams& P) {
-  const uint32_t FULL = 0xFFFFFFFFu;
+// Byte equality of two keys of length len, by the whole warp: lane l compares
+// bytes [8l, 8l+8) of each 256-byte step.  r and s are generic addresses
+// (global or shared); only aligned 8-byte words holding a key byte are read.
+__device__ __forceinline__ bool warp_equal(const uint8_t* r, const uint8_t* s, uint64_t len) {
   const int lane = threadIdx.x & 31;
-  uint64_t b = 0, steps = 0;
-  uint32_t fp = 0, sid = 0;
-  if (live) {
-    if (P.sigS_out) P.sigS_out[srow] = sig;
-    const uint64_t h = sig_hash(sig, slen);
-    b = h & P.mask;
-    fp = (uint32_t)(h >> 32);
-    sid = P.idS ? P.idS[srow] : (uint32_t)srow;
+  const uintptr_t ra = reinterpret_cast<uintptr_t>(r), sa = reinterpret_cast<uintptr_t>(s);
+  const uint32_t ro = (uint32_t)(ra & 7u), so = (uint32_t)(sa & 7u);
+  const uint64_t* rw = reinterpret_cast<const uint64_t*>(ra - ro);
+  const uint64_t* sw = reinterpret_cast<const uint64_t*>(sa - so);
+  const uint64_t rend = ro + len, send = so + len;
+  for (uint64_t b = 0; b < len; b += 256) {
+    const uint64_t wi = (b >> 3) + (uint64_t)lane;
+    const uint64_t r0 = 8 * wi < rend ? rw[wi] : 0;
+    const uint64_t s0 = 8 * wi < send ? sw[wi] : 0;
+    uint64_t r1 = __shfl_down_sync(kFull, r0, 1);
+    uint64_t s1 = __shfl_down_sync(kFull, s0, 1);
+    if (lane == 31) {
+      r1 = 8 * (wi + 1) < rend ? rw[wi + 1] : 0;
+      s1 = 8 * (wi + 1) < send ? sw[wi + 1] : 0;
+    }
+    const uint64_t rv = ro ? (r0 >> (8 * ro)) | (r1 << (64 - 8 * ro)) : r0;
+    const uint64_t sv = so ? (s0 >> (8 * so)) | (s1 << (64 - 8 * so)) : s0;
+    const uint64_t pos = b + 8 * (uint64_t)lane;
+    const uint64_t nv = len > pos ? len - pos : 0;
+    const uint64_t mk = nv >= 8 ? ~0ull : ((1ull << (8 * nv)) - 1ull);
+    if (!__all_sync(kFull, ((rv ^ sv) & mk) == 0)) return false;
   }
-  while (__any_sync(FULL, live)) {
-    bool hit = false;
-    uint32_t rid = 0;
+  return true;
+}
+
+// append the staged pairs of this warp to the output (one atomic per flush)
+__device__ __forceinline__ void flush_pairs(uint64_t* stage, uint32_t np, const ProbeParams& P) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(P.count, (unsigned long long)np);
+  base = __shfl_sync(kFull, base, 0);
+  __syncwarp();
+  for (uint32_t i = (uint32_t)lane; i < np; i += 32) {
+    const unsigned long long idx = base + i;
+    if (idx < P.cap) reinterpret_cast<uint64_t*>(P.pairs)[idx] = stage[i];
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kThreads, 1) probe_kernel(ProbeParams P) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  init_red_tables(red, red + kRedWords);
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  const uint32_t* redl = red + lane;
+  uint8_t* bufs = smem + kSmemTables + (size_t)wib * 2 * kBufBytes;
+  uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kSmemSig) + (size_t)wib * kPairBuf;
+  uint32_t np = 0;                                   // staged pairs (warp-uniform)
+  const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
+  uint64_t k_lo, k_hi;
+  warp_key_range(P.offS, P.n, warp, nwarps, &k_lo, &k_hi);
+  Plan cur = plan_round(plan_load(P.offS, k_lo, k_hi), k_lo, k_hi, 0);
+  issue_span(bufs, P.arenaS, cur);
+  Plan nxt = plan_round(plan_load(P.offS, cur.kc_next, k_hi), cur.kc_next, k_hi, cur.tc_next);
+  issue_span(bufs + kBufBytes, P.arenaS, nxt);
+  uint64_t carry = 0;
+  for (int r = 0; cur.valid; ++r) {
+    const PlanLoad ahead = plan_load(P.offS, nxt.kc_next, k_hi);
+    cp_async_wait_prev();
+    __syncwarp();
+    uint8_t* buf = bufs + (r & 1) * kBufBytes;
+    uint32_t a1, a2, a3, a4;
+    tile_accumulate(buf, cur.span_lo, cur, redl, a1, a2, a3, a4);
+    const TileVals tv = tile_logs(cur, a1, a2, a3, a4);
+    __syncwarp();
+    const Plan nn = plan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
+    issue_span(buf, P.arenaS, nn);
+    bool live;
+    const uint64_t sig = combine_round(cur, tv, carry, live);
+    // table walk of the keys finished in this round (their first lanes)
+    const uint64_t srow = cur.kc + (uint64_t)cur.q;
+    uint64_t b = 0, steps = 0;
+    uint32_t fp = 0;
     if (live) {
-      const uint64_t v = __ldg(P.slots + b);
-      if (v == kEmpty) {
-        live = false;
-      } else {
-        if ((uint32_t)(v >> 32) == fp) {
-          const uint32_t row = (uint32_t)v;
-          if (__ldg(P.sigR + row) == sig) {
-            const uint64_t rs = __ldg(P.offR + row);
-            const uint64_t rl = __ldg(P.offR + row + 1) - rs;
-            if (rl == slen && bytes_equal(P.arenaR + rs, P.arenaS + sstart, slen)) {
-              hit = true;
-              rid = P.idR ? __ldg(P.idR + row) : row;
+      if (P.sigS_out) P.sigS_out[srow] = sig;
+      const uint64_t h = sig_hash(sig, cur.klen);
+      b = h & P.mask;
+      fp = (uint32_t)(h >> 32);
+    }
+    while (__any_sync(kFull, live)) {
+      bool cand = false;
+      uint32_t row = 0;
+      if (live) {
+        const uint64_t v = __ldg(P.slots + b);
+        if (v == kEmpty) {
+          live = false;
+        } else {
+          if ((uint32_t)(v >> 32) == fp) {
+            row = (uint32_t)v;
+            if (__ldg(P.sigR + row) == sig) {
+              const uint64_t rs = __ldg(P.offR + row);
+              cand = __ldg(P.offR + row + 1) - rs == cur.klen;
             }
           }
-        }
-        b = (b + 1) & P.mask;
-        if (++steps > P.mask) live = false;
-      }
-    }
-    const uint32_t hm = __ballot_sync(FULL, hit);
-    if (hm) {
-      const int leader = __ffs(hm) - 1;
-      unsigned long long base = 0;
-      if (lane == leader) base = atomicAdd(P.count, (unsigned long long)__popc(hm));
-      base = __shfl_sync(FULL, base, leader);
-      if (hit) {
-        const unsigned long long idx = base + (unsigned long long)__popc(hm & lanemask_lt());
-        if (idx < P.cap) {
-          const uint64_t pr = (uint64_t)rid | ((uint64_t)sid << 32);
-          reinterpret_cast<uint64_t*>(P.pairs)[idx] = pr;
+          b = (b + 1) & P.mask;
+          if (++steps > P.mask) live = false;
         }
       }
+      uint32_t cm = __ballot_sync(kFull, cand);
+      while (cm) {                                   // verify candidates one by one, whole warp
+        const int j = __ffs(cm) - 1;
+        cm &= cm - 1;
+        const uint32_t rj = __shfl_sync(kFull, row, j);
+        const uint64_t len = __shfl_sync(kFull, cur.klen, j);
+        const uint64_t sj = __shfl_sync(kFull, cur.kstart, j);
+        const uint64_t srj = __shfl_sync(kFull, srow, j);
+        if (warp_equal(P.arenaR + __ldg(P.offR + rj), P.arenaS + sj, len)) {
+          if (lane == 0) {
+            const uint32_t rid = P.idR ? __ldg(P.idR + rj) : rj;
+            const uint32_t sid = P.idS ? __ldg(P.idS + srj) : (uint32_t)srj;
+            stage[np] = (uint64_t)rid | ((uint64_t)sid << 32);
+          }
+          if (++np == (uint32_t)kPairBuf) {
+            flush_pairs(stage, np, P);
+            np = 0;
+          }
+        }
+      }
     }
+    cur = nxt;
+    nxt = nn;
   }
-}
-
-__global__ void __launch_bounds__(kThreads) probe_kernel(ProbeParams P) {
-  extern __shared__ uint32_t smem[];
-  init_red_tables(smem, smem + kRedWords);
-  const int lane = threadIdx.x & 31;
-  const uint32_t* redl = smem + lane;
-  const uint64_t warp = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-  const uint64_t ntasks = (P.n + kKeysPerTask - 1) / kKeysPerTask;
-  for (uint64_t task = warp; task < ntasks; task += nwarps) {
-    uint64_t kc = task * kKeysPerTask;
-    const uint64_t k_end = kc + kKeysPerTask < P.n ? kc + kKeysPerTask : P.n;
-    uint64_t tc = 0, carry = 0;
-    while (kc < k_end) {
-      const RoundOut r = sig_round(P.arenaS, P.offS, kc, k_end, tc, carry, redl);
-      probe_keys(r.complete, r.key, r.sig, r.kstart, r.klen, P);
-    }
-  }
+  cp_async_wait_all();
+  if (np) flush_pairs(stage, np, P);
 }
 
 // ----------------------------------------------------------------------------
@@ -404,15 +290,13 @@ static as_status cuda_fail(cudaError_t e, const char* where) {
 struct DeviceState {
   bool ready = false;
   int sms = 0;
-  int sig_blocks_per_sm = 0;
-  int probe_blocks_per_sm = 0;
 };
 
 static std::mutex g_dev_mu;
 static DeviceState g_dev[kMaxDevices];
-constexpr size_t kSigSmem = (size_t)kRedBytes + 512 * 4;
 
-// GF tables by repeated multiplication by x (host), copied to the device once.
+// GF tables by repeated multiplication by x (host), copied to the device once;
+// kernel attributes set once per device.
 static as_status ensure_device(DeviceState** out) {
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
@@ -434,33 +318,24 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaMemcpyToSymbol(g_alog, h_alog, sizeof(h_alog))) != cudaSuccess) return cuda_fail(e, "table setup");
     if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return cuda_fail(e, "device query");
-    if ((e = cudaFuncSetAttribute(sig_tiles_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSigSmem)) !=
+    if ((e = cudaFuncSetAttribute(sig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
-    if ((e = cudaFuncSetAttribute(probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSigSmem)) !=
+    if ((e = cudaFuncSetAttribute(probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemProbe)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.sig_blocks_per_sm, sig_tiles_kernel, kThreads,
-                                                           kSigSmem)) != cudaSuccess)
-      return cuda_fail(e, "occupancy query");
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.probe_blocks_per_sm, probe_kernel, kThreads,
-                                                           kSigSmem)) != cudaSuccess)
-      return cuda_fail(e, "occupancy query");
-    if (d.sig_blocks_per_sm < 1) d.sig_blocks_per_sm = 1;
-    if (d.probe_blocks_per_sm < 1) d.probe_blocks_per_sm = 1;
     d.ready = true;
   }
   *out = &d;
   return AS_OK;
 }
 
-static uint64_t task_blocks(uint64_t n, int per_sm, int sms) {
-  const uint64_t ntasks = (n + kKeysPerTask - 1) / kKeysPerTask;
-  const uint64_t warps_per_block = kThreads / 32;
-  uint64_t want = (ntasks + warps_per_block - 1) / warps_per_block;
-  const uint64_t full = (uint64_t)per_sm * (uint64_t)sms;
-  if (want > full) want = full;
-  return want < 1 ? 1 : want;
+// persistent grid: one block per SM, fewer for small inputs (>= ~64 keys per warp)
+static unsigned walk_blocks(uint64_t n, int sms) {
+  const uint64_t per_block = 64ull * kWarpsPerBlock;
+  uint64_t want = (n + per_block - 1) / per_block;
+  if (want > (uint64_t)sms) want = (uint64_t)sms;
+  return (unsigned)(want < 1 ? 1 : want);
 }
 
 static bool misaligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
@@ -488,8 +363,7 @@ static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t 
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
   if (n == 0) return AS_OK;
-  const uint64_t blocks = task_blocks(n, d->sig_blocks_per_sm, d->sms);
-  sig_tiles_kernel<<<(unsigned)blocks, kThreads, kSigSmem, s>>>(arena, off, n, out);
+  sig_kernel<<<walk_blocks(n, d->sms), kThreads, kSmemSig, s>>>(arena, off, n, out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "signature kernel launch");
   return AS_OK;
@@ -619,8 +493,7 @@ as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64
     P.pairs = d_pairs;
     P.cap = cap_pairs;
     P.count = reinterpret_cast<unsigned long long*>(d_count);
-    const uint64_t blocks = task_blocks(n, d->probe_blocks_per_sm, d->sms);
-    probe_kernel<<<(unsigned)blocks, kThreads, kSigSmem, s>>>(P);
+    probe_kernel<<<walk_blocks(n, d->sms), kThreads, kSmemProbe, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "probe kernel launch");
   }
   if (h_count) {

@@ -89,6 +89,60 @@ __device__ __forceinline__ void horner_chunk(uint32_t v0, uint32_t v1, uint32_t 
   a4 = red32(u, redl);
 }
 
+// ---------------------------------------------------------------------------
+// Same step with explicit 32-bit shared-memory addressing of the reduction
+// tables.  Word (b * 32 + lane) of the table at byte offset `tab` holds the
+// bits-16..23 entry for byte b; the bits-24..31 table follows 32 KB later.
+// `lane4` = 4 * lane.  The byte address of entry b is (b << 7) | lane4, which
+// comes out of one shift and one LOP3.
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t lds32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared.u32 %0, [%1];" : "=r"(v) : "r"(addr));
+  return v;
+}
+
+__device__ __forceinline__ uint32_t lop3_and_or(uint32_t a, uint32_t mask, uint32_t o) {
+  // (a & mask) | o
+  uint32_t r;
+  asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(r) : "r"(a), "r"(mask), "r"(o));
+  return r;
+}
+
+__device__ __forceinline__ uint32_t red32s(uint32_t u, uint32_t tab_lane) {
+  const uint32_t i2 = lop3_and_or(u >> 9, 0x7F80u, tab_lane);
+  const uint32_t i3 = lop3_and_or(u >> 17, 0x7F80u, tab_lane + 32768u);
+  return u ^ lds32(i2) ^ lds32(i3);
+}
+
+__device__ __forceinline__ uint32_t red24s(uint32_t u, uint32_t tab_lane) {
+  return u ^ lds32(lop3_and_or(u >> 9, 0x7F80u, tab_lane));
+}
+
+// tab_lane = shared byte address of the tables + 4 * lane
+__device__ __forceinline__ void horner_chunk_s(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
+                                               uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& a4,
+                                               uint32_t tab_lane) {
+  const uint32_t l0 = v0 & 0xFFFFu, h0 = v0 >> 16;
+  const uint32_t l1 = v1 & 0xFFFFu, h1 = v1 >> 16;
+  const uint32_t l2 = v2 & 0xFFFFu, h2 = v2 >> 16;
+  const uint32_t l3 = v3 & 0xFFFFu, h3 = v3 >> 16;
+  uint32_t u;
+  u = (a1 << 8) ^ l0 ^ (h0 << 1) ^ (l1 << 2) ^ (h1 << 3) ^ (l2 << 4) ^ (h2 << 5) ^ (l3 << 6) ^ (h3 << 7);
+  a1 = red24s(u, tab_lane);
+  u = (a2 << 16) ^ l0 ^ (h0 << 2) ^ (l1 << 4) ^ (h1 << 6) ^ (l2 << 8) ^ (h2 << 10) ^ (l3 << 12) ^ (h3 << 14);
+  a2 = red32s(u, tab_lane);
+  u = (a3 << 12) ^ l2 ^ (h2 << 3) ^ (l3 << 6) ^ (h3 << 9);
+  a3 = red32s(u, tab_lane);
+  u = (a3 << 12) ^ l0 ^ (h0 << 3) ^ (l1 << 6) ^ (h1 << 9);
+  a3 = red32s(u, tab_lane);
+  u = (a4 << 16) ^ l2 ^ (h2 << 4) ^ (l3 << 8) ^ (h3 << 12);
+  a4 = red32s(u, tab_lane);
+  u = (a4 << 16) ^ l0 ^ (h0 << 4) ^ (l1 << 8) ^ (h1 << 12);
+  a4 = red32s(u, tab_lane);
+}
+
 // Mask of bytes [b0, b1) of a 16-byte chunk, for its 32-bit word j.
 __device__ __forceinline__ uint32_t byte_range_mask(int b0, int b1, int j) {
   int lo = b0 - 4 * j, hi = b1 - 4 * j;

@@ -1,0 +1,371 @@
+// rounds.cuh -- the warp-level tile walk shared by the signature and probe
+// kernels.
+//
+// Geometry.  A key starting at arena byte ks is read on the 16-byte chunk grid
+// of the arena.  If ks is odd, the byte stream is funnel-shifted by one byte
+// so that the key's symbols sit on 16-bit boundaries ("realigned" stream);
+// the key then starts at the even offset lo = (ks & 15) - (ks & 1) of its
+// first realigned chunk.  A tile is 8 realigned chunks (kTile = 128 bytes) of
+// that grid: tile j of a key covers realigned chunks [8j, 8j+8) (the first
+// tile starts at lo, the last ends with the key), so interior tiles read
+// exactly 8 aligned chunks.  An empty key has one empty tile.
+//
+// Rounds.  A warp owns a contiguous, byte-balanced range of keys and walks
+// their tiles in rounds of 32 (one per lane).  The 32 tiles of a round are
+// consecutive in the arena, so a round reads one contiguous span; cp.async
+// copies it to shared memory two rounds ahead of the arithmetic.  In shared
+// memory a 16-byte pad follows every 128 bytes of span, so that the lanes of
+// one key, whose tiles are 128 bytes apart, read different banks.
+//
+// Combination.  Each lane computes its tile's signature relative to the
+// tile's first slot (Horner over 16-byte chunks, gf16.cuh) and moves it to the
+// tile's place in the key by a multiplication with x^(k (64 j - lo/2)) through
+// log/antilog tables; the log lookups are issued before the next round is
+// planned, which hides their latency.  Tiles of one key sit in consecutive
+// lanes: a segmented XOR gathers them in the key's first lane of the round,
+// and a key that continues into the next round carries its partial signature
+// there.  Every key's signature is finished by exactly one lane.
+#pragma once
+#include <cstdint>
+
+#include "gf16.cuh"
+
+namespace algsig {
+
+constexpr int kTile = 128;                        // bytes of realigned key per tile (8 chunks)
+constexpr int kSpanChunks = 32 * (kTile / 16) + 2;   // chunks of a round's span, worst case
+constexpr int kBufBytes = 16 * (kSpanChunks + (kSpanChunks + 7) / 8) + 16;   // with one pad per 8 chunks
+constexpr uint32_t kFull = 0xFFFFFFFFu;
+
+// g_log / g_alog: GF(2^16) logarithm / antilogarithm of x, defined (and set
+// up once per device) by the translation unit that includes this header.
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// ---------------------------------------------------------------------------
+// async copy of a round's span into shared memory
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// shared-memory byte offset of span offset `rel` (16-byte pad after every 128 bytes)
+__device__ __forceinline__ uint32_t padded(uint32_t rel) { return rel + ((rel >> 7) << 4); }
+
+// ---------------------------------------------------------------------------
+// warp range: keys [k_lo, k_hi) whose starts fall in this warp's share of the
+// arena bytes (byte-balanced static partition)
+// ---------------------------------------------------------------------------
+
+// first i in [0, n] with off[i] >= target (off non-decreasing); 32-ary search by one warp
+__device__ __forceinline__ uint64_t warp_lower_bound(const uint64_t* __restrict__ off, uint64_t n, uint64_t target) {
+  const int lane = threadIdx.x & 31;
+  uint64_t lo = 0, hi = n;          // answer in [lo, hi]
+  while (hi - lo > 32) {
+    const uint64_t step = (hi - lo + 31) / 32;
+    const uint64_t idx = lo + (uint64_t)lane * step;
+    const bool below = idx <= hi && off[idx] < target;
+    const int cnt = __popc(__ballot_sync(kFull, below));   // lanes 0..cnt-1 are below
+    if (cnt == 0) { hi = lo; break; }
+    const uint64_t nlo = lo + (uint64_t)(cnt - 1) * step;
+    const uint64_t nhi = lo + (uint64_t)cnt * step;
+    lo = nlo + 1;                    // off[nlo] < target
+    hi = nhi < hi ? nhi : hi;
+    if (lo > hi) lo = hi;
+  }
+  const uint64_t idx = lo + (uint64_t)lane;
+  const bool below = idx < hi && off[idx] < target;
+  const int cnt = __popc(__ballot_sync(kFull, below));
+  return lo + (uint64_t)cnt;
+}
+
+__device__ __forceinline__ void warp_key_range(const uint64_t* __restrict__ off, uint64_t n, uint64_t warp,
+                                               uint64_t nwarps, uint64_t* k_lo, uint64_t* k_hi) {
+  const uint64_t base = off[0], total = off[n] - off[0];
+  auto cut = [&](uint64_t w) -> uint64_t {
+    if (w == 0) return 0;
+    if (w >= nwarps) return n;
+    const unsigned __int128 t = (unsigned __int128)total * w / nwarps;
+    return warp_lower_bound(off, n, base + (uint64_t)t);
+  };
+  *k_lo = cut(warp);
+  *k_hi = cut(warp + 1);
+  if (warp + 1 >= nwarps) *k_hi = n;
+}
+
+// ---------------------------------------------------------------------------
+// round plan
+// ---------------------------------------------------------------------------
+
+struct Plan {
+  // per lane: the tile
+  uint64_t cbase;    // arena address of the tile's first aligned chunk
+  uint64_t kstart;   // start / length of the tile's key
+  uint64_t klen;
+  uint32_t tile;     // tile index inside the key (< 2^32 tiles per key)
+  uint32_t nc;       // realigned chunks in the tile (0 for an empty key)
+  uint32_t lo;       // even start offset of the key in its first realigned chunk
+  uint32_t odd;      // key starts at an odd byte
+  uint32_t tail_e;   // valid bytes of the tile's last chunk (16 unless it ends the key)
+  bool last;         // tile ends its key
+  bool active;
+  int q;             // key-lane index: key = kc + q
+  uint32_t slot0;    // first slot of key q in this round
+  uint32_t rq;       // tiles of key q in this round and after (clamped to 33)
+  // warp-uniform
+  bool valid;
+  uint64_t kc;               // first key of the round
+  uint64_t kc_next, tc_next; // walk state after the round
+  uint64_t span_lo, span_hi; // 16-byte aligned arena span of the round
+  bool carries;              // key of slot 31 continues into the next round
+  uint32_t s31;              // its first slot
+};
+
+// Offsets a plan needs: off[kc + lane] and off[kc + lane + 1], loaded ahead of time.
+struct PlanLoad {
+  uint64_t o0, o1;
+};
+
+__device__ __forceinline__ PlanLoad plan_load(const uint64_t* __restrict__ off, uint64_t kc, uint64_t k_end) {
+  const uint64_t kl = kc + (uint64_t)(threadIdx.x & 31);
+  PlanLoad l;
+  l.o0 = 0;
+  l.o1 = 0;
+  if (kl < k_end) {
+    l.o0 = off[kl];
+    l.o1 = off[kl + 1];
+  }
+  return l;
+}
+
+__device__ __forceinline__ uint64_t key_tiles(uint64_t ks, uint64_t len) {
+  if (len == 0) return 1;
+  const uint64_t lo = (ks & 15u) & ~1ull;
+  return (lo + len + kTile - 1) / kTile;
+}
+
+__device__ __forceinline__ Plan plan_round(const PlanLoad& L, uint64_t kc, uint64_t k_end, uint64_t tc) {
+  Plan p;
+  p.valid = kc < k_end;
+  p.kc = kc;
+  const int lane = threadIdx.x & 31;
+  const uint64_t kl = kc + (uint64_t)lane;
+  const bool have = p.valid && kl < k_end;
+  const uint64_t sl = L.o0;
+  const uint64_t ll = L.o1 - L.o0;
+  uint32_t rc = 0;
+  if (have) {
+    uint64_t nt = key_tiles(sl, ll);
+    if (lane == 0) nt -= tc;
+    rc = nt > 33 ? 33u : (uint32_t)nt;
+  }
+  uint32_t cum = rc;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t t = __shfl_up_sync(kFull, cum, d);
+    if (lane >= d) cum += t;
+  }
+  const uint32_t total = __shfl_sync(kFull, cum, 31);
+  int q = 0;                        // first q with cum[q] > lane
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const uint32_t cv = __shfl_sync(kFull, cum, q + d - 1);
+    if (cv <= (uint32_t)lane) q += d;
+  }
+  p.active = p.valid && (uint32_t)lane < total;
+  const uint32_t cq = __shfl_sync(kFull, cum, q);
+  p.rq = __shfl_sync(kFull, rc, q);
+  p.kstart = __shfl_sync(kFull, sl, q);
+  p.klen = __shfl_sync(kFull, ll, q);
+  p.q = q;
+  p.slot0 = cq - p.rq;
+  const uint64_t tile = (uint64_t)((uint32_t)lane - p.slot0) + (q == 0 ? tc : 0);
+  p.tile = (uint32_t)tile;
+  // tile geometry
+  const uint32_t a = (uint32_t)(p.kstart & 15u);
+  p.odd = a & 1u;
+  p.lo = a - p.odd;
+  const uint64_t kbase = p.kstart - a;
+  const uint64_t C = p.klen == 0 ? 0 : (p.lo + p.klen + 15) >> 4;       // realigned chunks of the key
+  const uint64_t c0 = tile * (kTile / 16);
+  const uint64_t rest = C > c0 ? C - c0 : 0;
+  p.nc = p.active ? (uint32_t)(rest < (uint64_t)(kTile / 16) ? rest : (uint64_t)(kTile / 16)) : 0u;
+  p.last = c0 + (kTile / 16) >= C;
+  p.tail_e = p.last && p.klen ? (uint32_t)(p.lo + p.klen - 16 * (C - 1)) : 16u;
+  p.cbase = kbase + 16 * c0;
+  // tile's arena byte range: [max(ks, cbase + odd), min(ks + len, cbase + 128 + odd))
+  const uint64_t tb = c0 == 0 ? p.kstart : p.cbase + p.odd;
+  const uint64_t te_full = p.cbase + kTile + p.odd;
+  const uint64_t te = p.kstart + p.klen < te_full ? p.kstart + p.klen : te_full;
+  // span of the round: first active tile's first chunk .. last active tile's end
+  const int last = (int)(total < 32u ? total : 32u) - 1;
+  const uint64_t sa = __shfl_sync(kFull, tb, 0);
+  const uint64_t sb = __shfl_sync(kFull, p.active ? te : tb, last < 0 ? 0 : last);
+  p.span_lo = sa & ~15ull;
+  p.span_hi = (sb + 15) & ~15ull;
+  // advance the walk
+  if (!p.valid) {
+    p.kc_next = kc; p.tc_next = tc; p.carries = false; p.s31 = 0;
+  } else if (total <= 32u) {
+    const uint64_t loaded = k_end - kc < 32 ? k_end - kc : 32;
+    p.kc_next = kc + loaded;
+    p.tc_next = 0;
+    p.carries = false;
+    p.s31 = 0;
+  } else {
+    const int q31 = __shfl_sync(kFull, q, 31);
+    const uint32_t s31 = __shfl_sync(kFull, p.slot0, 31);
+    const uint32_t c31 = __shfl_sync(kFull, cq, 31);
+    if (c31 == 32u) {
+      p.kc_next = kc + (uint64_t)q31 + 1;
+      p.tc_next = 0;
+      p.carries = false;
+      p.s31 = 0;
+    } else {
+      p.kc_next = kc + (uint64_t)q31;
+      p.tc_next = (q31 == 0 ? tc : 0) + (uint64_t)(32u - s31);
+      p.carries = true;
+      p.s31 = s31;
+    }
+  }
+  return p;
+}
+
+// copy the round's span into `buf` (padded layout), one commit group per call
+__device__ __forceinline__ void issue_span(uint8_t* buf, const uint8_t* __restrict__ arena, const Plan& p) {
+  if (p.valid) {
+    const int lane = threadIdx.x & 31;
+    const uint32_t nchunks = (uint32_t)((p.span_hi - p.span_lo) >> 4);
+    const uint8_t* src = arena + p.span_lo;
+    for (uint32_t i = (uint32_t)lane; i < nchunks; i += 32) cp_async16(buf + 16 * (i + (i >> 3)), src + 16 * i);
+  }
+  cp_async_commit();
+}
+
+// ---------------------------------------------------------------------------
+// signature of one tile from the shared-memory copy of its span
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ uint4 chunk_at(const uint8_t* buf, uint32_t rel) {
+  return *reinterpret_cast<const uint4*>(buf + padded(rel));
+}
+
+// keep bytes [b0, 16) of a chunk given as two 64-bit halves
+__device__ __forceinline__ void keep_from(uint32_t b0, uint64_t& lo64, uint64_t& hi64) {
+  lo64 = b0 >= 8 ? 0ull : (~0ull << (8 * b0));
+  hi64 = b0 <= 8 ? ~0ull : (~0ull << (8 * (b0 - 8)));
+}
+// keep bytes [0, e) of a chunk, 1 <= e <= 16
+__device__ __forceinline__ void keep_below(uint32_t e, uint64_t& lo64, uint64_t& hi64) {
+  lo64 = e >= 8 ? ~0ull : ((1ull << (8 * e)) - 1ull);
+  hi64 = e >= 16 ? ~0ull : (e <= 8 ? 0ull : ((1ull << (8 * (e - 8))) - 1ull));
+}
+
+// Unreduced-free tile signature: a_k = sum over the tile's slots t of q_t x^(k t)
+// (slot 0 = first byte pair of the tile's first realigned chunk), reduced to 16 bits.
+__device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t span_lo, const Plan& p,
+                                                const uint32_t* __restrict__ redl, uint32_t& a1, uint32_t& a2,
+                                                uint32_t& a3, uint32_t& a4) {
+  a1 = a2 = a3 = a4 = 0;
+  if (p.nc == 0) return;
+  const uint32_t rel0 = (uint32_t)(p.cbase - span_lo);
+  const uint32_t sh = p.odd * 8u;
+  // head / tail masks of the first / last chunk
+  uint64_t hl = ~0ull, hh = ~0ull, tl = ~0ull, th = ~0ull;
+  if (p.tile == 0) keep_from(p.lo, hl, hh);
+  if (p.last) keep_below(p.tail_e, tl, th);
+  int c = (int)p.nc - 1;
+  // the odd realignment of the tile's last chunk reads the first word of the next chunk
+  uint32_t nxt0 = 0;
+  if (p.odd && (!p.last || p.tail_e == 16)) nxt0 = chunk_at(buf, rel0 + 16u * (uint32_t)(c + 1)).x;
+  {
+    const uint4 w = chunk_at(buf, rel0 + 16u * (uint32_t)c);
+    uint64_t ml = tl, mh = th;
+    if (c == 0) { ml &= hl; mh &= hh; }
+    const uint32_t v0 = __funnelshift_r(w.x, w.y, sh) & (uint32_t)ml;
+    const uint32_t v1 = __funnelshift_r(w.y, w.z, sh) & (uint32_t)(ml >> 32);
+    const uint32_t v2 = __funnelshift_r(w.z, w.w, sh) & (uint32_t)mh;
+    const uint32_t v3 = __funnelshift_r(w.w, nxt0, sh) & (uint32_t)(mh >> 32);
+    horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, redl);
+    nxt0 = w.x;
+  }
+  for (--c; c >= 1; --c) {
+    const uint4 w = chunk_at(buf, rel0 + 16u * (uint32_t)c);
+    horner_chunk(__funnelshift_r(w.x, w.y, sh), __funnelshift_r(w.y, w.z, sh), __funnelshift_r(w.z, w.w, sh),
+                 __funnelshift_r(w.w, nxt0, sh), a1, a2, a3, a4, redl);
+    nxt0 = w.x;
+  }
+  if (c == 0) {
+    const uint4 w = chunk_at(buf, rel0);
+    const uint32_t v0 = __funnelshift_r(w.x, w.y, sh) & (uint32_t)hl;
+    const uint32_t v1 = __funnelshift_r(w.y, w.z, sh) & (uint32_t)(hl >> 32);
+    const uint32_t v2 = __funnelshift_r(w.z, w.w, sh) & (uint32_t)hh;
+    const uint32_t v3 = __funnelshift_r(w.w, nxt0, sh) & (uint32_t)(hh >> 32);
+    horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, redl);
+  }
+}
+
+// exponent of the tile's shift: 64*tile - lo/2 (mod 65535), for component 1
+__device__ __forceinline__ uint32_t tile_exponent(const Plan& p) {
+  const uint32_t t = (p.tile % kOrder) * (uint32_t)(kTile / 2) % kOrder;
+  const uint32_t h = p.lo >> 1;
+  return t >= h ? t - h : t + kOrder - h;
+}
+
+// Combine: multiply the lanes' tile values by x^(k e) (log/antilog), gather
+// each key's tiles in its first lane, apply / produce the carry.
+struct TileVals {
+  uint32_t l1, l2, l3, l4;   // logs of a_k + k*e (mod 65535), or 0xFFFFFFFF for a_k = 0
+};
+
+__device__ __forceinline__ TileVals tile_logs(const Plan& p, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4) {
+  const uint32_t e1 = tile_exponent(p);
+  uint32_t e2 = e1 * 2u; if (e2 >= kOrder) e2 -= kOrder;
+  uint32_t e3 = e2 + e1; if (e3 >= kOrder) e3 -= kOrder;
+  uint32_t e4 = e2 * 2u; if (e4 >= kOrder) e4 -= kOrder;
+  TileVals v;
+  v.l1 = a1 ? (uint32_t)__ldg(&g_log[a1]) + e1 : 0xFFFFFFFFu;
+  v.l2 = a2 ? (uint32_t)__ldg(&g_log[a2]) + e2 : 0xFFFFFFFFu;
+  v.l3 = a3 ? (uint32_t)__ldg(&g_log[a3]) + e3 : 0xFFFFFFFFu;
+  v.l4 = a4 ? (uint32_t)__ldg(&g_log[a4]) + e4 : 0xFFFFFFFFu;
+  return v;
+}
+
+__device__ __forceinline__ uint32_t alog_of(uint32_t l) {
+  if (l == 0xFFFFFFFFu) return 0;
+  if (l >= kOrder) l -= kOrder;
+  return __ldg(&g_alog[l]);
+}
+
+__device__ __forceinline__ uint64_t combine_round(const Plan& p, const TileVals& v, uint64_t& carry, bool& complete) {
+  const int lane = threadIdx.x & 31;
+  uint64_t contrib = 0;
+  if (p.active) {
+    contrib = (uint64_t)alog_of(v.l1) | ((uint64_t)alog_of(v.l2) << 16) | ((uint64_t)alog_of(v.l3) << 32) |
+              ((uint64_t)alog_of(v.l4) << 48);
+  }
+  const int g = p.active ? p.q : 32 + lane;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t o = __shfl_down_sync(kFull, contrib, d);
+    const int og = __shfl_down_sync(kFull, g, d);
+    if (lane + d < 32 && og == g) contrib ^= o;
+  }
+  const bool head = p.active && (uint32_t)lane == p.slot0;
+  if (head && p.q == 0) contrib ^= carry;
+  complete = head && (p.slot0 + p.rq <= 32u);
+  const uint64_t part = __shfl_sync(kFull, contrib, (int)p.s31);
+  carry = p.carries ? part : 0;
+  return contrib;
+}
+
+}  // namespace algsig
