@@ -239,8 +239,9 @@ def run_gpu(args):
     dR = ag.DeviceRelation(hR[0].cuda(), hR[1].cuda(), hR[2].cuda())
     dS = ag.DeviceRelation(hS[0].cuda(), hS[1].cuda(), hS[2].cuda())
     lf = args.load_factor
-    ws = ag.alloc_ws(ag.join_ws_bytes(m, lf))
+    ws = ag.alloc_ws(ag.join_ws_bytes(m, n, lf))
     tb = ag.join_table_bytes(m, lf)
+    pws = ws[tb + 256:]
     cap = int(max(1024, wl.expected_pairs() * 1.25 + 1024))
     pairs = torch.empty(2 * cap, dtype=torch.int32, device="cuda")
     count = ws[tb:tb + 8].view(torch.int64)
@@ -254,7 +255,7 @@ def run_gpu(args):
         t = ag.join_build(dR, ws[:tb], lf, stream=stream)
         if evs:
             evs[1].record(stream)
-        ag.join_probe(t, dS, pairs, count, sync=False, stream=stream)
+        ag.join_probe(t, dS, pairs, count, ws=pws, sync=False, stream=stream)
         if evs:
             evs[2].record(stream)
 
@@ -288,6 +289,27 @@ def run_gpu(args):
     total_ms = max_over_ranks(total_ms)
     ms_per_step = total_ms / args.steps
     value = world * n / (ms_per_step * 1e-3)
+
+    # the same-GPU comparison join on full strings (plain and tagged variants)
+    bws = ag.alloc_ws(ag.baseline_ws_bytes(m, n, lf))
+    bcount = torch.zeros(1, dtype=torch.int64, device="cuda")
+    baseline = {}
+    for tagged in (False, True):
+        st, bcnt = ag.baseline_join_into(dR, dS, bws, pairs, bcount, lf, tagged=tagged, sync=True)
+        if bcnt != total_pairs:
+            raise SystemExit(f"comparison join found {bcnt} pairs, signature join {total_pairs}")
+        for _ in range(2):
+            ag.baseline_join_into(dR, dS, bws, pairs, bcount, lf, tagged=tagged, sync=False, stream=stream)
+        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        breps = max(3, min(10, args.steps))
+        b0.record(stream)
+        for _ in range(breps):
+            ag.baseline_join_into(dR, dS, bws, pairs, bcount, lf, tagged=tagged, sync=False, stream=stream)
+        b1.record(stream)
+        torch.cuda.synchronize()
+        bms = b0.elapsed_time(b1) / breps
+        baseline["tagged" if tagged else "plain"] = {"ms_per_join": bms, "tuples_per_s": n / (bms * 1e-3)}
+    del bws
 
     # signature kernel alone on S (key GB/s against HBM)
     sig_out = torch.empty(n, dtype=torch.int64, device="cuda")
@@ -368,10 +390,12 @@ def run_gpu(args):
         "probe_only_tuples_per_s": n / (probe_avg * 1e-3),
         "key_gbps": key_bytes / (ms_per_step * 1e-3) / 1e9,
         "sig_kernel": {"gbps": sig_gbps, "frac_hbm": sig_gbps / hbm, "ms": sig_ms},
+        "fullstring_gpu_join": baseline,
+        "speedup_vs_fullstring": {k: value / v["tuples_per_s"] for k, v in baseline.items()},
         "pairs": total_pairs,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-        "gpu_launches": 3 * args.steps,
+        "gpu_launches": 4 * args.steps,
         "roofline": {"bound": "hbm", "kernel": "probe_kernel", "achieved": achieved, "peak": hbm,
                      "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
                      "algorithmic_bytes": probe_alg},
@@ -385,7 +409,7 @@ def run_gpu(args):
     return 0
 
 
-KERNEL_REV = "v3"
+KERNEL_REV = "v7"
 
 
 def main():

@@ -91,9 +91,10 @@ as_status as_sig_compute(const uint8_t* d_arena, const uint64_t* d_off, uint64_t
 
 /*
  * Hash table of R's signatures (H_sign of Figure 2).  Open addressing with
- * linear probing over cap = next power of two >= m / load_factor slots; a slot
- * is one uint64 (32-bit fingerprint of the signature hash << 32 | R row), all
- * ones when empty.  R's signatures and key offsets are referenced by row.
+ * linear probing over cap = next power of two >= max(64, m / load_factor)
+ * slots of 16 bytes: the R row's 64-bit signature, then one uint64 holding
+ * (min(key length, 2^32 - 2) << 32) | R row, all ones when the slot is empty.
+ * The bucket of a key is a hash of its signature and length.
  * The struct is plain data and is filled by as_join_build; the caller keeps
  * it (host memory) and passes it to as_join_probe.  The device buffers it
  * points to belong to the caller: the workspace given to as_join_build and
@@ -101,7 +102,7 @@ as_status as_sig_compute(const uint8_t* d_arena, const uint64_t* d_off, uint64_t
  * table is used.
  */
 typedef struct as_table {
-    uint64_t* slots;          /* device: cap slots */
+    uint64_t* slots;          /* device: cap slots of two uint64 */
     const uint64_t* sigR;     /* device: m signatures of R */
     const uint8_t* arenaR;    /* device */
     const uint64_t* offR;     /* device: m+1 */
@@ -114,9 +115,9 @@ typedef struct as_table {
 } as_table;
 
 /*
- * Workspace of as_join_build: the slots, R's signatures and the flags, each
- * 256-byte aligned.  load_factor must be in (0, 1].  Returns 0 for invalid
- * arguments.
+ * Workspace of as_join_build: the slots (16 bytes each), R's signatures and
+ * the flags, each 256-byte aligned.  load_factor must be in (0, 1].  Returns 0
+ * for invalid arguments.
  */
 size_t as_join_table_bytes(uint64_t m, float load_factor);
 
@@ -134,16 +135,25 @@ as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, co
                         const uint32_t* d_idR, uint64_t m, const uint64_t* d_sigR, float load_factor,
                         as_table* out, as_stream stream);
 
+/* Workspace of as_join_probe when it must keep S's signatures itself
+ * (d_sigS_out == NULL): n signatures, 256-byte aligned. */
+size_t as_join_probe_ws_bytes(uint64_t n);
+
 /*
  * as_join_probe -- probe H_sign with every key of S and emit the verified
  * matches (Figure 2, "Probe(H_sign, S); output the matching tuples").
- * S's signatures are computed on the fly; a candidate is a slot whose
- * fingerprint, full signature and key length all match, and it is emitted
- * only if its bytes equal the S key's bytes.
+ * S's signatures are computed first (as by as_sig_compute); then every S key
+ * walks its bucket sequence until an empty slot; a slot is a candidate when
+ * its signature and key length equal the S key's, and a candidate is emitted
+ * only if the R key's bytes equal the S key's bytes.
  *   t              : table from as_join_build (host struct)
  *   d_arenaS, d_offS, d_idS, n : relation S
  *   d_sigS_out     : uint64[n] device buffer to receive S's signatures, or NULL
- *   d_pairs        : uint32[2*cap_pairs] device buffer for (r_id, s_id) pairs
+ *   d_ws, ws_bytes : device workspace of as_join_probe_ws_bytes(n) bytes,
+ *                    256-byte aligned; used (and required) only when
+ *                    d_sigS_out is NULL
+ *   d_pairs        : uint32[2*cap_pairs] device buffer for (r_id, s_id) pairs,
+ *                    8-byte aligned
  *   cap_pairs      : capacity of d_pairs in pairs; pairs beyond it are counted
  *                    but not written
  *   d_count        : device uint64 receiving the total pair count
@@ -151,14 +161,17 @@ as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, co
  *                    the count is copied here and the build's error flags are
  *                    checked: AS_ERR_CAPACITY if count > cap_pairs,
  *                    AS_ERR_TABLE_FULL if the build overflowed.
- * Errors: AS_ERR_INVALID, AS_ERR_CAPACITY, AS_ERR_TABLE_FULL, AS_ERR_CUDA.
+ * Errors: AS_ERR_INVALID, AS_ERR_NOMEM, AS_ERR_CAPACITY, AS_ERR_TABLE_FULL,
+ * AS_ERR_CUDA.
  */
 as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
-                        const uint32_t* d_idS, uint64_t n, uint64_t* d_sigS_out, uint32_t* d_pairs,
-                        uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream);
+                        const uint32_t* d_idS, uint64_t n, uint64_t* d_sigS_out, void* d_ws, size_t ws_bytes,
+                        uint32_t* d_pairs, uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count,
+                        as_stream stream);
 
-/* Workspace of as_join: the table workspace plus the pair counter. */
-size_t as_join_ws_bytes(uint64_t m, float load_factor);
+/* Workspace of as_join for |R| = m and |S| = n: the table workspace, the pair
+ * counter and the probe workspace. */
+size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor);
 
 /*
  * as_join -- the whole signature hash join T = Join(R, S) in one call:
@@ -171,6 +184,75 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
                   const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
                   float load_factor, void* d_ws, size_t ws_bytes, uint32_t* d_pairs, uint64_t cap_pairs,
                   uint64_t* d_count, uint64_t* h_count, as_stream stream);
+
+/*
+ * Batches of independent joins (many joins of uneven sizes and key lengths in
+ * one set of launches).  All joins' R relations are packed into one R
+ * relation (one arena, one offset array) and all S relations into one S
+ * relation; join j owns R rows [r_begin, r_end) and S rows [s_begin, s_end)
+ * (ranges in increasing order, not overlapping), its own hash table (sized by
+ * its own |R|) and its own output region: pairs [pair_offset, pair_offset +
+ * pair_cap) of d_pairs, with its pair count in d_counts[j].  Pair ids are
+ * the relations' ids if given, else row numbers relative to the join's first
+ * row.  Per join the result is exactly that of as_join on the join's rows.
+ */
+typedef struct as_join_desc {
+    uint64_t r_begin, r_end;
+    uint64_t s_begin, s_end;
+    uint64_t pair_offset;
+    uint64_t pair_cap;
+} as_join_desc;
+
+/* Prepared batch: device descriptors and workspace regions (plain data). */
+typedef struct as_batch {
+    void* descs;
+    uint64_t* slots;
+    uint64_t* sigR;
+    uint64_t* sigS;
+    uint32_t* flags;
+    uint64_t n_joins;
+    uint64_t slots_total;
+    uint64_t mR, nS;
+} as_batch;
+
+/* Workspace of a batch (0 for invalid descriptors or load factor). */
+size_t as_join_batch_ws_bytes(const as_join_desc* descs, int n_joins, uint64_t mR, uint64_t nS, float load_factor);
+
+/* Lay out the workspace and upload the descriptors (host array, copied; the
+ * stream is synchronised once).  The prepared batch can be run many times, and
+ * as_join_batch_run can be captured in a CUDA graph. */
+as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t mR, uint64_t nS, float load_factor,
+                                void* d_ws, size_t ws_bytes, as_batch* out, as_stream stream);
+
+/* Run a prepared batch: clear the tables and counters, signatures of all R
+ * keys, build of every join's table, signatures of all S keys, probe and
+ * verification of every S key against its join's table.  Asynchronous; a
+ * join's count may exceed its pair_cap (the excess pairs are not written). */
+as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR,
+                            const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint32_t* d_pairs,
+                            uint64_t* d_counts, as_stream stream);
+
+/* prepare + run */
+as_status as_join_batch(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t mR,
+                        const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t nS,
+                        const as_join_desc* descs, int n_joins, float load_factor, void* d_ws, size_t ws_bytes,
+                        uint32_t* d_pairs, uint64_t* d_counts, as_stream stream);
+
+/*
+ * Comparison join (not the paper's method): the simple hash join on full
+ * strings that the paper measures against (Section 2; Section 4.3 compares
+ * with a join that tests a.equal(b) on every bucket entry).  The bucket is a
+ * 64-bit hash of all key bytes; a slot holds the R row (tagged = 0), or the
+ * R row and a 32-bit tag of the key hash (tagged = 1, an honesty control that
+ * filters like a signature would).  Every visited slot costs a length check
+ * and, when the lengths agree (and the tag matches, if tagged), a full byte
+ * comparison.  Same output and errors as as_join.
+ */
+size_t as_baseline_ws_bytes(uint64_t m, uint64_t n, float load_factor);
+as_status as_baseline_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
+                           const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
+                           float load_factor, int tagged, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
+                           uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream);
 
 #ifdef __cplusplus
 }

@@ -31,7 +31,8 @@ AS_ERR_CUDA = 5
 AS_ERR_UNSUPPORTED = 6
 
 EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_join_table_bytes",
-           "as_join_build", "as_join_probe", "as_join_ws_bytes", "as_join")
+           "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_ws_bytes", "as_join",
+           "as_baseline_ws_bytes", "as_baseline_join")
 
 
 class AlgsigError(RuntimeError):
@@ -71,14 +72,20 @@ def load(path: str | None = None):
         lib.as_sig_compute.restype = S
         lib.as_join_table_bytes.argtypes = [U64, F]
         lib.as_join_table_bytes.restype = SZ
-        lib.as_join_ws_bytes.argtypes = [U64, F]
+        lib.as_join_ws_bytes.argtypes = [U64, U64, F]
         lib.as_join_ws_bytes.restype = SZ
+        lib.as_join_probe_ws_bytes.argtypes = [U64]
+        lib.as_join_probe_ws_bytes.restype = SZ
         lib.as_join_build.argtypes = [P, SZ, P, P, P, U64, P, F, ctypes.POINTER(Table), P]
         lib.as_join_build.restype = S
-        lib.as_join_probe.argtypes = [ctypes.POINTER(Table), P, P, P, U64, P, P, U64, P, P, P]
+        lib.as_join_probe.argtypes = [ctypes.POINTER(Table), P, P, P, U64, P, P, SZ, P, U64, P, P, P]
         lib.as_join_probe.restype = S
         lib.as_join.argtypes = [P, P, P, U64, P, P, P, U64, F, P, SZ, P, U64, P, P, P]
         lib.as_join.restype = S
+        lib.as_baseline_ws_bytes.argtypes = [U64, U64, F]
+        lib.as_baseline_ws_bytes.restype = SZ
+        lib.as_baseline_join.argtypes = [P, P, P, U64, P, P, P, U64, F, S, P, SZ, P, U64, P, P, P]
+        lib.as_baseline_join.restype = S
         if path is None:
             _lib = lib
         return lib
@@ -152,8 +159,12 @@ def join_table_bytes(m: int, load_factor: float = 0.5) -> int:
     return int(load().as_join_table_bytes(m, load_factor))
 
 
-def join_ws_bytes(m: int, load_factor: float = 0.5) -> int:
-    return int(load().as_join_ws_bytes(m, load_factor))
+def join_ws_bytes(m: int, n: int, load_factor: float = 0.5) -> int:
+    return int(load().as_join_ws_bytes(m, n, load_factor))
+
+
+def join_probe_ws_bytes(n: int) -> int:
+    return int(load().as_join_probe_ws_bytes(n))
 
 
 def alloc_ws(nbytes: int, device="cuda") -> torch.Tensor:
@@ -171,14 +182,17 @@ def join_build(R: DeviceRelation, ws: torch.Tensor, load_factor: float = 0.5, si
 
 
 def join_probe(t: Table, S: DeviceRelation, pairs: torch.Tensor, count: torch.Tensor,
-               sigS_out: torch.Tensor | None = None, sync: bool = True, stream=None) -> int | None:
-    """as_join_probe.  pairs: int32 tensor of 2*cap entries; count: int64 device scalar.
+               sigS_out: torch.Tensor | None = None, ws: torch.Tensor | None = None, sync: bool = True,
+               stream=None) -> int | None:
+    """as_join_probe.  pairs: int32 tensor of 2*cap entries; count: int64 device scalar;
+    ws: workspace of join_probe_ws_bytes(S.n) bytes when sigS_out is None.
     With sync=True returns the pair count (raises AlgsigError on capacity overflow)."""
     lib = load()
     cap = pairs.numel() // 2
     h = ctypes.c_uint64(0)
     _check(lib.as_join_probe(ctypes.byref(t), _ptr(S.arena), _ptr(S.off), _ptr(S.ids), S.n, _ptr(sigS_out),
-                             _ptr(pairs), cap, _ptr(count), ctypes.byref(h) if sync else None, _stream(stream)))
+                             _ptr(ws), 0 if ws is None else ws.numel(), _ptr(pairs), cap, _ptr(count),
+                             ctypes.byref(h) if sync else None, _stream(stream)))
     return int(h.value) if sync else None
 
 
@@ -201,7 +215,7 @@ def join(R: DeviceRelation, S: DeviceRelation, load_factor: float = 0.5, cap_pai
     pairs (uint32 bits) in unspecified order, retrying once with the exact
     size if the first guess of the capacity was too small."""
     dev = R.arena.device
-    ws = alloc_ws(join_ws_bytes(R.n, load_factor), dev)
+    ws = alloc_ws(join_ws_bytes(R.n, S.n, load_factor), dev)
     cap = cap_pairs if cap_pairs is not None else max(1024, S.n)
     count = torch.zeros(1, dtype=torch.int64, device=dev)
     while True:
@@ -210,3 +224,120 @@ def join(R: DeviceRelation, S: DeviceRelation, load_factor: float = 0.5, cap_pai
         if st == AS_OK:
             return pairs[:2 * cnt].view(-1, 2)
         cap = cnt
+
+
+def baseline_ws_bytes(m: int, n: int, load_factor: float = 0.5) -> int:
+    return int(load().as_baseline_ws_bytes(m, n, load_factor))
+
+
+def baseline_join_into(R: DeviceRelation, S: DeviceRelation, ws: torch.Tensor, pairs: torch.Tensor,
+                       count: torch.Tensor, load_factor: float = 0.5, tagged: bool = False, sync: bool = True,
+                       stream=None, allow_capacity: bool = False):
+    """as_baseline_join (the full-string comparison join) into caller buffers."""
+    lib = load()
+    cap = pairs.numel() // 2
+    h = ctypes.c_uint64(0)
+    st = lib.as_baseline_join(_ptr(R.arena), _ptr(R.off), _ptr(R.ids), R.n, _ptr(S.arena), _ptr(S.off),
+                              _ptr(S.ids), S.n, load_factor, 1 if tagged else 0, _ptr(ws), ws.numel(), _ptr(pairs),
+                              cap, _ptr(count), ctypes.byref(h) if sync else None, _stream(stream))
+    _check(st, allow=(AS_ERR_CAPACITY,) if allow_capacity else ())
+    return st, (int(h.value) if sync else None)
+
+
+def baseline_join(R: DeviceRelation, S: DeviceRelation, load_factor: float = 0.5, tagged: bool = False,
+                  cap_pairs: int | None = None, stream=None) -> torch.Tensor:
+    """The full-string comparison join; (cnt, 2) int32 tensor of (r_id, s_id) pairs."""
+    dev = R.arena.device
+    ws = alloc_ws(baseline_ws_bytes(R.n, S.n, load_factor), dev)
+    cap = cap_pairs if cap_pairs is not None else max(1024, S.n)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    while True:
+        pairs = torch.empty(2 * max(cap, 1), dtype=torch.int32, device=dev)
+        st, cnt = baseline_join_into(R, S, ws, pairs, count, load_factor, tagged, sync=True, stream=stream,
+                                     allow_capacity=True)
+        if st == AS_OK:
+            return pairs[:2 * cnt].view(-1, 2)
+        cap = cnt
+
+
+# ----------------------------------------------------------------------------- batches of joins
+
+class JoinDesc(ctypes.Structure):
+    """as_join_desc: join j's row ranges in the batch's R and S and its output region."""
+    _fields_ = [("r_begin", ctypes.c_uint64), ("r_end", ctypes.c_uint64), ("s_begin", ctypes.c_uint64),
+                ("s_end", ctypes.c_uint64), ("pair_offset", ctypes.c_uint64), ("pair_cap", ctypes.c_uint64)]
+
+
+class Batch(ctypes.Structure):
+    """as_batch: a prepared batch (device descriptors and workspace regions)."""
+    _fields_ = [("descs", ctypes.c_void_p), ("slots", ctypes.c_void_p), ("sigR", ctypes.c_void_p),
+                ("sigS", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("n_joins", ctypes.c_uint64),
+                ("slots_total", ctypes.c_uint64), ("mR", ctypes.c_uint64), ("nS", ctypes.c_uint64)]
+
+
+def _batch_lib():
+    lib = load()
+    if not getattr(lib, "_batch_ready", False):
+        P, U64, SZ, F, S = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_float, ctypes.c_int
+        D = ctypes.POINTER(JoinDesc)
+        lib.as_join_batch_ws_bytes.argtypes = [D, S, U64, U64, F]
+        lib.as_join_batch_ws_bytes.restype = SZ
+        lib.as_join_batch_prepare.argtypes = [D, S, U64, U64, F, P, SZ, ctypes.POINTER(Batch), P]
+        lib.as_join_batch_prepare.restype = S
+        lib.as_join_batch_run.argtypes = [ctypes.POINTER(Batch), P, P, P, P, P, P, P, P, P]
+        lib.as_join_batch_run.restype = S
+        lib._batch_ready = True
+    return lib
+
+
+def make_descs(ranges, pair_caps) -> ctypes.Array:
+    """ranges: iterable of (r_begin, r_end, s_begin, s_end); output regions laid out back to back."""
+    ranges = list(ranges)
+    arr = (JoinDesc * len(ranges))()
+    off = 0
+    for j, ((rb, re_, sb, se), cap) in enumerate(zip(ranges, pair_caps)):
+        arr[j] = JoinDesc(int(rb), int(re_), int(sb), int(se), off, int(cap))
+        off += int(cap)
+    return arr
+
+
+def total_pair_cap(descs) -> int:
+    return max((d.pair_offset + d.pair_cap for d in descs), default=0)
+
+
+def join_batch_ws_bytes(descs, mR: int, nS: int, load_factor: float = 0.5) -> int:
+    return int(_batch_lib().as_join_batch_ws_bytes(descs, len(descs), mR, nS, load_factor))
+
+
+def join_batch_prepare(descs, R: DeviceRelation, S: DeviceRelation, ws: torch.Tensor, load_factor: float = 0.5,
+                       stream=None) -> Batch:
+    b = Batch()
+    _check(_batch_lib().as_join_batch_prepare(descs, len(descs), R.n, S.n, load_factor, _ptr(ws), ws.numel(),
+                                              ctypes.byref(b), _stream(stream)))
+    return b
+
+
+def join_batch_run(b: Batch, R: DeviceRelation, S: DeviceRelation, pairs: torch.Tensor, counts: torch.Tensor,
+                   stream=None) -> None:
+    """Asynchronous (capturable in a CUDA graph)."""
+    _check(_batch_lib().as_join_batch_run(ctypes.byref(b), _ptr(R.arena), _ptr(R.off), _ptr(R.ids), _ptr(S.arena),
+                                          _ptr(S.off), _ptr(S.ids), _ptr(pairs), _ptr(counts), _stream(stream)))
+
+
+def join_batch(R: DeviceRelation, S: DeviceRelation, ranges, pair_caps, load_factor: float = 0.5):
+    """Run a batch once; returns a list of per-join (cnt, 2) int32 pair tensors (join-local ids
+    unless the relations carry ids).  Raises if a join overflows its pair_cap."""
+    descs = make_descs(ranges, pair_caps)
+    dev = R.arena.device
+    ws = alloc_ws(join_batch_ws_bytes(descs, R.n, S.n, load_factor), dev)
+    b = join_batch_prepare(descs, R, S, ws, load_factor)
+    pairs = torch.empty(2 * max(1, total_pair_cap(descs)), dtype=torch.int32, device=dev)
+    counts = torch.zeros(len(descs), dtype=torch.int64, device=dev)
+    join_batch_run(b, R, S, pairs, counts)
+    cnt = counts.cpu().tolist()
+    out = []
+    for d, c in zip(descs, cnt):
+        if c > d.pair_cap:
+            raise AlgsigError(AS_ERR_CAPACITY, f"join overflowed its pair capacity ({c} > {d.pair_cap})")
+        out.append(pairs[2 * d.pair_offset: 2 * (d.pair_offset + c)].view(-1, 2))
+    return out

@@ -3,11 +3,12 @@
 // Pipeline of one join T = Join(R, S) (Figure 2 of the paper):
 //   1. signatures of R      sig_kernel     (Section 3.1)
 //   2. build H_sign on R    build_kernel   (Figure 2, formula 3)
-//   3. probe with S         probe_kernel: S signatures, table walk, byte-exact
-//                           verification, output compaction (formulas 4-5)
+//   3. probe with S         sig_kernel on S, then verify_kernel: table walk,
+//                           byte-exact verification, output compaction
+//                           (formulas 4-5)
 // The signature work of 1 and 3 is the warp tile walk of rounds.cuh: each
 // warp streams its share of the arena through shared memory with cp.async,
-// one round (32 tiles of kTile bytes) ahead of the arithmetic.
+// two rounds (32 tiles of kTile bytes each) ahead of the arithmetic.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -15,6 +16,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <vector>
 
 #include "../../include/algsig.h"
 #include "gf16.cuh"
@@ -23,15 +25,20 @@ namespace algsig {
 // GF(2^16) logarithm / antilogarithm of x, set up once per device.
 __device__ uint16_t g_log[65536];
 __device__ uint16_t g_alog[65536];
+// constant-multiply tables of the tile combination (rounds.cuh), set up once per device
+__device__ uint16_t g_const[21 * 512];
 }  // namespace algsig
 
 #include "rounds.cuh"
+#include "baseline.cuh"
 
 namespace algsig {
 
-constexpr int kWarpsPerBlock = 16;
+#ifndef ALGSIG_WARPS
+#define ALGSIG_WARPS 8
+#endif
+constexpr int kWarpsPerBlock = ALGSIG_WARPS;
 constexpr int kThreads = 32 * kWarpsPerBlock;   // one block per SM
-constexpr int kPairBuf = 64;                    // verified pairs staged per warp before one atomic
 constexpr uint64_t kEmpty = ~0ull;              // empty hash slot
 constexpr uint32_t kFlagTableFull = 1u;
 constexpr int kMaxDevices = 64;
@@ -39,8 +46,8 @@ constexpr int kMaxDevices = 64;
 // shared memory: reduction tables | their scratch | per-warp double buffers | per-warp pair buffers
 constexpr size_t kSmemTables = (size_t)kRedBytes + 512 * 4;
 constexpr size_t kSmemBufs = (size_t)kWarpsPerBlock * 2 * kBufBytes;
-constexpr size_t kSmemSig = kSmemTables + kSmemBufs;
-constexpr size_t kSmemProbe = kSmemSig + (size_t)kWarpsPerBlock * kPairBuf * 8;
+constexpr size_t kSmemSig = kSmemTables + kConstBytes + kSmemBufs;
+static_assert(kConstEntries == 21 * 512, "constant table size");
 
 // ----------------------------------------------------------------------------
 // Signature kernel
@@ -51,11 +58,14 @@ __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restr
                                                           uint64_t* __restrict__ sig_out) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* red = reinterpret_cast<uint32_t*>(smem);
-  init_red_tables(red, red + kRedWords);
+  uint16_t* ctab = reinterpret_cast<uint16_t*>(smem + kSmemTables);
+  for (int i = threadIdx.x; i < kConstEntries / 2; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ctab)[i] = reinterpret_cast<const uint32_t*>(g_const)[i];
+  init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
   const int lane = threadIdx.x & 31;
   const int wib = threadIdx.x >> 5;
-  const uint32_t* redl = red + lane;
-  uint8_t* bufs = smem + kSmemTables + (size_t)wib * 2 * kBufBytes;
+  const RedCursor rc = red_cursor(red);
+  uint8_t* bufs = smem + kSmemTables + kConstBytes + (size_t)wib * 2 * kBufBytes;
   const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
   const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
   uint64_t k_lo, k_hi;
@@ -65,46 +75,384 @@ __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restr
   issue_span(bufs, arena, cur);
   Plan nxt = plan_round(plan_load(off, cur.kc_next, k_hi), cur.kc_next, k_hi, cur.tc_next);
   issue_span(bufs + kBufBytes, arena, nxt);
-  uint64_t carry = 0;
+  uint64_t carry = 0;                               // partial signature of the key continuing into `cur`
+  Pending pd;
+  pd.valid = false;
   for (int r = 0; cur.valid; ++r) {
     const PlanLoad ahead = plan_load(off, nxt.kc_next, k_hi);
     cp_async_wait_prev();
     __syncwarp();
     uint8_t* buf = bufs + (r & 1) * kBufBytes;
     uint32_t a1, a2, a3, a4;
-    tile_accumulate(buf, cur.span_lo, cur, redl, a1, a2, a3, a4);
-    const TileVals tv = tile_logs(cur, a1, a2, a3, a4);
+    tile_accumulate(buf, cur.span_lo, cur, rc, a1, a2, a3, a4);
+    if (pd.valid) pending_alogs(pd);                // its logs were loaded one round ago
     __syncwarp();                                   // buf is free: refill it with round r+2
     const Plan nn = plan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
     issue_span(buf, arena, nn);
-    bool complete;
-    const uint64_t s = combine_round(cur, tv, carry, complete);
-    if (complete) sig_out[cur.kc + (uint64_t)cur.q] = s;
+    const uint64_t V = scan_round(cur, cur.active ? pack4(a1, a2, a3, a4) : 0ull, ctab);
+    if (pd.valid) {                                 // finish the previous round's deferred product
+      const uint64_t P = pending_value(pd);
+      if (pd.complete) {
+        const uint64_t s = lo_correct(ctab, P, pd.lo, rc);
+        if (lane == 0) sig_out[pd.key] = s;
+      } else {
+        carry = P;
+      }
+      pd.valid = false;
+    }
+    const bool head = cur.active && (uint32_t)lane == cur.slot0;
+    const bool fresh = cur.q != 0 || cur.tc == 0;   // the key's first tile is in this round
+    if (head && fresh && cur.slot0 + cur.rq <= 32u) sig_out[cur.kc + (uint64_t)cur.q] = lo_correct(ctab, V, cur.lo, rc);
+    if (cur.tc > 0) {                               // group 0 continues a key: x^(k e) B, finished next round
+      pd.valid = true;
+      pd.key = cur.kc;
+      pd.carry = carry;
+      pd.lo = __shfl_sync(kFull, cur.lo, 0);
+      pd.complete = __shfl_sync(kFull, cur.rq, 0) <= 32u;
+      pending_logs(pd, __shfl_sync(kFull, V, 0), cur.tc);
+    }
+    const uint64_t vlast = __shfl_sync(kFull, V, (int)cur.s31);
+    if (cur.carries && !(cur.s31 == 0 && cur.tc > 0)) carry = vlast;   // a key that starts here continues
+    cur = nxt;
+    nxt = nn;
+  }
+  if (pd.valid) {                                   // the range's last key, if it was deferred
+    pending_alogs(pd);
+    const uint64_t s = lo_correct(ctab, pending_value(pd), pd.lo, rc);
+    if (lane == 0) sig_out[pd.key] = s;
+  }
+  cp_async_wait_all();
+}
+
+// ----------------------------------------------------------------------------
+// Hash table H_sign: open addressing, linear probing, 16-byte slots
+//   word 0: the R row's full 64-bit signature
+//   word 1: (min(len, 2^32 - 2) << 32) | R row; all ones when the slot is empty
+// A build thread claims word 1 with atomicCAS and then writes word 0; the
+// probe runs in a later kernel, so it never sees a half-written slot.
+// ----------------------------------------------------------------------------
+
+struct Slot {
+  uint64_t sig;
+  uint64_t key;   // (len32 << 32) | row
+};
+
+__device__ __forceinline__ uint32_t len32(uint64_t len) {
+  return len < 0xFFFFFFFEull ? (uint32_t)len : 0xFFFFFFFEu;
+}
+
+// A batch of independent joins over one concatenated R and one concatenated
+// S relation: join j owns R rows [r_begin, r_end), S rows [s_begin, s_end),
+// its own table (slots [slot_off, slot_off + mask + 1)) and its own output
+// region (pairs [pair_off, pair_off + pair_cap), counter counts[j]).
+struct BatchJoin {
+  uint64_t r_begin, r_end, s_begin, s_end;
+  uint64_t slot_off, mask;
+  uint64_t pair_off, pair_cap;
+};
+
+// join owning `row` (rows outside every join: -1); joins are ordered by row ranges
+template <bool S_SIDE>
+__device__ __forceinline__ int find_join(const BatchJoin* __restrict__ J, int nj, uint64_t row) {
+  int lo = 0, hi = nj - 1, ans = -1;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const uint64_t b = S_SIDE ? __ldg(&J[mid].s_begin) : __ldg(&J[mid].r_begin);
+    if (b <= row) { ans = mid; lo = mid + 1; } else { hi = mid - 1; }
+  }
+  if (ans >= 0) {
+    const uint64_t e = S_SIDE ? __ldg(&J[ans].s_end) : __ldg(&J[ans].r_end);
+    if (row >= e) ans = -1;
+  }
+  return ans;
+}
+
+// Insert R rows.  Single join: J == nullptr, the table is slots[0..mask].
+__global__ void build_kernel(Slot* __restrict__ slots, uint64_t mask, const uint64_t* __restrict__ sigR,
+                             const uint64_t* __restrict__ offR, uint64_t m, uint32_t* __restrict__ flags,
+                             const BatchJoin* __restrict__ J, int nj) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; row < m; row += stride) {
+    Slot* tab = slots;
+    uint64_t msk = mask;
+    if (J) {
+      const int j = find_join<false>(J, nj, row);
+      if (j < 0) continue;
+      tab = slots + __ldg(&J[j].slot_off);
+      msk = __ldg(&J[j].mask);
+    }
+    const uint64_t len = offR[row + 1] - offR[row];
+    const uint64_t sig = sigR[row];
+    const uint64_t word = ((uint64_t)len32(len) << 32) | row;
+    uint64_t b = sig_hash(sig, len) & msk;
+    bool placed = false;
+    for (uint64_t step = 0; step <= msk; ++step) {
+      const uint64_t cur = *(volatile const uint64_t*)(&tab[b].key);
+      if (cur == kEmpty) {
+        const unsigned long long prev =
+            atomicCAS(reinterpret_cast<unsigned long long*>(&tab[b].key), (unsigned long long)kEmpty,
+                      (unsigned long long)word);
+        if (prev == kEmpty) {
+          tab[b].sig = sig;
+          placed = true;
+          break;
+        }
+      }
+      b = (b + 1) & msk;
+    }
+    if (!placed) atomicOr(flags, kFlagTableFull);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Probe: table walk + byte-exact verification + output compaction.  The S
+// signatures come from sig_kernel; this kernel needs no large shared memory,
+// so it runs at full occupancy and hides the latency of its random accesses
+// (slots, R offsets, key bytes) behind many warps.
+// ----------------------------------------------------------------------------
+
+constexpr int kVThreads = 256;
+constexpr int kVWarps = kVThreads / 32;
+constexpr int kVStage = 64;     // verified pairs staged per warp before one atomic append
+
+struct VerifyParams {
+  const Slot* slots;
+  uint64_t mask;
+  const uint8_t* arenaR;
+  const uint64_t* offR;
+  const uint32_t* idR;
+  const uint8_t* arenaS;
+  const uint64_t* offS;
+  const uint32_t* idS;
+  const uint64_t* sigS;
+  uint64_t n;
+  uint32_t* pairs;
+  uint64_t cap;
+  unsigned long long* count;
+  // batch mode (J != nullptr): per-join tables, output regions and counters
+  const BatchJoin* J;
+  int nj;
+  unsigned long long* counts;
+};
+
+// aligned 8-byte word i of a key region whose first aligned word is `w`, or 0
+// if the word holds no key byte (region end `end` counted from w in bytes)
+__device__ __forceinline__ uint64_t word_or0(const uint64_t* w, uint64_t i, uint64_t end) {
+  return 8 * i < end ? __ldg(w + i) : 0ull;
+}
+
+__device__ __forceinline__ uint64_t funnel64(uint64_t lo, uint64_t hi, uint32_t o) {
+  return o ? (lo >> (8 * o)) | (hi << (64 - 8 * o)) : lo;
+}
+
+// Byte equality of two keys of length len by the whole warp: lane l compares
+// bytes [8l, 8l+8) and [8l+256, 8l+264) of each 512-byte step, with both
+// steps' loads in flight together.  Only aligned 8-byte words that hold a key
+// byte are read.
+__device__ __forceinline__ bool warp_equal(const uint8_t* r, const uint8_t* s, uint64_t len) {
+  const int lane = threadIdx.x & 31;
+  const uintptr_t ra = reinterpret_cast<uintptr_t>(r), sa = reinterpret_cast<uintptr_t>(s);
+  const uint32_t ro = (uint32_t)(ra & 7u), so = (uint32_t)(sa & 7u);
+  const uint64_t* rw = reinterpret_cast<const uint64_t*>(ra - ro);
+  const uint64_t* sw = reinterpret_cast<const uint64_t*>(sa - so);
+  const uint64_t rend = ro + len, send = so + len;
+  for (uint64_t b = 0; b < len; b += 512) {
+    const uint64_t wa = (b >> 3) + (uint64_t)lane, wb = wa + 32;
+    const uint64_t ra0 = word_or0(rw, wa, rend), rb0 = word_or0(rw, wb, rend);
+    const uint64_t sa0 = word_or0(sw, wa, send), sb0 = word_or0(sw, wb, send);
+    const uint64_t rtail = lane == 31 ? word_or0(rw, wb + 1, rend) : 0;
+    const uint64_t stail = lane == 31 ? word_or0(sw, wb + 1, send) : 0;
+    uint64_t ra1 = __shfl_down_sync(kFull, ra0, 1), sa1 = __shfl_down_sync(kFull, sa0, 1);
+    uint64_t rb1 = __shfl_down_sync(kFull, rb0, 1), sb1 = __shfl_down_sync(kFull, sb0, 1);
+    const uint64_t rnext = __shfl_sync(kFull, rb0, 0), snext = __shfl_sync(kFull, sb0, 0);
+    if (lane == 31) {
+      ra1 = rnext; sa1 = snext;
+      rb1 = rtail; sb1 = stail;
+    }
+    const uint64_t pa = b + 8 * (uint64_t)lane, pb = pa + 256;
+    const uint64_t na = len > pa ? len - pa : 0, nb = len > pb ? len - pb : 0;
+    const uint64_t ma = na >= 8 ? ~0ull : ((1ull << (8 * na)) - 1ull);
+    const uint64_t mb = nb >= 8 ? ~0ull : ((1ull << (8 * nb)) - 1ull);
+    const bool eq = ((funnel64(ra0, ra1, ro) ^ funnel64(sa0, sa1, so)) & ma) == 0 &&
+                    ((funnel64(rb0, rb1, ro) ^ funnel64(sb0, sb1, so)) & mb) == 0;
+    if (!__all_sync(kFull, eq)) return false;
+  }
+  return true;
+}
+
+__device__ __forceinline__ void flush_stage(const uint64_t* stage, uint32_t np, const VerifyParams& P) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(P.count, (unsigned long long)np);
+  base = __shfl_sync(kFull, base, 0);
+  for (uint32_t i = (uint32_t)lane; i < np; i += 32) {
+    const unsigned long long idx = base + i;
+    if (idx < P.cap) reinterpret_cast<uint64_t*>(P.pairs)[idx] = stage[i];
+  }
+  __syncwarp();
+}
+
+// flush for join j of a batch: its counter, region and capacity
+__device__ __forceinline__ void flush_stage_join(const uint64_t* stage, uint32_t np, const VerifyParams& P, int j) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long base = 0;
+  if (lane == 0) base = atomicAdd(P.counts + j, (unsigned long long)np);
+  base = __shfl_sync(kFull, base, 0);
+  const uint64_t off = __ldg(&P.J[j].pair_off), cap = __ldg(&P.J[j].pair_cap);
+  for (uint32_t i = (uint32_t)lane; i < np; i += 32) {
+    const unsigned long long idx = base + i;
+    if (idx < cap) reinterpret_cast<uint64_t*>(P.pairs)[off + idx] = stage[i];
+  }
+  __syncwarp();
+}
+
+__global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
+  __shared__ uint64_t stage_all[kVWarps][kVStage];
+  const int lane = threadIdx.x & 31;
+  uint64_t* stage = stage_all[threadIdx.x >> 5];
+  uint32_t np = 0;                                   // staged pairs (warp-uniform)
+  int sj = -1;                                       // batch: join of the staged pairs
+  const bool batch = P.J != nullptr;
+  const uint64_t ngroups = (P.n + 31) / 32;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kVWarps;
+  for (uint64_t grp = (uint64_t)blockIdx.x * kVWarps + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
+    const uint64_t i = grp * 32 + (uint64_t)lane;
+    bool live = i < P.n;
+    const Slot* slots = P.slots;
+    uint64_t mask = P.mask;
+    int jn = 0;                                      // batch: join of the lane's S row
+    if (batch && live) {
+      jn = find_join<true>(P.J, P.nj, i);
+      if (jn < 0) {
+        live = false;
+      } else {
+        slots = P.slots + __ldg(&P.J[jn].slot_off);
+        mask = __ldg(&P.J[jn].mask);
+      }
+    }
+    uint64_t sig = 0, start = 0, len = 0, b = 0, steps = 0;
+    uint32_t l32 = 0;
+    if (live) {
+      sig = __ldg(P.sigS + i);
+      start = __ldg(P.offS + i);
+      len = __ldg(P.offS + i + 1) - start;
+      b = sig_hash(sig, len) & mask;
+      l32 = len32(len);
+    }
+    while (__any_sync(kFull, live)) {
+      bool cand = false;
+      uint32_t row = 0;
+      if (live) {
+        const ulonglong2 v = __ldg(reinterpret_cast<const ulonglong2*>(slots + b));
+        if (v.y == kEmpty) {
+          live = false;
+        } else {
+          if (v.x == sig && (uint32_t)(v.y >> 32) == l32) {
+            cand = true;
+            row = (uint32_t)v.y;
+          }
+          b = (b + 1) & mask;
+          if (++steps > mask) live = false;
+        }
+      }
+      uint32_t cm = __ballot_sync(kFull, cand);
+      while (cm) {                                   // verify candidates one by one, whole warp
+        const int j = __ffs(cm) - 1;
+        cm &= cm - 1;
+        const uint32_t rj = __shfl_sync(kFull, row, j);
+        const uint64_t lj = __shfl_sync(kFull, len, j);
+        const uint64_t stj = __shfl_sync(kFull, start, j);
+        const uint64_t rs = __ldg(P.offR + rj);
+        const uint64_t rl = __ldg(P.offR + rj + 1) - rs;
+        if (rl == lj && warp_equal(P.arenaR + rs, P.arenaS + stj, lj)) {
+          const int jj = __shfl_sync(kFull, jn, j);
+          if (batch && np && jj != sj) {              // the stage holds one join's pairs
+            flush_stage_join(stage, np, P, sj);
+            np = 0;
+          }
+          sj = jj;
+          if (lane == 0) {
+            const uint64_t srow = grp * 32 + (uint64_t)j;
+            const uint32_t rid = P.idR ? __ldg(P.idR + rj) : (uint32_t)(rj - (batch ? __ldg(&P.J[jj].r_begin) : 0));
+            const uint32_t sid = P.idS ? __ldg(P.idS + srow) : (uint32_t)(srow - (batch ? __ldg(&P.J[jj].s_begin) : 0));
+            stage[np] = (uint64_t)rid | ((uint64_t)sid << 32);
+          }
+          __syncwarp();
+          if (++np == (uint32_t)kVStage) {
+            if (batch) flush_stage_join(stage, np, P, sj); else flush_stage(stage, np, P);
+            np = 0;
+          }
+        }
+      }
+    }
+  }
+  if (np) {
+    if (batch) flush_stage_join(stage, np, P, sj); else flush_stage(stage, np, P);
+  }
+}
+
+// ----------------------------------------------------------------------------
+// Comparison join on full strings (baseline.cuh): hash, build, probe
+// ----------------------------------------------------------------------------
+
+constexpr size_t kSmemBHash = (size_t)kWarpsPerBlock * 2 * kBBufBytes;
+
+__global__ void __launch_bounds__(kThreads, 1) bl_hash_kernel(const uint8_t* __restrict__ arena,
+                                                              const uint64_t* __restrict__ off, uint64_t n,
+                                                              uint64_t* __restrict__ hash_out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  const int lane = threadIdx.x & 31;
+  const int wib = threadIdx.x >> 5;
+  uint8_t* bufs = smem + (size_t)wib * 2 * kBBufBytes;
+  const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
+  uint64_t k_lo, k_hi;
+  warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
+  BPlan cur = bplan_round(plan_load(off, k_lo, k_hi), k_lo, k_hi, 0);
+  bissue_span(bufs, arena, cur);
+  BPlan nxt = bplan_round(plan_load(off, cur.kc_next, k_hi), cur.kc_next, k_hi, cur.tc_next);
+  bissue_span(bufs + kBBufBytes, arena, nxt);
+  uint64_t carry = 0;
+  for (int r = 0; cur.valid; ++r) {
+    const PlanLoad ahead = plan_load(off, nxt.kc_next, k_hi);
+    cp_async_wait_prev();
+    __syncwarp();
+    uint8_t* buf = bufs + (r & 1) * kBBufBytes;
+    uint64_t v = cur.active ? btile_hash(buf, cur) : 0ull;
+    __syncwarp();
+    const BPlan nn = bplan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
+    bissue_span(buf, arena, nn);
+    const int g = cur.active ? cur.q : 32 + lane;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t o = __shfl_down_sync(kFull, v, d);
+      const int og = __shfl_down_sync(kFull, g, d);
+      if (lane + d < 32 && og == g) v ^= o;
+    }
+    const bool head = cur.active && (uint32_t)lane == cur.slot0;
+    if (head && cur.q == 0) v ^= carry;
+    if (head && cur.slot0 + cur.rq <= 32u) hash_out[cur.kc + (uint64_t)cur.q] = key_hash_final(v, cur.klen);
+    const uint64_t part = __shfl_sync(kFull, v, (int)cur.s31);
+    carry = cur.carries ? part : 0ull;
     cur = nxt;
     nxt = nn;
   }
   cp_async_wait_all();
 }
 
-// ----------------------------------------------------------------------------
-// Build: insert every R row into the open-addressing table (linear probing)
-// ----------------------------------------------------------------------------
-
-__global__ void build_kernel(uint64_t* __restrict__ slots, uint64_t mask, const uint64_t* __restrict__ sigR,
-                             const uint64_t* __restrict__ offR, uint64_t m, uint32_t* __restrict__ flags) {
+__global__ void bl_build_kernel(uint64_t* __restrict__ slots, uint64_t mask, const uint64_t* __restrict__ hashR,
+                                uint64_t m, int tagged, uint32_t* __restrict__ flags) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; row < m; row += stride) {
-    const uint64_t len = offR[row + 1] - offR[row];
-    const uint64_t h = sig_hash(sigR[row], len);
-    const uint64_t word = (h & 0xFFFFFFFF00000000ull) | row;
+    const uint64_t h = hashR[row];
+    const uint64_t word = (tagged ? (h & 0xFFFFFFFF00000000ull) : 0ull) | row;
     uint64_t b = h & mask;
     bool placed = false;
     for (uint64_t step = 0; step <= mask; ++step) {
       const uint64_t cur = *(volatile const uint64_t*)(slots + b);
       if (cur == kEmpty) {
-        const unsigned long long prev =
-            atomicCAS(reinterpret_cast<unsigned long long*>(slots + b), (unsigned long long)kEmpty,
-                      (unsigned long long)word);
+        const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(slots + b),
+                                                  (unsigned long long)kEmpty, (unsigned long long)word);
         if (prev == kEmpty) { placed = true; break; }
       }
       b = (b + 1) & mask;
@@ -113,158 +461,87 @@ __global__ void build_kernel(uint64_t* __restrict__ slots, uint64_t mask, const 
   }
 }
 
-// ----------------------------------------------------------------------------
-// Probe: S signatures + table walk + verification + compaction
-// ----------------------------------------------------------------------------
-
-struct ProbeParams {
+struct BVerifyParams {
   const uint64_t* slots;
   uint64_t mask;
-  const uint64_t* sigR;
+  int tagged;
   const uint8_t* arenaR;
   const uint64_t* offR;
   const uint32_t* idR;
   const uint8_t* arenaS;
   const uint64_t* offS;
   const uint32_t* idS;
+  const uint64_t* hashS;
   uint64_t n;
-  uint64_t* sigS_out;
   uint32_t* pairs;
   uint64_t cap;
   unsigned long long* count;
 };
 
-// Byte equality of two keys of length len, by the whole warp: lane l compares
-// bytes [8l, 8l+8) of each 256-byte step.  r and s are generic addresses
-// (global or shared); only aligned 8-byte words holding a key byte are read.
-__device__ __forceinline__ bool warp_equal(const uint8_t* r, const uint8_t* s, uint64_t len) {
+__global__ void __launch_bounds__(kVThreads, 4) bl_verify_kernel(BVerifyParams P) {
+  __shared__ uint64_t stage_all[kVWarps][kVStage];
   const int lane = threadIdx.x & 31;
-  const uintptr_t ra = reinterpret_cast<uintptr_t>(r), sa = reinterpret_cast<uintptr_t>(s);
-  const uint32_t ro = (uint32_t)(ra & 7u), so = (uint32_t)(sa & 7u);
-  const uint64_t* rw = reinterpret_cast<const uint64_t*>(ra - ro);
-  const uint64_t* sw = reinterpret_cast<const uint64_t*>(sa - so);
-  const uint64_t rend = ro + len, send = so + len;
-  for (uint64_t b = 0; b < len; b += 256) {
-    const uint64_t wi = (b >> 3) + (uint64_t)lane;
-    const uint64_t r0 = 8 * wi < rend ? rw[wi] : 0;
-    const uint64_t s0 = 8 * wi < send ? sw[wi] : 0;
-    uint64_t r1 = __shfl_down_sync(kFull, r0, 1);
-    uint64_t s1 = __shfl_down_sync(kFull, s0, 1);
-    if (lane == 31) {
-      r1 = 8 * (wi + 1) < rend ? rw[wi + 1] : 0;
-      s1 = 8 * (wi + 1) < send ? sw[wi + 1] : 0;
-    }
-    const uint64_t rv = ro ? (r0 >> (8 * ro)) | (r1 << (64 - 8 * ro)) : r0;
-    const uint64_t sv = so ? (s0 >> (8 * so)) | (s1 << (64 - 8 * so)) : s0;
-    const uint64_t pos = b + 8 * (uint64_t)lane;
-    const uint64_t nv = len > pos ? len - pos : 0;
-    const uint64_t mk = nv >= 8 ? ~0ull : ((1ull << (8 * nv)) - 1ull);
-    if (!__all_sync(kFull, ((rv ^ sv) & mk) == 0)) return false;
-  }
-  return true;
-}
-
-// append the staged pairs of this warp to the output (one atomic per flush)
-__device__ __forceinline__ void flush_pairs(uint64_t* stage, uint32_t np, const ProbeParams& P) {
-  const int lane = threadIdx.x & 31;
-  unsigned long long base = 0;
-  if (lane == 0) base = atomicAdd(P.count, (unsigned long long)np);
-  base = __shfl_sync(kFull, base, 0);
-  __syncwarp();
-  for (uint32_t i = (uint32_t)lane; i < np; i += 32) {
-    const unsigned long long idx = base + i;
-    if (idx < P.cap) reinterpret_cast<uint64_t*>(P.pairs)[idx] = stage[i];
-  }
-  __syncwarp();
-}
-
-__global__ void __launch_bounds__(kThreads, 1) probe_kernel(ProbeParams P) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
-  init_red_tables(red, red + kRedWords);
-  const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const uint32_t* redl = red + lane;
-  uint8_t* bufs = smem + kSmemTables + (size_t)wib * 2 * kBufBytes;
-  uint64_t* stage = reinterpret_cast<uint64_t*>(smem + kSmemSig) + (size_t)wib * kPairBuf;
-  uint32_t np = 0;                                   // staged pairs (warp-uniform)
-  const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
-  const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
-  uint64_t k_lo, k_hi;
-  warp_key_range(P.offS, P.n, warp, nwarps, &k_lo, &k_hi);
-  Plan cur = plan_round(plan_load(P.offS, k_lo, k_hi), k_lo, k_hi, 0);
-  issue_span(bufs, P.arenaS, cur);
-  Plan nxt = plan_round(plan_load(P.offS, cur.kc_next, k_hi), cur.kc_next, k_hi, cur.tc_next);
-  issue_span(bufs + kBufBytes, P.arenaS, nxt);
-  uint64_t carry = 0;
-  for (int r = 0; cur.valid; ++r) {
-    const PlanLoad ahead = plan_load(P.offS, nxt.kc_next, k_hi);
-    cp_async_wait_prev();
-    __syncwarp();
-    uint8_t* buf = bufs + (r & 1) * kBufBytes;
-    uint32_t a1, a2, a3, a4;
-    tile_accumulate(buf, cur.span_lo, cur, redl, a1, a2, a3, a4);
-    const TileVals tv = tile_logs(cur, a1, a2, a3, a4);
-    __syncwarp();
-    const Plan nn = plan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
-    issue_span(buf, P.arenaS, nn);
-    bool live;
-    const uint64_t sig = combine_round(cur, tv, carry, live);
-    // table walk of the keys finished in this round (their first lanes)
-    const uint64_t srow = cur.kc + (uint64_t)cur.q;
-    uint64_t b = 0, steps = 0;
-    uint32_t fp = 0;
+  uint64_t* stage = stage_all[threadIdx.x >> 5];
+  VerifyParams VP;                                  // for flush_stage
+  VP.pairs = P.pairs;
+  VP.cap = P.cap;
+  VP.count = P.count;
+  uint32_t np = 0;
+  const uint64_t ngroups = (P.n + 31) / 32;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kVWarps;
+  for (uint64_t grp = (uint64_t)blockIdx.x * kVWarps + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
+    const uint64_t i = grp * 32 + (uint64_t)lane;
+    bool live = i < P.n;
+    uint64_t h = 0, start = 0, len = 0, b = 0, steps = 0;
     if (live) {
-      if (P.sigS_out) P.sigS_out[srow] = sig;
-      const uint64_t h = sig_hash(sig, cur.klen);
+      h = __ldg(P.hashS + i);
+      start = __ldg(P.offS + i);
+      len = __ldg(P.offS + i + 1) - start;
       b = h & P.mask;
-      fp = (uint32_t)(h >> 32);
     }
     while (__any_sync(kFull, live)) {
       bool cand = false;
       uint32_t row = 0;
+      uint64_t rs = 0;
       if (live) {
         const uint64_t v = __ldg(P.slots + b);
         if (v == kEmpty) {
           live = false;
         } else {
-          if ((uint32_t)(v >> 32) == fp) {
-            row = (uint32_t)v;
-            if (__ldg(P.sigR + row) == sig) {
-              const uint64_t rs = __ldg(P.offR + row);
-              cand = __ldg(P.offR + row + 1) - rs == cur.klen;
-            }
+          row = (uint32_t)v;
+          if (!P.tagged || (uint32_t)(v >> 32) == (uint32_t)(h >> 32)) {
+            rs = __ldg(P.offR + row);                 // every visited slot: length check
+            cand = __ldg(P.offR + row + 1) - rs == len;
           }
           b = (b + 1) & P.mask;
           if (++steps > P.mask) live = false;
         }
       }
       uint32_t cm = __ballot_sync(kFull, cand);
-      while (cm) {                                   // verify candidates one by one, whole warp
+      while (cm) {                                   // full byte comparison, whole warp
         const int j = __ffs(cm) - 1;
         cm &= cm - 1;
         const uint32_t rj = __shfl_sync(kFull, row, j);
-        const uint64_t len = __shfl_sync(kFull, cur.klen, j);
-        const uint64_t sj = __shfl_sync(kFull, cur.kstart, j);
-        const uint64_t srj = __shfl_sync(kFull, srow, j);
-        if (warp_equal(P.arenaR + __ldg(P.offR + rj), P.arenaS + sj, len)) {
+        const uint64_t lj = __shfl_sync(kFull, len, j);
+        const uint64_t sj = __shfl_sync(kFull, start, j);
+        const uint64_t rsj = __shfl_sync(kFull, rs, j);
+        if (warp_equal(P.arenaR + rsj, P.arenaS + sj, lj)) {
           if (lane == 0) {
+            const uint64_t srow = grp * 32 + (uint64_t)j;
             const uint32_t rid = P.idR ? __ldg(P.idR + rj) : rj;
-            const uint32_t sid = P.idS ? __ldg(P.idS + srj) : (uint32_t)srj;
+            const uint32_t sid = P.idS ? __ldg(P.idS + srow) : (uint32_t)srow;
             stage[np] = (uint64_t)rid | ((uint64_t)sid << 32);
           }
-          if (++np == (uint32_t)kPairBuf) {
-            flush_pairs(stage, np, P);
+          __syncwarp();
+          if (++np == (uint32_t)kVStage) {
+            flush_stage(stage, np, VP);
             np = 0;
           }
         }
       }
     }
-    cur = nxt;
-    nxt = nn;
   }
-  cp_async_wait_all();
-  if (np) flush_pairs(stage, np, P);
+  if (np) flush_stage(stage, np, VP);
 }
 
 // ----------------------------------------------------------------------------
@@ -290,6 +567,7 @@ static as_status cuda_fail(cudaError_t e, const char* where) {
 struct DeviceState {
   bool ready = false;
   int sms = 0;
+  int verify_blocks_per_sm = 1;
 };
 
 static std::mutex g_dev_mu;
@@ -316,14 +594,39 @@ static as_status ensure_device(DeviceState** out) {
     h_log[0] = 0;
     if ((e = cudaMemcpyToSymbol(g_log, h_log, sizeof(h_log))) != cudaSuccess) return cuda_fail(e, "table setup");
     if ((e = cudaMemcpyToSymbol(g_alog, h_alog, sizeof(h_alog))) != cudaSuccess) return cuda_fail(e, "table setup");
+    // constant-multiply tables: c_k^(2^s) = x^(k kTile/2 2^s) at (k-1)*5+s, then x^-32
+    static uint16_t h_const[kConstEntries];
+    auto mul = [&](uint32_t a, uint32_t b) -> uint32_t {
+      if (a == 0 || b == 0) return 0;
+      return h_alog[((uint32_t)h_log[a] + (uint32_t)h_log[b]) % kOrder];
+    };
+    for (int t = 0; t < kConstCount; t++) {
+      uint64_t ex;
+      if (t < 20) {
+        const int k = t / 5 + 1, sh = t % 5;
+        ex = ((uint64_t)k * (kTile / 2) << sh) % kOrder;
+      } else {
+        ex = kOrder - 32;
+      }
+      const uint32_t C = h_alog[ex];
+      for (uint32_t b = 0; b < 256; b++) {
+        h_const[t * 512 + b] = (uint16_t)mul(b, C);
+        h_const[t * 512 + 256 + b] = (uint16_t)mul(mul(b, h_alog[8]), C);
+      }
+    }
+    if ((e = cudaMemcpyToSymbol(g_const, h_const, sizeof(h_const))) != cudaSuccess) return cuda_fail(e, "table setup");
     if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return cuda_fail(e, "device query");
     if ((e = cudaFuncSetAttribute(sig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
-    if ((e = cudaFuncSetAttribute(probe_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemProbe)) !=
+    if ((e = cudaFuncSetAttribute(bl_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBHash)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.verify_blocks_per_sm, verify_kernel, kVThreads, 0)) !=
+        cudaSuccess)
+      return cuda_fail(e, "occupancy query");
+    if (d.verify_blocks_per_sm < 1) d.verify_blocks_per_sm = 1;
     d.ready = true;
   }
   *out = &d;
@@ -403,12 +706,12 @@ size_t as_join_table_bytes(uint64_t m, float load_factor) {
   uint64_t cap;
   uint32_t l2;
   if (!table_geometry(m, load_factor, &cap, &l2)) return 0;
-  return (size_t)(round256(cap * 8) + round256(m * 8) + 256);
+  return (size_t)(round256(cap * 16) + round256(m * 8) + 256);
 }
 
-size_t as_join_ws_bytes(uint64_t m, float load_factor) {
+size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor) {
   const size_t t = as_join_table_bytes(m, load_factor);
-  return t ? t + 256 : 0;
+  return t ? t + 256 + as_join_probe_ws_bytes(n) : 0;
 }
 
 as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, const uint64_t* d_offR,
@@ -430,11 +733,11 @@ as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, co
   if (st != AS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   uint8_t* ws = (uint8_t*)d_ws;
-  uint64_t* slots = (uint64_t*)ws;
-  uint64_t* sig_ws = (uint64_t*)(ws + round256(cap * 8));
-  uint32_t* flags = (uint32_t*)(ws + round256(cap * 8) + round256(m * 8));
+  Slot* slots = (Slot*)ws;
+  uint64_t* sig_ws = (uint64_t*)(ws + round256(cap * 16));
+  uint32_t* flags = (uint32_t*)(ws + round256(cap * 16) + round256(m * 8));
   cudaError_t e;
-  if ((e = cudaMemsetAsync(slots, 0xFF, cap * 8, s)) != cudaSuccess) return cuda_fail(e, "table clear");
+  if ((e = cudaMemsetAsync(slots, 0xFF, cap * 16, s)) != cudaSuccess) return cuda_fail(e, "table clear");
   if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
   const uint64_t* sigR = d_sigR;
   if (!sigR && m > 0) {
@@ -446,10 +749,10 @@ as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, co
     uint64_t blocks = (m + 255) / 256;
     const uint64_t lim = (uint64_t)d->sms * 16;
     if (blocks > lim) blocks = lim;
-    build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, cap - 1, sigR, d_offR, m, flags);
+    build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, cap - 1, sigR, d_offR, m, flags, nullptr, 0);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "build kernel launch");
   }
-  out->slots = slots;
+  out->slots = reinterpret_cast<uint64_t*>(slots);
   out->sigR = sigR ? sigR : sig_ws;
   out->arenaR = d_arenaR;
   out->offR = d_offR;
@@ -462,15 +765,26 @@ as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, co
   return AS_OK;
 }
 
+size_t as_join_probe_ws_bytes(uint64_t n) { return (size_t)(round256(n * 8) + 256); }
+
 as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS,
-                        uint64_t n, uint64_t* d_sigS_out, uint32_t* d_pairs, uint64_t cap_pairs, uint64_t* d_count,
-                        uint64_t* h_count, as_stream stream) {
+                        uint64_t n, uint64_t* d_sigS_out, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
+                        uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
   if (!t || !t->slots || !t->flags || !d_count) return fail(AS_ERR_INVALID, "as_join_probe: null table or counter");
   if (n > 0 && (!d_arenaS || !d_offS)) return fail(AS_ERR_INVALID, "as_join_probe: null relation");
   if (cap_pairs > 0 && !d_pairs) return fail(AS_ERR_INVALID, "as_join_probe: null pair buffer");
   if (n > 0 && misaligned16(d_arenaS)) return fail(AS_ERR_INVALID, "as_join_probe: arena not 16-byte aligned");
   if (d_pairs && (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
     return fail(AS_ERR_INVALID, "as_join_probe: pair buffer not 8-byte aligned");
+  uint64_t* sigS = d_sigS_out;
+  if (!sigS && n > 0) {
+    const size_t need = as_join_probe_ws_bytes(n);
+    if (!d_ws || ws_bytes < need)
+      return fail(AS_ERR_NOMEM, "as_join_probe: workspace of %zu bytes, need %zu", d_ws ? ws_bytes : 0, need);
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255u)
+      return fail(AS_ERR_INVALID, "as_join_probe: workspace not 256-byte aligned");
+    sigS = reinterpret_cast<uint64_t*>(d_ws);
+  }
   DeviceState* d = nullptr;
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
@@ -478,22 +792,29 @@ as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64
   cudaError_t e;
   if ((e = cudaMemsetAsync(d_count, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
   if (n > 0) {
-    ProbeParams P;
-    P.slots = t->slots;
+    st = launch_sig(d_arenaS, d_offS, n, sigS, s);
+    if (st != AS_OK) return st;
+    VerifyParams P;
+    P.slots = reinterpret_cast<const Slot*>(t->slots);
     P.mask = t->cap - 1;
-    P.sigR = t->sigR;
     P.arenaR = t->arenaR;
     P.offR = t->offR;
     P.idR = t->idR;
     P.arenaS = d_arenaS;
     P.offS = d_offS;
     P.idS = d_idS;
+    P.sigS = sigS;
     P.n = n;
-    P.sigS_out = d_sigS_out;
     P.pairs = d_pairs;
     P.cap = cap_pairs;
     P.count = reinterpret_cast<unsigned long long*>(d_count);
-    probe_kernel<<<walk_blocks(n, d->sms), kThreads, kSmemProbe, s>>>(P);
+    P.J = nullptr;
+    P.nj = 0;
+    P.counts = nullptr;
+    uint64_t blocks = (n + kVThreads - 1) / kVThreads;
+    const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
+    if (blocks > lim) blocks = lim;
+    verify_kernel<<<(unsigned)blocks, kVThreads, 0, s>>>(P);
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "probe kernel launch");
   }
   if (h_count) {
@@ -519,12 +840,254 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
                   uint64_t* d_count, uint64_t* h_count, as_stream stream) {
   const size_t tb = as_join_table_bytes(m, load_factor);
   if (!tb) return fail(AS_ERR_INVALID, "as_join: need 0 < load_factor <= 1 and m < 2^32-1");
-  if (ws_bytes < tb + 256) return fail(AS_ERR_NOMEM, "as_join: workspace of %zu bytes, need %zu", ws_bytes, tb + 256);
+  const size_t need = as_join_ws_bytes(m, n, load_factor);
+  if (!d_ws || ws_bytes < need) return fail(AS_ERR_NOMEM, "as_join: workspace of %zu bytes, need %zu", ws_bytes, need);
   as_table t;
   as_status st = as_join_build(d_ws, tb, d_arenaR, d_offR, d_idR, m, nullptr, load_factor, &t, stream);
   if (st != AS_OK) return st;
-  uint64_t* cnt = d_count ? d_count : (uint64_t*)((uint8_t*)d_ws + tb);
-  return as_join_probe(&t, d_arenaS, d_offS, d_idS, n, nullptr, d_pairs, cap_pairs, cnt, h_count, stream);
+  uint8_t* rest = (uint8_t*)d_ws + tb;
+  uint64_t* cnt = d_count ? d_count : (uint64_t*)rest;
+  return as_join_probe(&t, d_arenaS, d_offS, d_idS, n, nullptr, rest + 256, need - tb - 256, d_pairs, cap_pairs, cnt,
+                       h_count, stream);
+}
+
+// ----------------------------------------------------------------------------
+// Batches of independent joins
+// ----------------------------------------------------------------------------
+
+static_assert(sizeof(BatchJoin) == 64, "BatchJoin layout");
+
+// layout of a batch workspace: descriptors | slots | sigR | sigS | flags
+static bool batch_layout(const as_join_desc* descs, int nj, uint64_t mR, uint64_t nS, float lf,
+                         uint64_t* slots_total, uint64_t* bytes) {
+  if (nj < 1 || !descs || !(lf > 0.0f && lf <= 1.0f) || mR >= 0xFFFFFFFFull) return false;
+  uint64_t tot = 0, prev_r = 0, prev_s = 0;
+  for (int j = 0; j < nj; j++) {
+    const as_join_desc& d = descs[j];
+    if (d.r_begin > d.r_end || d.s_begin > d.s_end || d.r_end > mR || d.s_end > nS) return false;
+    if (d.r_begin < prev_r || d.s_begin < prev_s) return false;     // ordered, non-overlapping
+    prev_r = d.r_end;
+    prev_s = d.s_end;
+    uint64_t cap;
+    uint32_t l2;
+    if (!table_geometry(d.r_end - d.r_begin, lf, &cap, &l2)) return false;
+    tot += cap;
+  }
+  *slots_total = tot;
+  *bytes = round256((uint64_t)nj * sizeof(BatchJoin)) + round256(tot * 16) + round256(mR * 8) + round256(nS * 8) + 256;
+  return true;
+}
+
+size_t as_baseline_ws_bytes(uint64_t m, uint64_t n, float load_factor) {
+  uint64_t cap;
+  uint32_t l2;
+  if (!table_geometry(m, load_factor, &cap, &l2)) return 0;
+  return (size_t)(round256(cap * 8) + round256(m * 8) + round256(n * 8) + 512);
+}
+
+as_status as_baseline_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
+                           const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
+                           float load_factor, int tagged, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
+                           uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  uint64_t cap;
+  uint32_t l2;
+  if (!table_geometry(m, load_factor, &cap, &l2))
+    return fail(AS_ERR_INVALID, "as_baseline_join: need 0 < load_factor <= 1 and m < 2^32-1");
+  if ((m > 0 && (!d_arenaR || !d_offR)) || (n > 0 && (!d_arenaS || !d_offS)) || (cap_pairs > 0 && !d_pairs))
+    return fail(AS_ERR_INVALID, "as_baseline_join: null pointer");
+  if ((m > 0 && misaligned16(d_arenaR)) || (n > 0 && misaligned16(d_arenaS)))
+    return fail(AS_ERR_INVALID, "as_baseline_join: arena not 16-byte aligned");
+  if (d_pairs && (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
+    return fail(AS_ERR_INVALID, "as_baseline_join: pair buffer not 8-byte aligned");
+  const size_t need = as_baseline_ws_bytes(m, n, load_factor);
+  if (!d_ws || ws_bytes < need)
+    return fail(AS_ERR_NOMEM, "as_baseline_join: workspace of %zu bytes, need %zu", ws_bytes, need);
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255u)
+    return fail(AS_ERR_INVALID, "as_baseline_join: workspace not 256-byte aligned");
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t* ws = (uint8_t*)d_ws;
+  uint64_t* slots = (uint64_t*)ws;
+  uint64_t* hR = (uint64_t*)(ws + round256(cap * 8));
+  uint64_t* hS = (uint64_t*)(ws + round256(cap * 8) + round256(m * 8));
+  uint8_t* tail = ws + round256(cap * 8) + round256(m * 8) + round256(n * 8);
+  uint32_t* flags = (uint32_t*)tail;
+  uint64_t* cnt = d_count ? d_count : (uint64_t*)(tail + 256);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(slots, 0xFF, cap * 8, s)) != cudaSuccess) return cuda_fail(e, "table clear");
+  if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
+  if ((e = cudaMemsetAsync(cnt, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  if (m > 0) {
+    bl_hash_kernel<<<walk_blocks(m, d->sms), kThreads, kSmemBHash, s>>>(d_arenaR, d_offR, m, hR);
+    uint64_t blocks = (m + 255) / 256;
+    const uint64_t lim = (uint64_t)d->sms * 16;
+    if (blocks > lim) blocks = lim;
+    bl_build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, cap - 1, hR, m, tagged, flags);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "baseline build launch");
+  }
+  if (n > 0) {
+    bl_hash_kernel<<<walk_blocks(n, d->sms), kThreads, kSmemBHash, s>>>(d_arenaS, d_offS, n, hS);
+    BVerifyParams P;
+    P.slots = slots;
+    P.mask = cap - 1;
+    P.tagged = tagged;
+    P.arenaR = d_arenaR;
+    P.offR = d_offR;
+    P.idR = d_idR;
+    P.arenaS = d_arenaS;
+    P.offS = d_offS;
+    P.idS = d_idS;
+    P.hashS = hS;
+    P.n = n;
+    P.pairs = d_pairs;
+    P.cap = cap_pairs;
+    P.count = reinterpret_cast<unsigned long long*>(cnt);
+    uint64_t blocks = (n + kVThreads - 1) / kVThreads;
+    const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
+    if (blocks > lim) blocks = lim;
+    bl_verify_kernel<<<(unsigned)blocks, kVThreads, 0, s>>>(P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "baseline probe launch");
+  }
+  if (h_count) {
+    uint64_t c = 0;
+    uint32_t flags_h = 0;
+    if ((e = cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "count readback");
+    if ((e = cudaMemcpyAsync(&flags_h, flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_fail(e, "flag readback");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "baseline join");
+    *h_count = c;
+    if (flags_h & kFlagTableFull) return fail(AS_ERR_TABLE_FULL, "as_baseline_join: build overflow");
+    if (c > cap_pairs)
+      return fail(AS_ERR_CAPACITY, "as_baseline_join: %llu pairs, capacity %llu", (unsigned long long)c,
+                  (unsigned long long)cap_pairs);
+  }
+  return AS_OK;
+}
+
+size_t as_join_batch_ws_bytes(const as_join_desc* descs, int n_joins, uint64_t mR, uint64_t nS, float load_factor) {
+  uint64_t tot, bytes;
+  if (!batch_layout(descs, n_joins, mR, nS, load_factor, &tot, &bytes)) return 0;
+  return (size_t)bytes;
+}
+
+as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t mR, uint64_t nS, float load_factor,
+                                void* d_ws, size_t ws_bytes, as_batch* out, as_stream stream) {
+  if (!out) return fail(AS_ERR_INVALID, "as_join_batch_prepare: null batch");
+  uint64_t tot, bytes;
+  if (!batch_layout(descs, n_joins, mR, nS, load_factor, &tot, &bytes))
+    return fail(AS_ERR_INVALID, "as_join_batch_prepare: bad descriptors or load factor");
+  if (!d_ws || ws_bytes < bytes)
+    return fail(AS_ERR_NOMEM, "as_join_batch_prepare: workspace of %zu bytes, need %llu", ws_bytes,
+                (unsigned long long)bytes);
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return fail(AS_ERR_INVALID, "as_join_batch_prepare: workspace alignment");
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  std::vector<BatchJoin> h(n_joins);
+  uint64_t off = 0;
+  for (int j = 0; j < n_joins; j++) {
+    uint64_t cap;
+    uint32_t l2;
+    table_geometry(descs[j].r_end - descs[j].r_begin, load_factor, &cap, &l2);
+    h[j].r_begin = descs[j].r_begin;
+    h[j].r_end = descs[j].r_end;
+    h[j].s_begin = descs[j].s_begin;
+    h[j].s_end = descs[j].s_end;
+    h[j].slot_off = off;
+    h[j].mask = cap - 1;
+    h[j].pair_off = descs[j].pair_offset;
+    h[j].pair_cap = descs[j].pair_cap;
+    off += cap;
+  }
+  uint8_t* ws = (uint8_t*)d_ws;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(ws, h.data(), sizeof(BatchJoin) * n_joins, cudaMemcpyHostToDevice, (cudaStream_t)stream)) !=
+      cudaSuccess)
+    return cuda_fail(e, "batch descriptors");
+  if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e, "batch descriptors");
+  uint64_t o = round256((uint64_t)n_joins * sizeof(BatchJoin));
+  out->descs = ws;
+  out->slots = reinterpret_cast<uint64_t*>(ws + o);
+  o += round256(tot * 16);
+  out->sigR = reinterpret_cast<uint64_t*>(ws + o);
+  o += round256(mR * 8);
+  out->sigS = reinterpret_cast<uint64_t*>(ws + o);
+  o += round256(nS * 8);
+  out->flags = reinterpret_cast<uint32_t*>(ws + o);
+  out->n_joins = (uint64_t)n_joins;
+  out->slots_total = tot;
+  out->mR = mR;
+  out->nS = nS;
+  return AS_OK;
+}
+
+as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR,
+                            const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint32_t* d_pairs,
+                            uint64_t* d_counts, as_stream stream) {
+  if (!b || !b->descs || !d_counts) return fail(AS_ERR_INVALID, "as_join_batch_run: null batch or counters");
+  if ((b->mR > 0 && (!d_arenaR || !d_offR)) || (b->nS > 0 && (!d_arenaS || !d_offS)))
+    return fail(AS_ERR_INVALID, "as_join_batch_run: null relation");
+  if ((b->mR > 0 && misaligned16(d_arenaR)) || (b->nS > 0 && misaligned16(d_arenaS)))
+    return fail(AS_ERR_INVALID, "as_join_batch_run: arena not 16-byte aligned");
+  if (d_pairs && (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
+    return fail(AS_ERR_INVALID, "as_join_batch_run: pair buffer not 8-byte aligned");
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  const BatchJoin* J = reinterpret_cast<const BatchJoin*>(b->descs);
+  const int nj = (int)b->n_joins;
+  Slot* slots = reinterpret_cast<Slot*>(b->slots);
+  if ((e = cudaMemsetAsync(slots, 0xFF, b->slots_total * 16, s)) != cudaSuccess) return cuda_fail(e, "table clear");
+  if ((e = cudaMemsetAsync(b->flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
+  if ((e = cudaMemsetAsync(d_counts, 0, 8 * b->n_joins, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  if (b->mR > 0) {
+    sig_kernel<<<walk_blocks(b->mR, d->sms), kThreads, kSmemSig, s>>>(d_arenaR, d_offR, b->mR, b->sigR);
+    uint64_t blocks = (b->mR + 255) / 256;
+    const uint64_t lim = (uint64_t)d->sms * 16;
+    if (blocks > lim) blocks = lim;
+    build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, 0, b->sigR, d_offR, b->mR, b->flags, J, nj);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch build launch");
+  }
+  if (b->nS > 0) {
+    sig_kernel<<<walk_blocks(b->nS, d->sms), kThreads, kSmemSig, s>>>(d_arenaS, d_offS, b->nS, b->sigS);
+    VerifyParams P;
+    P.slots = slots;
+    P.mask = 0;
+    P.arenaR = d_arenaR;
+    P.offR = d_offR;
+    P.idR = d_idR;
+    P.arenaS = d_arenaS;
+    P.offS = d_offS;
+    P.idS = d_idS;
+    P.sigS = b->sigS;
+    P.n = b->nS;
+    P.pairs = d_pairs;
+    P.cap = 0;
+    P.count = nullptr;
+    P.J = J;
+    P.nj = nj;
+    P.counts = reinterpret_cast<unsigned long long*>(d_counts);
+    uint64_t blocks = (b->nS + kVThreads - 1) / kVThreads;
+    const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
+    if (blocks > lim) blocks = lim;
+    verify_kernel<<<(unsigned)blocks, kVThreads, 0, s>>>(P);
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch probe launch");
+  }
+  return AS_OK;
+}
+
+as_status as_join_batch(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t mR,
+                        const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t nS,
+                        const as_join_desc* descs, int n_joins, float load_factor, void* d_ws, size_t ws_bytes,
+                        uint32_t* d_pairs, uint64_t* d_counts, as_stream stream) {
+  as_batch b;
+  as_status st = as_join_batch_prepare(descs, n_joins, mR, nS, load_factor, d_ws, ws_bytes, &b, stream);
+  if (st != AS_OK) return st;
+  return as_join_batch_run(&b, d_arenaR, d_offR, d_idR, d_arenaS, d_offS, d_idS, d_pairs, d_counts, stream);
 }
 
 }  // extern "C"

@@ -13,8 +13,7 @@
 // lookups (bits 16..23 and 24..31), each entry holding b*x^16 (or b*x^24)
 // mod P together with b shifted into the cleared byte, so that one XOR both
 // removes the high byte and adds its residue.  The tables live in shared
-// memory, replicated once per bank so that the 32 lanes of a warp never
-// conflict.
+// memory, one copy per bank so that the 32 lanes of a warp never conflict.
 #pragma once
 #include <cstdint>
 
@@ -23,8 +22,14 @@ namespace algsig {
 constexpr uint32_t kPoly = 0x1100Bu;   // x^16 + x^12 + x^3 + x + 1
 constexpr uint32_t kOrder = 65535u;    // order of x (x is primitive for this P)
 
-// Shared-memory reduction tables: 2 tables x 256 entries x 32 replicas.
-constexpr int kRedWords = 2 * 256 * 32;
+// Shared-memory reduction tables: 256 rows of 256 bytes.  Row b holds, for
+// every lane l, the bits-16..23 entry of byte b at word 32*... see below:
+//   byte offset 256*b + 4*l        : T16[b] = (b * x^16 mod P) ^ (b << 16)
+//   byte offset 256*b + 128 + 4*l  : T24[b] = (b * x^24 mod P) ^ (b << 24)
+// Each lane reads its own bank, so the 32 lanes of a warp never conflict, and
+// the byte address of an entry is (b << 8) | (4*l [+128]): one PRMT builds it
+// from the unreduced value and the lane's offset.
+constexpr int kRedWords = 256 * 64;
 constexpr int kRedBytes = kRedWords * 4;
 
 __host__ __device__ __forceinline__ uint32_t gf_times_x(uint32_t a) {
@@ -32,8 +37,8 @@ __host__ __device__ __forceinline__ uint32_t gf_times_x(uint32_t a) {
   return (a & 0x10000u) ? (a ^ kPoly) : a;
 }
 
-// Fill the replicated reduction tables.  `tmp` is 512 words of scratch shared
-// memory.  Must be called by the whole block; ends with __syncthreads().
+// Fill the reduction tables.  `tmp` is 512 words of scratch shared memory.
+// Must be called by the whole block; ends with __syncthreads().
 __device__ __forceinline__ void init_red_tables(uint32_t* red, uint32_t* tmp) {
   for (int e = threadIdx.x; e < 512; e += blockDim.x) {
     const int tbl = e >> 8;            // 0: bits 16..23, 1: bits 24..31
@@ -44,58 +49,12 @@ __device__ __forceinline__ void init_red_tables(uint32_t* red, uint32_t* tmp) {
     tmp[e] = v ^ (b << (16 + 8 * tbl));
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < kRedWords; i += blockDim.x) red[i] = tmp[i >> 5];
+  for (int i = threadIdx.x; i < kRedWords; i += blockDim.x) {
+    const int b = i >> 6, tbl = (i >> 5) & 1;
+    red[i] = tmp[tbl * 256 + b];
+  }
   __syncthreads();
 }
-
-// 32-bit unreduced value -> 16-bit residue mod P.  `redl` = red + lane.
-__device__ __forceinline__ uint32_t red32(uint32_t u, const uint32_t* __restrict__ redl) {
-  const uint32_t b2 = (u >> 16) & 0xFFu;
-  const uint32_t b3 = u >> 24;
-  return u ^ redl[b2 << 5] ^ redl[(256u + b3) << 5];
-}
-
-// value < 2^24 -> 16-bit residue (only bits 16..23 to clear)
-__device__ __forceinline__ uint32_t red24(uint32_t u, const uint32_t* __restrict__ redl) {
-  return u ^ redl[(u >> 16) << 5];
-}
-
-// One Horner step over a 16-byte chunk: acc_k <- acc_k * x^(8k) + sum_j q_j x^(kj),
-// where q_{2t} = low half of word t and q_{2t+1} = high half of word t.
-// Accumulators enter and leave reduced (< 2^16).
-__device__ __forceinline__ void horner_chunk(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
-                                             uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& a4,
-                                             const uint32_t* __restrict__ redl) {
-  const uint32_t l0 = v0 & 0xFFFFu, h0 = v0 >> 16;
-  const uint32_t l1 = v1 & 0xFFFFu, h1 = v1 >> 16;
-  const uint32_t l2 = v2 & 0xFFFFu, h2 = v2 >> 16;
-  const uint32_t l3 = v3 & 0xFFFFu, h3 = v3 >> 16;
-  uint32_t u;
-  // k = 1: 8 symbols, growth 8 bits
-  u = (a1 << 8) ^ l0 ^ (h0 << 1) ^ (l1 << 2) ^ (h1 << 3) ^ (l2 << 4) ^ (h2 << 5) ^ (l3 << 6) ^ (h3 << 7);
-  a1 = red24(u, redl);
-  // k = 2: 8 symbols, growth 16 bits
-  u = (a2 << 16) ^ l0 ^ (h0 << 2) ^ (l1 << 4) ^ (h1 << 6) ^ (l2 << 8) ^ (h2 << 10) ^ (l3 << 12) ^ (h3 << 14);
-  a2 = red32(u, redl);
-  // k = 3: two halves of 4 symbols, growth 12 bits each (upper half first)
-  u = (a3 << 12) ^ l2 ^ (h2 << 3) ^ (l3 << 6) ^ (h3 << 9);
-  a3 = red32(u, redl);
-  u = (a3 << 12) ^ l0 ^ (h0 << 3) ^ (l1 << 6) ^ (h1 << 9);
-  a3 = red32(u, redl);
-  // k = 4: two halves of 4 symbols, growth 16 bits each
-  u = (a4 << 16) ^ l2 ^ (h2 << 4) ^ (l3 << 8) ^ (h3 << 12);
-  a4 = red32(u, redl);
-  u = (a4 << 16) ^ l0 ^ (h0 << 4) ^ (l1 << 8) ^ (h1 << 12);
-  a4 = red32(u, redl);
-}
-
-// ---------------------------------------------------------------------------
-// Same step with explicit 32-bit shared-memory addressing of the reduction
-// tables.  Word (b * 32 + lane) of the table at byte offset `tab` holds the
-// bits-16..23 entry for byte b; the bits-24..31 table follows 32 KB later.
-// `lane4` = 4 * lane.  The byte address of entry b is (b << 7) | lane4, which
-// comes out of one shift and one LOP3.
-// ---------------------------------------------------------------------------
 
 __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
   uint32_t v;
@@ -103,44 +62,74 @@ __device__ __forceinline__ uint32_t lds32(uint32_t addr) {
   return v;
 }
 
-__device__ __forceinline__ uint32_t lop3_and_or(uint32_t a, uint32_t mask, uint32_t o) {
-  // (a & mask) | o
+// bytes (b_sel << 8) | low byte of `base`: byte 0 from base, byte 1 from u's byte
+// `sel` (2 or 3), bytes 2..3 zero (base < 256)
+__device__ __forceinline__ uint32_t tab_index(uint32_t u, uint32_t base, uint32_t sel) {
   uint32_t r;
-  asm("lop3.b32 %0, %1, %2, %3, 0xEA;" : "=r"(r) : "r"(a), "r"(mask), "r"(o));
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(r) : "r"(u), "r"(base), "r"(sel));
   return r;
 }
 
-__device__ __forceinline__ uint32_t red32s(uint32_t u, uint32_t tab_lane) {
-  const uint32_t i2 = lop3_and_or(u >> 9, 0x7F80u, tab_lane);
-  const uint32_t i3 = lop3_and_or(u >> 17, 0x7F80u, tab_lane + 32768u);
-  return u ^ lds32(i2) ^ lds32(i3);
+// Per-lane table cursor: shared byte address of the tables, the lane's two
+// offsets (4*l and 4*l + 128) and the PRMT selectors.
+struct RedCursor {
+  uint32_t tab;       // shared byte address of the tables
+  uint32_t off16;     // 4*lane
+  uint32_t off24;     // 4*lane + 128
+};
+
+__device__ __forceinline__ RedCursor red_cursor(const uint32_t* red) {
+  RedCursor c;
+  c.tab = (uint32_t)__cvta_generic_to_shared(red);
+  c.off16 = 4u * (threadIdx.x & 31u);
+  c.off24 = c.off16 + 128u;
+  return c;
 }
 
-__device__ __forceinline__ uint32_t red24s(uint32_t u, uint32_t tab_lane) {
-  return u ^ lds32(lop3_and_or(u >> 9, 0x7F80u, tab_lane));
+// PRMT selectors: result byte0 = base byte0 (index 4), byte1 = u byte 2 or 3,
+// bytes 2, 3 = base byte 1 (index 5, zero)
+constexpr uint32_t kSel16 = 0x5524u;
+constexpr uint32_t kSel24 = 0x5534u;
+
+// 32-bit unreduced value -> 16-bit residue mod P
+__device__ __forceinline__ uint32_t red32(uint32_t u, const RedCursor& c) {
+  const uint32_t t16 = lds32(c.tab + tab_index(u, c.off16, kSel16));
+  const uint32_t t24 = lds32(c.tab + tab_index(u, c.off24, kSel24));
+  return u ^ t16 ^ t24;
 }
 
-// tab_lane = shared byte address of the tables + 4 * lane
-__device__ __forceinline__ void horner_chunk_s(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
-                                               uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& a4,
-                                               uint32_t tab_lane) {
+// value < 2^24 -> 16-bit residue (only bits 16..23 to clear)
+__device__ __forceinline__ uint32_t red24(uint32_t u, const RedCursor& c) {
+  return u ^ lds32(c.tab + tab_index(u, c.off16, kSel16));
+}
+
+// One Horner step over a 16-byte chunk: acc_k <- acc_k * x^(8k) + sum_j q_j x^(kj),
+// where q_{2t} = low half of word t and q_{2t+1} = high half of word t.
+// Accumulators enter and leave reduced (< 2^16).
+__device__ __forceinline__ void horner_chunk(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
+                                             uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& a4,
+                                             const RedCursor& rc) {
   const uint32_t l0 = v0 & 0xFFFFu, h0 = v0 >> 16;
   const uint32_t l1 = v1 & 0xFFFFu, h1 = v1 >> 16;
   const uint32_t l2 = v2 & 0xFFFFu, h2 = v2 >> 16;
   const uint32_t l3 = v3 & 0xFFFFu, h3 = v3 >> 16;
   uint32_t u;
+  // k = 1: 8 symbols, growth 8 bits
   u = (a1 << 8) ^ l0 ^ (h0 << 1) ^ (l1 << 2) ^ (h1 << 3) ^ (l2 << 4) ^ (h2 << 5) ^ (l3 << 6) ^ (h3 << 7);
-  a1 = red24s(u, tab_lane);
+  a1 = red24(u, rc);
+  // k = 2: 8 symbols, growth 16 bits
   u = (a2 << 16) ^ l0 ^ (h0 << 2) ^ (l1 << 4) ^ (h1 << 6) ^ (l2 << 8) ^ (h2 << 10) ^ (l3 << 12) ^ (h3 << 14);
-  a2 = red32s(u, tab_lane);
+  a2 = red32(u, rc);
+  // k = 3: two halves of 4 symbols, growth 12 bits each (upper half first)
   u = (a3 << 12) ^ l2 ^ (h2 << 3) ^ (l3 << 6) ^ (h3 << 9);
-  a3 = red32s(u, tab_lane);
+  a3 = red32(u, rc);
   u = (a3 << 12) ^ l0 ^ (h0 << 3) ^ (l1 << 6) ^ (h1 << 9);
-  a3 = red32s(u, tab_lane);
+  a3 = red32(u, rc);
+  // k = 4: two halves of 4 symbols, growth 16 bits each
   u = (a4 << 16) ^ l2 ^ (h2 << 4) ^ (l3 << 8) ^ (h3 << 12);
-  a4 = red32s(u, tab_lane);
+  a4 = red32(u, rc);
   u = (a4 << 16) ^ l0 ^ (h0 << 4) ^ (l1 << 8) ^ (h1 << 12);
-  a4 = red32s(u, tab_lane);
+  a4 = red32(u, rc);
 }
 
 // Mask of bytes [b0, b1) of a 16-byte chunk, for its 32-bit word j.

@@ -5,21 +5,21 @@
 // of the arena.  If ks is odd, the byte stream is funnel-shifted by one byte
 // so that the key's symbols sit on 16-bit boundaries ("realigned" stream);
 // the key then starts at the even offset lo = (ks & 15) - (ks & 1) of its
-// first realigned chunk.  A tile is 8 realigned chunks (kTile = 128 bytes) of
-// that grid: tile j of a key covers realigned chunks [8j, 8j+8) (the first
-// tile starts at lo, the last ends with the key), so interior tiles read
-// exactly 8 aligned chunks.  An empty key has one empty tile.
+// first realigned chunk.  A tile is kTileChunks realigned chunks of that grid
+// (kTile bytes): tile j of a key covers realigned chunks [j, j+1) * kTileChunks
+// (the first tile starts at lo, the last ends with the key), so interior tiles
+// read exactly kTileChunks aligned chunks.  An empty key has one empty tile.
 //
 // Rounds.  A warp owns a contiguous, byte-balanced range of keys and walks
 // their tiles in rounds of 32 (one per lane).  The 32 tiles of a round are
 // consecutive in the arena, so a round reads one contiguous span; cp.async
 // copies it to shared memory two rounds ahead of the arithmetic.  In shared
-// memory a 16-byte pad follows every 128 bytes of span, so that the lanes of
-// one key, whose tiles are 128 bytes apart, read different banks.
+// memory a 16-byte pad follows every kTile bytes of span, so that the lanes of
+// one key, whose tiles are kTile bytes apart, read different banks.
 //
 // Combination.  Each lane computes its tile's signature relative to the
 // tile's first slot (Horner over 16-byte chunks, gf16.cuh) and moves it to the
-// tile's place in the key by a multiplication with x^(k (64 j - lo/2)) through
+// tile's place in the key by a multiplication with x^(k (kTile/2 j - lo/2)) through
 // log/antilog tables; the log lookups are issued before the next round is
 // planned, which hides their latency.  Tiles of one key sit in consecutive
 // lanes: a segmented XOR gathers them in the key's first lane of the round,
@@ -32,9 +32,14 @@
 
 namespace algsig {
 
-constexpr int kTile = 128;                        // bytes of realigned key per tile (8 chunks)
-constexpr int kSpanChunks = 32 * (kTile / 16) + 2;   // chunks of a round's span, worst case
-constexpr int kBufBytes = 16 * (kSpanChunks + (kSpanChunks + 7) / 8) + 16;   // with one pad per 8 chunks
+#ifndef ALGSIG_TILE_CHUNKS
+#define ALGSIG_TILE_CHUNKS 16
+#endif
+constexpr int kTileChunks = ALGSIG_TILE_CHUNKS;       // 16-byte chunks per tile
+constexpr int kTile = 16 * kTileChunks;               // bytes of realigned key per tile
+constexpr int kSpanChunks = 32 * kTileChunks + 2;     // chunks of a round's span, worst case
+// one 16-byte pad per tile-length of span, so that tiles kTile bytes apart hit different banks
+constexpr int kBufBytes = 16 * (kSpanChunks + (kSpanChunks + kTileChunks - 1) / kTileChunks) + 16;
 constexpr uint32_t kFull = 0xFFFFFFFFu;
 
 // g_log / g_alog: GF(2^16) logarithm / antilogarithm of x, defined (and set
@@ -58,8 +63,8 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait_prev() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
-// shared-memory byte offset of span offset `rel` (16-byte pad after every 128 bytes)
-__device__ __forceinline__ uint32_t padded(uint32_t rel) { return rel + ((rel >> 7) << 4); }
+// shared-memory byte offset of span offset `rel` (16-byte pad after every kTile bytes)
+__device__ __forceinline__ uint32_t padded(uint32_t rel) { return rel + (rel / (uint32_t)kTile) * 16u; }
 
 // ---------------------------------------------------------------------------
 // warp range: keys [k_lo, k_hi) whose starts fall in this warp's share of the
@@ -124,6 +129,7 @@ struct Plan {
   // warp-uniform
   bool valid;
   uint64_t kc;               // first key of the round
+  uint64_t tc;               // tiles of key kc done before the round
   uint64_t kc_next, tc_next; // walk state after the round
   uint64_t span_lo, span_hi; // 16-byte aligned arena span of the round
   bool carries;              // key of slot 31 continues into the next round
@@ -157,6 +163,7 @@ __device__ __forceinline__ Plan plan_round(const PlanLoad& L, uint64_t kc, uint6
   Plan p;
   p.valid = kc < k_end;
   p.kc = kc;
+  p.tc = tc;
   const int lane = threadIdx.x & 31;
   const uint64_t kl = kc + (uint64_t)lane;
   const bool have = p.valid && kl < k_end;
@@ -196,10 +203,10 @@ __device__ __forceinline__ Plan plan_round(const PlanLoad& L, uint64_t kc, uint6
   p.lo = a - p.odd;
   const uint64_t kbase = p.kstart - a;
   const uint64_t C = p.klen == 0 ? 0 : (p.lo + p.klen + 15) >> 4;       // realigned chunks of the key
-  const uint64_t c0 = tile * (kTile / 16);
+  const uint64_t c0 = tile * (kTileChunks);
   const uint64_t rest = C > c0 ? C - c0 : 0;
-  p.nc = p.active ? (uint32_t)(rest < (uint64_t)(kTile / 16) ? rest : (uint64_t)(kTile / 16)) : 0u;
-  p.last = c0 + (kTile / 16) >= C;
+  p.nc = p.active ? (uint32_t)(rest < (uint64_t)(kTileChunks) ? rest : (uint64_t)(kTileChunks)) : 0u;
+  p.last = c0 + (kTileChunks) >= C;
   p.tail_e = p.last && p.klen ? (uint32_t)(p.lo + p.klen - 16 * (C - 1)) : 16u;
   p.cbase = kbase + 16 * c0;
   // tile's arena byte range: [max(ks, cbase + odd), min(ks + len, cbase + 128 + odd))
@@ -246,7 +253,8 @@ __device__ __forceinline__ void issue_span(uint8_t* buf, const uint8_t* __restri
     const int lane = threadIdx.x & 31;
     const uint32_t nchunks = (uint32_t)((p.span_hi - p.span_lo) >> 4);
     const uint8_t* src = arena + p.span_lo;
-    for (uint32_t i = (uint32_t)lane; i < nchunks; i += 32) cp_async16(buf + 16 * (i + (i >> 3)), src + 16 * i);
+    for (uint32_t i = (uint32_t)lane; i < nchunks; i += 32)
+      cp_async16(buf + 16 * (i + i / (uint32_t)kTileChunks), src + 16 * i);
   }
   cp_async_commit();
 }
@@ -273,7 +281,7 @@ __device__ __forceinline__ void keep_below(uint32_t e, uint64_t& lo64, uint64_t&
 // Unreduced-free tile signature: a_k = sum over the tile's slots t of q_t x^(k t)
 // (slot 0 = first byte pair of the tile's first realigned chunk), reduced to 16 bits.
 __device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t span_lo, const Plan& p,
-                                                const uint32_t* __restrict__ redl, uint32_t& a1, uint32_t& a2,
+                                                const RedCursor& redl, uint32_t& a1, uint32_t& a2,
                                                 uint32_t& a3, uint32_t& a4) {
   a1 = a2 = a3 = a4 = 0;
   if (p.nc == 0) return;
@@ -314,58 +322,120 @@ __device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t spa
   }
 }
 
-// exponent of the tile's shift: 64*tile - lo/2 (mod 65535), for component 1
-__device__ __forceinline__ uint32_t tile_exponent(const Plan& p) {
-  const uint32_t t = (p.tile % kOrder) * (uint32_t)(kTile / 2) % kOrder;
-  const uint32_t h = p.lo >> 1;
-  return t >= h ? t - h : t + kOrder - h;
+// ---------------------------------------------------------------------------
+// Combination of the tiles of a round
+// ---------------------------------------------------------------------------
+//
+// Tile values A_j (relative to each tile's first slot) of one key are joined
+// by Horner's rule with the constant c_k = x^(k kTile/2):
+//     B = sum_i c_k^i A_(j0+i)
+// computed as a reverse segmented scan over the lanes of the key (log2(32)
+// doubling steps, step s multiplying by c_k^(2^s)).  A multiplication by a
+// constant C is two lookups in a 512-entry table (low byte, high byte) held in
+// shared memory: tables for c_k^(2^s) (k = 1..4, s = 0..4) and for x^-32.
+//
+// A key whose tile 0 lies in the round gets its signature from B directly; the
+// shift of its first symbol to slot lo/2 of the chunk grid is undone once per
+// key by x^-(k lo/2).  A key that continues from an earlier round needs
+// x^(k kTile/2 j0) B with a variable j0: that product goes through the
+// log/antilog tables in global memory and is finished one round later, so the
+// lookups overlap the next round's arithmetic.
+
+constexpr int kConstCount = 21;                       // 20 scan constants + x^-32
+constexpr int kConstEntries = kConstCount * 512;
+constexpr int kConstBytes = kConstEntries * 2;
+
+// multiply by the constant whose table starts at `tab`
+__device__ __forceinline__ uint32_t mulc(const uint16_t* tab, uint32_t v) {
+  return (uint32_t)tab[v & 0xFFu] ^ (uint32_t)tab[256u + (v >> 8)];
 }
 
-// Combine: multiply the lanes' tile values by x^(k e) (log/antilog), gather
-// each key's tiles in its first lane, apply / produce the carry.
-struct TileVals {
-  uint32_t l1, l2, l3, l4;   // logs of a_k + k*e (mod 65535), or 0xFFFFFFFF for a_k = 0
+// component-wise multiply of a packed signature by c_k^(2^s)
+__device__ __forceinline__ uint64_t mul_scan(const uint16_t* ctab, uint64_t v, int s) {
+  uint64_t r = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint16_t* t = ctab + (size_t)(k * 5 + s) * 512;
+    r |= (uint64_t)mulc(t, (uint32_t)(v >> (16 * k)) & 0xFFFFu) << (16 * k);
+  }
+  return r;
+}
+
+// x^-(k lo/2) * P, component-wise
+__device__ __forceinline__ uint64_t lo_correct(const uint16_t* ctab, uint64_t P, uint32_t lo, const RedCursor& rc) {
+  const uint16_t* inv32 = ctab + 20 * 512;
+  uint64_t out = 0;
+#pragma unroll
+  for (int k = 1; k <= 4; k++) {
+    const uint32_t m = (uint32_t)k * (lo >> 1);                 // <= 28
+    const uint32_t d = mulc(inv32, (uint32_t)(P >> (16 * (k - 1))) & 0xFFFFu);
+    const uint64_t E = (uint64_t)d << (32 - m);                 // d x^(32-m), < 2^48
+    const uint32_t r1 = red32((uint32_t)(E >> 16), rc);
+    const uint32_t r = red32(((uint32_t)E & 0xFFFFu) ^ (r1 << 16), rc);
+    out |= (uint64_t)r << (16 * (k - 1));
+  }
+  return out;
+}
+
+// packed tile value of a lane
+__device__ __forceinline__ uint64_t pack4(uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4) {
+  return (uint64_t)a1 | ((uint64_t)a2 << 16) | ((uint64_t)a3 << 32) | ((uint64_t)a4 << 48);
+}
+
+// Reverse segmented scan: the first lane of every key group ends with B.
+__device__ __forceinline__ uint64_t scan_round(const Plan& p, uint64_t V, const uint16_t* ctab) {
+  const int lane = threadIdx.x & 31;
+  const int g = p.active ? p.q : 32 + lane;
+  const uint32_t room = 32u - p.slot0;
+  const uint32_t gsize = p.active ? (p.rq < room ? p.rq : room) : 1u;
+  const uint32_t gmax = __reduce_max_sync(kFull, gsize);
+  for (int s = 0; (1u << s) < gmax; ++s) {
+    const uint64_t o = __shfl_down_sync(kFull, V, 1u << s);
+    const int og = __shfl_down_sync(kFull, g, 1u << s);
+    if (lane + (1 << s) < 32 && og == g) V ^= mul_scan(ctab, o, s);
+  }
+  return V;
+}
+
+// The deferred product x^(k e) B of a continuing key (see above), held by
+// every lane (warp-uniform).
+struct Pending {
+  bool valid;
+  bool complete;     // the key ends in the round that created this
+  uint64_t key;
+  uint64_t carry;    // partial signature of the key before that round
+  uint32_t lo;
+  uint32_t l1, l2, l3, l4;   // log(B_k) + k e, or ~0 for B_k = 0 (then: antilogs)
 };
 
-__device__ __forceinline__ TileVals tile_logs(const Plan& p, uint32_t a1, uint32_t a2, uint32_t a3, uint32_t a4) {
-  const uint32_t e1 = tile_exponent(p);
-  uint32_t e2 = e1 * 2u; if (e2 >= kOrder) e2 -= kOrder;
-  uint32_t e3 = e2 + e1; if (e3 >= kOrder) e3 -= kOrder;
-  uint32_t e4 = e2 * 2u; if (e4 >= kOrder) e4 -= kOrder;
-  TileVals v;
-  v.l1 = a1 ? (uint32_t)__ldg(&g_log[a1]) + e1 : 0xFFFFFFFFu;
-  v.l2 = a2 ? (uint32_t)__ldg(&g_log[a2]) + e2 : 0xFFFFFFFFu;
-  v.l3 = a3 ? (uint32_t)__ldg(&g_log[a3]) + e3 : 0xFFFFFFFFu;
-  v.l4 = a4 ? (uint32_t)__ldg(&g_log[a4]) + e4 : 0xFFFFFFFFu;
-  return v;
+__device__ __forceinline__ uint32_t log_plus(uint32_t b, uint32_t e) {
+  return b ? (uint32_t)__ldg(&g_log[b]) + e : 0xFFFFFFFFu;
 }
-
 __device__ __forceinline__ uint32_t alog_of(uint32_t l) {
   if (l == 0xFFFFFFFFu) return 0;
   if (l >= kOrder) l -= kOrder;
   return __ldg(&g_alog[l]);
 }
 
-__device__ __forceinline__ uint64_t combine_round(const Plan& p, const TileVals& v, uint64_t& carry, bool& complete) {
-  const int lane = threadIdx.x & 31;
-  uint64_t contrib = 0;
-  if (p.active) {
-    contrib = (uint64_t)alog_of(v.l1) | ((uint64_t)alog_of(v.l2) << 16) | ((uint64_t)alog_of(v.l3) << 32) |
-              ((uint64_t)alog_of(v.l4) << 48);
-  }
-  const int g = p.active ? p.q : 32 + lane;
-#pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const uint64_t o = __shfl_down_sync(kFull, contrib, d);
-    const int og = __shfl_down_sync(kFull, g, d);
-    if (lane + d < 32 && og == g) contrib ^= o;
-  }
-  const bool head = p.active && (uint32_t)lane == p.slot0;
-  if (head && p.q == 0) contrib ^= carry;
-  complete = head && (p.slot0 + p.rq <= 32u);
-  const uint64_t part = __shfl_sync(kFull, contrib, (int)p.s31);
-  carry = p.carries ? part : 0;
-  return contrib;
+// start the product x^(k e) B: logs (the caller later turns them into antilogs)
+__device__ __forceinline__ void pending_logs(Pending& pd, uint64_t B, uint64_t tile0) {
+  const uint32_t e1 = (uint32_t)(tile0 % kOrder) * (uint32_t)(kTile / 2) % kOrder;
+  uint32_t e2 = e1 * 2u; if (e2 >= kOrder) e2 -= kOrder;
+  uint32_t e3 = e2 + e1; if (e3 >= kOrder) e3 -= kOrder;
+  uint32_t e4 = e2 * 2u; if (e4 >= kOrder) e4 -= kOrder;
+  pd.l1 = log_plus((uint32_t)B & 0xFFFFu, e1);
+  pd.l2 = log_plus((uint32_t)(B >> 16) & 0xFFFFu, e2);
+  pd.l3 = log_plus((uint32_t)(B >> 32) & 0xFFFFu, e3);
+  pd.l4 = log_plus((uint32_t)(B >> 48) & 0xFFFFu, e4);
+}
+__device__ __forceinline__ void pending_alogs(Pending& pd) {
+  pd.l1 = alog_of(pd.l1);
+  pd.l2 = alog_of(pd.l2);
+  pd.l3 = alog_of(pd.l3);
+  pd.l4 = alog_of(pd.l4);
+}
+__device__ __forceinline__ uint64_t pending_value(const Pending& pd) {
+  return pd.carry ^ pack4(pd.l1, pd.l2, pd.l3, pd.l4);
 }
 
 }  // namespace algsig

@@ -1,0 +1,73 @@
+"""Batches of joins (as_join_batch_prepare / as_join_batch_run through the C
+ABI): every join's sorted pairs equal the oracle's on that join's rows, equal
+the same join run alone, and a CUDA-graph replay gives the same result."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(ag, rel):
+    return ag.DeviceRelation.from_host(rel.arena, rel.off, rel.ids)
+
+
+@pytest.fixture(scope="module")
+def batch():
+    spec = workloads.BatchSpec().scaled(400, n_joins=24)
+    return workloads.generate_batch(spec)
+
+
+def test_batch_matches_oracle_and_solo(cuda, batch):
+    ag = cuda
+    Rd, Sd = dev(ag, batch.R), dev(ag, batch.S)
+    R = ag.DeviceRelation(Rd.arena, Rd.off, None)     # no ids: join-local row numbers
+    S = ag.DeviceRelation(Sd.arena, Sd.off, None)
+    caps = [max(64, 2 * e + 64) for e in batch.expected]
+    out = ag.join_batch(R, S, batch.ranges, caps, load_factor=0.5)
+    for j in range(len(batch.ranges)):
+        Rj, Sj = batch.join_relations(j)
+        want = oracle.join_simple(Rj, Sj)
+        got = oracle.sort_pairs(out[j].cpu().numpy().view(np.uint32))
+        assert np.array_equal(got, want), j
+        assert len(want) == batch.expected[j]
+        solo = oracle.sort_pairs(ag.join(dev(ag, Rj), dev(ag, Sj)).cpu().numpy().view(np.uint32))
+        assert np.array_equal(solo, got), j
+
+
+def test_batch_graph_replay_and_ids(cuda, batch):
+    ag = cuda
+    R = dev(ag, batch.R)            # ids = global rows, so pairs carry global ids
+    S = dev(ag, batch.S)
+    caps = [max(64, 2 * e + 64) for e in batch.expected]
+    descs = ag.make_descs(batch.ranges, caps)
+    ws = ag.alloc_ws(ag.join_batch_ws_bytes(descs, R.n, S.n, 0.7))
+    b = ag.join_batch_prepare(descs, R, S, ws, 0.7)
+    pairs = torch.zeros(2 * ag.total_pair_cap(descs), dtype=torch.int32, device="cuda")
+    counts = torch.zeros(len(descs), dtype=torch.int64, device="cuda")
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        ag.join_batch_run(b, R, S, pairs, counts)        # warm-up outside capture
+    torch.cuda.synchronize()
+    first = [oracle.sort_pairs(pairs[2 * d.pair_offset: 2 * (d.pair_offset + c)].cpu().numpy().view(np.uint32))
+             for d, c in zip(descs, counts.cpu().tolist())]
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        ag.join_batch_run(b, R, S, pairs, counts)
+    for _ in range(2):
+        pairs.zero_()
+        g.replay()
+        torch.cuda.synchronize()
+        again = [oracle.sort_pairs(pairs[2 * d.pair_offset: 2 * (d.pair_offset + c)].cpu().numpy().view(np.uint32))
+                 for d, c in zip(descs, counts.cpu().tolist())]
+        for a_, b_ in zip(first, again):
+            assert np.array_equal(a_, b_)
+    for j, (rb, re_, sb, se) in enumerate(batch.ranges):
+        Rj, Sj = batch.join_relations(j)
+        want = oracle.join_simple(Rj, Sj).astype(np.int64)
+        want[:, 0] += rb
+        want[:, 1] += sb
+        assert np.array_equal(first[j].astype(np.int64), want)

@@ -79,7 +79,7 @@ def test_capacity_overflow_reports_exact_count(cuda):
     ag = cuda
     wl = workloads.generate(workloads.CONFIGS["plain"].scaled(1000, 10_000))
     R, S = dev(ag, wl.R), dev(ag, wl.S)
-    ws = ag.alloc_ws(ag.join_ws_bytes(R.n, 0.5))
+    ws = ag.alloc_ws(ag.join_ws_bytes(R.n, S.n, 0.5))
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     pairs = torch.full((2 * 100,), -1, dtype=torch.int32, device="cuda")
     st, cnt = ag.join_into(R, S, ws, pairs, count, 0.5, sync=True, allow_capacity=True)
@@ -101,6 +101,9 @@ def test_build_probe_split_and_signature_output(cuda):
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
     sigS = torch.empty(S.n, dtype=torch.int64, device="cuda")
     cnt = ag.join_probe(t, S, pairs, count, sigS_out=sigS)
+    pws = ag.alloc_ws(ag.join_probe_ws_bytes(S.n))
+    cnt2 = ag.join_probe(t, S, pairs, count, ws=pws)
+    assert cnt2 == cnt
     got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
     assert np.array_equal(got, oracle.join_simple(wl.R, wl.S))
     assert np.array_equal(sigS.cpu().numpy().view(np.uint64), oracle.sig_batch(wl.S.arena, wl.S.off, nthreads=8))
@@ -122,3 +125,26 @@ def test_large_config_scaled(cuda):
     wl = workloads.generate(workloads.CONFIGS["large"].scaled(20_000, 200_000))
     want = check(cuda, wl.R, wl.S)
     assert len(want) == wl.expected_pairs()
+
+
+# ----------------------------------------------------------------------------- the comparison join
+
+def gpu_baseline(ag, R, S, tagged, lf=0.5):
+    pairs = ag.baseline_join(dev(ag, R), dev(ag, S), load_factor=lf, tagged=tagged)
+    return oracle.sort_pairs(pairs.cpu().numpy().view(np.uint32))
+
+
+@pytest.mark.parametrize("tagged", [False, True])
+def test_baseline_join_matches_oracle(cuda, tagged):
+    keys = edge_keys()
+    R = relation_garbage_tail(keys, seed=11)
+    S = relation_garbage_tail(list(reversed(keys)) + keys, seed=12)
+    assert np.array_equal(gpu_baseline(cuda, R, S, tagged), oracle.join_simple(R, S))
+    rng = random.Random(13)
+    pool = [bytes(rng.randrange(4) for _ in range(rng.randrange(0, 40))) for _ in range(60)]
+    R = relation_garbage_tail([rng.choice(pool) for _ in range(800)], seed=14)
+    S = relation_garbage_tail([rng.choice(pool) for _ in range(2000)], seed=15)
+    for lf in (1.0, 0.5):
+        assert np.array_equal(gpu_baseline(cuda, R, S, tagged, lf), oracle.join_simple(R, S))
+    wl = workloads.generate(workloads.CONFIGS["large"].scaled(5_000, 50_000))
+    assert np.array_equal(gpu_baseline(cuda, wl.R, wl.S, tagged), oracle.join_simple(wl.R, wl.S))

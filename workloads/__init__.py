@@ -238,3 +238,100 @@ def key_bytes(spec: JoinSpec, rel: int, ident: int, length: int) -> bytes:
 
 def perm(seed: int, tag: int, n: int, x: int) -> int:
     return int(_load().gen_perm(seed, tag, n, x))
+
+
+# ----------------------------------------------------------------------------- batches of joins
+
+@dataclasses.dataclass(frozen=True)
+class BatchSpec:
+    """Many independent joins of uneven sizes and key lengths (packed in one R
+    and one S relation).  |R_j| is log-normal (median, sigma) clipped to
+    r_range; |S_j| = s_factor |R_j|; each join draws one key-length band."""
+    n_joins: int = 512
+    r_median: float = 20_000
+    sigma: float = 1.0
+    r_range: tuple = (1_000, 1_000_000)
+    s_factor: int = 10
+    bands: tuple = ((32, 128), (256, 1024), (2048, 8192))
+    frac_copy: float = 0.25
+    alphabet: str = "printable"
+    seed: int = 20084
+
+    def scaled(self, factor: float, n_joins: int | None = None) -> "BatchSpec":
+        """Relation sizes divided by `factor` (the shape is kept)."""
+        return dataclasses.replace(self, r_median=self.r_median / factor,
+                                   r_range=(max(1, int(self.r_range[0] / factor)), max(1, int(self.r_range[1] / factor))),
+                                   n_joins=self.n_joins if n_joins is None else n_joins)
+
+    def joins(self):
+        """The JoinSpec of every join (pure function of the seed)."""
+        rng = np.random.default_rng(self.seed)
+        sizes = np.exp(rng.normal(np.log(self.r_median), self.sigma, self.n_joins))
+        sizes = np.clip(np.rint(sizes), self.r_range[0], self.r_range[1]).astype(np.int64)
+        bands = rng.integers(0, len(self.bands), self.n_joins)
+        out = []
+        for j in range(self.n_joins):
+            lo, hi = self.bands[bands[j]]
+            m = int(sizes[j])
+            out.append(JoinSpec(m=m, n=self.s_factor * m, r_len=(lo, hi), s_len=(lo, hi), alphabet=self.alphabet,
+                                frac_copy=self.frac_copy, seed=self.seed * 1_000_003 + j))
+        return out
+
+
+@dataclasses.dataclass
+class BatchWorkload:
+    spec: BatchSpec
+    R: Relation
+    S: Relation
+    ranges: list          # (r_begin, r_end, s_begin, s_end) per join
+    expected: list        # pair count implied by the construction, per join
+    joins: list           # per-join Workload (views are not kept; for the oracle, see join_relations)
+
+    def join_relations(self, j: int):
+        """R and S of join j as stand-alone relations (ids = join-local rows)."""
+        rb, re_, sb, se = self.ranges[j]
+        def sub(rel, a, b):
+            off = rel.off[a:b + 1]
+            base = int(off[0])
+            arena = rel.arena[base: int(off[-1])]
+            pad = np.zeros(padded_size(arena.shape[0]), dtype=np.uint8)
+            pad[: arena.shape[0]] = arena
+            return Relation(pad, (off - np.uint64(base)).astype(np.uint64), np.arange(b - a, dtype=np.uint32))
+        return sub(self.R, rb, re_), sub(self.S, sb, se)
+
+
+def generate_batch(spec: BatchSpec, nthreads: int | None = None, alloc=None) -> BatchWorkload:
+    """Generate every join and pack them into one R and one S relation."""
+    specs = spec.joins()
+    parts = [generate(js, nthreads=nthreads) for js in specs]
+    mR = sum(p.R.n for p in parts)
+    nS = sum(p.S.n for p in parts)
+    bR = sum(p.R.nbytes for p in parts)
+    bS = sum(p.S.nbytes for p in parts)
+
+    def _arena(nb):
+        size = padded_size(nb)
+        a = np.empty(size, dtype=np.uint8) if alloc is None else alloc(size)
+        a[nb:size] = 0
+        return a
+
+    aR, aS = _arena(bR), _arena(bS)
+    offR = np.zeros(mR + 1, dtype=np.uint64)
+    offS = np.zeros(nS + 1, dtype=np.uint64)
+    ranges, expected = [], []
+    r0 = s0 = 0
+    pr = ps = 0
+    for p in parts:
+        aR[pr: pr + p.R.nbytes] = p.R.arena[: p.R.nbytes]
+        aS[ps: ps + p.S.nbytes] = p.S.arena[: p.S.nbytes]
+        offR[r0: r0 + p.R.n + 1] = p.R.off + np.uint64(pr)
+        offS[s0: s0 + p.S.n + 1] = p.S.off + np.uint64(ps)
+        ranges.append((r0, r0 + p.R.n, s0, s0 + p.S.n))
+        expected.append(p.expected_pairs())
+        r0 += p.R.n
+        s0 += p.S.n
+        pr += p.R.nbytes
+        ps += p.S.nbytes
+    R = Relation(aR, offR, np.arange(mR, dtype=np.uint32))
+    S = Relation(aS, offS, np.arange(nS, dtype=np.uint32))
+    return BatchWorkload(spec, R, S, ranges, expected, [])
