@@ -195,6 +195,9 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
  * pair_cap) of d_pairs, with its pair count in d_counts[j].  Pair ids are
  * the relations' ids if given, else row numbers relative to the join's first
  * row.  Per join the result is exactly that of as_join on the join's rows.
+ * Only the rows inside the joins' ranges are read, so a batch may pick any
+ * ordered subset of joins out of a larger resident pool (mR / nS are the
+ * pool relations' sizes).
  */
 typedef struct as_join_desc {
     uint64_t r_begin, r_end;
@@ -203,7 +206,8 @@ typedef struct as_join_desc {
     uint64_t pair_cap;
 } as_join_desc;
 
-/* Prepared batch: device descriptors and workspace regions (plain data). */
+/* Prepared batch: device descriptors and workspace regions (plain data).
+ * mR / nS here count the rows of the batch's joins only. */
 typedef struct as_batch {
     void* descs;
     uint64_t* slots;

@@ -50,26 +50,105 @@ constexpr size_t kSmemSig = kSmemTables + kConstBytes + kSmemBufs;
 static_assert(kConstEntries == 21 * 512, "constant table size");
 
 // ----------------------------------------------------------------------------
+// Batches of joins
+// ----------------------------------------------------------------------------
+//
+// A batch runs independent joins whose relations are row ranges of one packed
+// R and one packed S relation (for example a pool of resident requests).  The
+// kernels work on the virtual concatenation of the batch's ranges: virtual R
+// row v of join j is actual row r_begin + (v - vr); signatures are stored by
+// virtual row.  A single join is the batch of one join covering all rows.
+// Join j owns the table slots [slot_off, slot_off + mask] and the output
+// region [pair_off, pair_off + pair_cap) with counter counts[j].  Descriptor
+// nj (one past the last) holds the totals: vr = rows of R, vs = rows of S,
+// vbr / vbs = key bytes of R / S.
+struct BatchJoin {
+  uint64_t r_begin, r_end, s_begin, s_end;   // actual rows
+  uint64_t vr, vs;                           // first virtual R / S row
+  uint64_t vbr, vbs;                         // first virtual R / S key byte (set on the device)
+  uint64_t slot_off, mask;
+  uint64_t pair_off, pair_cap;
+};
+
+// join of virtual row v: the last j with v_j <= v (joins with no rows are skipped)
+template <bool S_SIDE>
+__device__ __forceinline__ int join_of_virtual(const BatchJoin* __restrict__ J, int nj, uint64_t v) {
+  int lo = 0, hi = nj - 1, ans = 0;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const uint64_t b = S_SIDE ? __ldg(&J[mid].vs) : __ldg(&J[mid].vr);
+    if (b <= v) { ans = mid; lo = mid + 1; } else { hi = mid - 1; }
+  }
+  return ans;
+}
+
+// join whose virtual byte range holds byte `t` (last j with vb_j <= t)
+template <bool S_SIDE>
+__device__ __forceinline__ int join_of_vbyte(const BatchJoin* __restrict__ J, int nj, uint64_t t) {
+  int lo = 0, hi = nj - 1, ans = 0;
+  while (lo <= hi) {
+    const int mid = (lo + hi) >> 1;
+    const uint64_t b = S_SIDE ? __ldg(&J[mid].vbs) : __ldg(&J[mid].vbr);
+    if (b <= t) { ans = mid; lo = mid + 1; } else { hi = mid - 1; }
+  }
+  return ans;
+}
+
+// virtual byte starts of every join's keys: one block, prefix over joins
+__global__ void batch_bytes_kernel(BatchJoin* J, int nj, const uint64_t* __restrict__ offR,
+                                   const uint64_t* __restrict__ offS) {
+  __shared__ uint64_t carry_r, carry_s;
+  __shared__ uint64_t wr[32], wsum[32];
+  if (threadIdx.x == 0) { carry_r = 0; carry_s = 0; }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int base = 0; base < nj; base += blockDim.x) {
+    const int j = base + (int)threadIdx.x;
+    uint64_t br = 0, bs = 0;
+    if (j < nj) {
+      br = offR ? offR[J[j].r_end] - offR[J[j].r_begin] : 0;
+      bs = offS ? offS[J[j].s_end] - offS[J[j].s_begin] : 0;
+    }
+    uint64_t ir = br, is = bs;                     // inclusive warp scans
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t tr = __shfl_up_sync(kFull, ir, d), ts = __shfl_up_sync(kFull, is, d);
+      if (lane >= d) { ir += tr; is += ts; }
+    }
+    if (lane == 31) { wr[w] = ir; wsum[w] = is; }
+    __syncthreads();
+    if (threadIdx.x == 0) {                        // exclusive scan of warp totals
+      uint64_t ar = carry_r, as = carry_s;
+      for (int i = 0; i < nw; i++) {
+        const uint64_t tr = wr[i], ts = wsum[i];
+        wr[i] = ar; wsum[i] = as;
+        ar += tr; as += ts;
+      }
+      carry_r = ar; carry_s = as;
+    }
+    __syncthreads();
+    if (j < nj) {
+      J[j].vbr = wr[w] + ir - br;
+      J[j].vbs = wsum[w] + is - bs;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    J[nj].vbr = carry_r;
+    J[nj].vbs = carry_s;
+  }
+}
+
+// ----------------------------------------------------------------------------
 // Signature kernel
 // ----------------------------------------------------------------------------
 
-__global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restrict__ arena,
-                                                          const uint64_t* __restrict__ off, uint64_t n,
-                                                          uint64_t* __restrict__ sig_out) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
-  uint16_t* ctab = reinterpret_cast<uint16_t*>(smem + kSmemTables);
-  for (int i = threadIdx.x; i < kConstEntries / 2; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(ctab)[i] = reinterpret_cast<const uint32_t*>(g_const)[i];
-  init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
+// Signatures of actual keys [k_lo, k_hi) of one relation; key k's signature
+// goes to sig_out[k + out_shift] (out_shift = virtual minus actual row).
+__device__ __forceinline__ void sig_walk(const uint8_t* __restrict__ arena, const uint64_t* __restrict__ off,
+                                         uint64_t k_lo, uint64_t k_hi, uint64_t out_shift,
+                                         uint64_t* __restrict__ sig_out, uint8_t* bufs, const uint16_t* ctab,
+                                         const RedCursor& rc) {
   const int lane = threadIdx.x & 31;
-  const int wib = threadIdx.x >> 5;
-  const RedCursor rc = red_cursor(red);
-  uint8_t* bufs = smem + kSmemTables + kConstBytes + (size_t)wib * 2 * kBufBytes;
-  const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
-  const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
-  uint64_t k_lo, k_hi;
-  warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
   // rounds r and r+1 are in flight before round r is computed
   Plan cur = plan_round(plan_load(off, k_lo, k_hi), k_lo, k_hi, 0);
   issue_span(bufs, arena, cur);
@@ -94,7 +173,7 @@ __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restr
       const uint64_t P = pending_value(pd);
       if (pd.complete) {
         const uint64_t s = lo_correct(ctab, P, pd.lo, rc);
-        if (lane == 0) sig_out[pd.key] = s;
+        if (lane == 0) sig_out[pd.key + out_shift] = s;
       } else {
         carry = P;
       }
@@ -102,7 +181,8 @@ __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restr
     }
     const bool head = cur.active && (uint32_t)lane == cur.slot0;
     const bool fresh = cur.q != 0 || cur.tc == 0;   // the key's first tile is in this round
-    if (head && fresh && cur.slot0 + cur.rq <= 32u) sig_out[cur.kc + (uint64_t)cur.q] = lo_correct(ctab, V, cur.lo, rc);
+    if (head && fresh && cur.slot0 + cur.rq <= 32u)
+      sig_out[cur.kc + (uint64_t)cur.q + out_shift] = lo_correct(ctab, V, cur.lo, rc);
     if (cur.tc > 0) {                               // group 0 continues a key: x^(k e) B, finished next round
       pd.valid = true;
       pd.key = cur.kc;
@@ -119,9 +199,69 @@ __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restr
   if (pd.valid) {                                   // the range's last key, if it was deferred
     pending_alogs(pd);
     const uint64_t s = lo_correct(ctab, pending_value(pd), pd.lo, rc);
-    if (lane == 0) sig_out[pd.key] = s;
+    if (lane == 0) sig_out[pd.key + out_shift] = s;
   }
   cp_async_wait_all();
+}
+
+// first actual key of join j whose start lies at or after virtual byte t
+// (t inside join j's byte range), as a virtual row
+template <bool S_SIDE>
+__device__ __forceinline__ uint64_t vcut_in_join(const BatchJoin* J, const uint64_t* off, int j, uint64_t t) {
+  const uint64_t b = S_SIDE ? __ldg(&J[j].s_begin) : __ldg(&J[j].r_begin);
+  const uint64_t e = S_SIDE ? __ldg(&J[j].s_end) : __ldg(&J[j].r_end);
+  const uint64_t vb = S_SIDE ? __ldg(&J[j].vbs) : __ldg(&J[j].vbr);
+  const uint64_t v0 = S_SIDE ? __ldg(&J[j].vs) : __ldg(&J[j].vr);
+  const uint64_t k = b + warp_lower_bound(off + b, e - b, off[b] + (t - vb));
+  return v0 + (k - b);
+}
+
+// Signatures of all keys of a relation (J == nullptr), or of the rows of a
+// batch's joins (S_SIDE picks the relation), byte-balanced over the warps.
+template <bool S_SIDE>
+__global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restrict__ arena,
+                                                          const uint64_t* __restrict__ off, uint64_t n,
+                                                          uint64_t* __restrict__ sig_out,
+                                                          const BatchJoin* __restrict__ J, int nj) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  uint16_t* ctab = reinterpret_cast<uint16_t*>(smem + kSmemTables);
+  for (int i = threadIdx.x; i < kConstEntries / 2; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ctab)[i] = reinterpret_cast<const uint32_t*>(g_const)[i];
+  init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
+  const int wib = threadIdx.x >> 5;
+  const RedCursor rc = red_cursor(red);
+  uint8_t* bufs = smem + kSmemTables + kConstBytes + (size_t)wib * 2 * kBufBytes;
+  const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
+  if (!J) {
+    uint64_t k_lo, k_hi;
+    warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
+    sig_walk(arena, off, k_lo, k_hi, 0, sig_out, bufs, ctab, rc);
+    return;
+  }
+  // batch: this warp's share of the virtual bytes, as virtual rows [v_lo, v_hi)
+  const uint64_t vrows = S_SIDE ? __ldg(&J[nj].vs) : __ldg(&J[nj].vr);
+  const uint64_t vbytes = S_SIDE ? __ldg(&J[nj].vbs) : __ldg(&J[nj].vbr);
+  auto vcut = [&](uint64_t w) -> uint64_t {
+    if (w == 0) return 0;
+    if (w >= nwarps) return vrows;
+    const uint64_t t = (uint64_t)((unsigned __int128)vbytes * w / nwarps);
+    if (t >= vbytes) return vrows;
+    return vcut_in_join<S_SIDE>(J, off, join_of_vbyte<S_SIDE>(J, nj, t), t);
+  };
+  const uint64_t v_lo = vcut(warp), v_hi = warp + 1 >= nwarps ? vrows : vcut(warp + 1);
+  // walk the pieces of [v_lo, v_hi) that fall in each join
+  uint64_t v = v_lo;
+  while (v < v_hi) {
+    const int j = join_of_virtual<S_SIDE>(J, nj, v);
+    const uint64_t b = S_SIDE ? __ldg(&J[j].s_begin) : __ldg(&J[j].r_begin);
+    const uint64_t e = S_SIDE ? __ldg(&J[j].s_end) : __ldg(&J[j].r_end);
+    const uint64_t v0 = S_SIDE ? __ldg(&J[j].vs) : __ldg(&J[j].vr);
+    const uint64_t vend = v0 + (e - b) < v_hi ? v0 + (e - b) : v_hi;
+    sig_walk(arena, off, b + (v - v0), b + (vend - v0), v0 - b, sig_out, bufs, ctab, rc);
+    v = vend;
+  }
 }
 
 // ----------------------------------------------------------------------------
@@ -141,48 +281,24 @@ __device__ __forceinline__ uint32_t len32(uint64_t len) {
   return len < 0xFFFFFFFEull ? (uint32_t)len : 0xFFFFFFFEu;
 }
 
-// A batch of independent joins over one concatenated R and one concatenated
-// S relation: join j owns R rows [r_begin, r_end), S rows [s_begin, s_end),
-// its own table (slots [slot_off, slot_off + mask + 1)) and its own output
-// region (pairs [pair_off, pair_off + pair_cap), counter counts[j]).
-struct BatchJoin {
-  uint64_t r_begin, r_end, s_begin, s_end;
-  uint64_t slot_off, mask;
-  uint64_t pair_off, pair_cap;
-};
-
-// join owning `row` (rows outside every join: -1); joins are ordered by row ranges
-template <bool S_SIDE>
-__device__ __forceinline__ int find_join(const BatchJoin* __restrict__ J, int nj, uint64_t row) {
-  int lo = 0, hi = nj - 1, ans = -1;
-  while (lo <= hi) {
-    const int mid = (lo + hi) >> 1;
-    const uint64_t b = S_SIDE ? __ldg(&J[mid].s_begin) : __ldg(&J[mid].r_begin);
-    if (b <= row) { ans = mid; lo = mid + 1; } else { hi = mid - 1; }
-  }
-  if (ans >= 0) {
-    const uint64_t e = S_SIDE ? __ldg(&J[ans].s_end) : __ldg(&J[ans].r_end);
-    if (row >= e) ans = -1;
-  }
-  return ans;
-}
-
-// Insert R rows.  Single join: J == nullptr, the table is slots[0..mask].
+// Insert R rows (batch: the m virtual rows of the joins).  Single join:
+// J == nullptr, the table is slots[0..mask].
 __global__ void build_kernel(Slot* __restrict__ slots, uint64_t mask, const uint64_t* __restrict__ sigR,
                              const uint64_t* __restrict__ offR, uint64_t m, uint32_t* __restrict__ flags,
                              const BatchJoin* __restrict__ J, int nj) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t row = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; row < m; row += stride) {
+  for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < m; v += stride) {
     Slot* tab = slots;
     uint64_t msk = mask;
+    uint64_t row = v;                                 // batch: virtual row v -> actual row
     if (J) {
-      const int j = find_join<false>(J, nj, row);
-      if (j < 0) continue;
+      const int j = join_of_virtual<false>(J, nj, v);
+      row = __ldg(&J[j].r_begin) + (v - __ldg(&J[j].vr));
       tab = slots + __ldg(&J[j].slot_off);
       msk = __ldg(&J[j].mask);
     }
     const uint64_t len = offR[row + 1] - offR[row];
-    const uint64_t sig = sigR[row];
+    const uint64_t sig = sigR[v];
     const uint64_t word = ((uint64_t)len32(len) << 32) | row;
     uint64_t b = sig_hash(sig, len) & msk;
     bool placed = false;
@@ -316,24 +432,22 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
   const uint64_t ngroups = (P.n + 31) / 32;
   const uint64_t nwarps = (uint64_t)gridDim.x * kVWarps;
   for (uint64_t grp = (uint64_t)blockIdx.x * kVWarps + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
-    const uint64_t i = grp * 32 + (uint64_t)lane;
-    bool live = i < P.n;
+    const uint64_t vi = grp * 32 + (uint64_t)lane;   // virtual S row (= actual row for one join)
+    bool live = vi < P.n;
     const Slot* slots = P.slots;
     uint64_t mask = P.mask;
+    uint64_t i = vi;
     int jn = 0;                                      // batch: join of the lane's S row
     if (batch && live) {
-      jn = find_join<true>(P.J, P.nj, i);
-      if (jn < 0) {
-        live = false;
-      } else {
-        slots = P.slots + __ldg(&P.J[jn].slot_off);
-        mask = __ldg(&P.J[jn].mask);
-      }
+      jn = join_of_virtual<true>(P.J, P.nj, vi);
+      i = __ldg(&P.J[jn].s_begin) + (vi - __ldg(&P.J[jn].vs));
+      slots = P.slots + __ldg(&P.J[jn].slot_off);
+      mask = __ldg(&P.J[jn].mask);
     }
     uint64_t sig = 0, start = 0, len = 0, b = 0, steps = 0;
     uint32_t l32 = 0;
     if (live) {
-      sig = __ldg(P.sigS + i);
+      sig = __ldg(P.sigS + vi);
       start = __ldg(P.offS + i);
       len = __ldg(P.offS + i + 1) - start;
       b = sig_hash(sig, len) & mask;
@@ -362,6 +476,7 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         const uint32_t rj = __shfl_sync(kFull, row, j);
         const uint64_t lj = __shfl_sync(kFull, len, j);
         const uint64_t stj = __shfl_sync(kFull, start, j);
+        const uint64_t srow = __shfl_sync(kFull, i, j);
         const uint64_t rs = __ldg(P.offR + rj);
         const uint64_t rl = __ldg(P.offR + rj + 1) - rs;
         if (rl == lj && warp_equal(P.arenaR + rs, P.arenaS + stj, lj)) {
@@ -372,7 +487,6 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
           }
           sj = jj;
           if (lane == 0) {
-            const uint64_t srow = grp * 32 + (uint64_t)j;
             const uint32_t rid = P.idR ? __ldg(P.idR + rj) : (uint32_t)(rj - (batch ? __ldg(&P.J[jj].r_begin) : 0));
             const uint32_t sid = P.idS ? __ldg(P.idS + srow) : (uint32_t)(srow - (batch ? __ldg(&P.J[jj].s_begin) : 0));
             stage[np] = (uint64_t)rid | ((uint64_t)sid << 32);
@@ -617,7 +731,10 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaMemcpyToSymbol(g_const, h_const, sizeof(h_const))) != cudaSuccess) return cuda_fail(e, "table setup");
     if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return cuda_fail(e, "device query");
-    if ((e = cudaFuncSetAttribute(sig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
+    if ((e = cudaFuncSetAttribute(sig_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
+        cudaSuccess)
+      return cuda_fail(e, "kernel attribute");
+    if ((e = cudaFuncSetAttribute(sig_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
     if ((e = cudaFuncSetAttribute(bl_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBHash)) !=
@@ -666,7 +783,7 @@ static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t 
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
   if (n == 0) return AS_OK;
-  sig_kernel<<<walk_blocks(n, d->sms), kThreads, kSmemSig, s>>>(arena, off, n, out);
+  sig_kernel<false><<<walk_blocks(n, d->sms), kThreads, kSmemSig, s>>>(arena, off, n, out, nullptr, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "signature kernel launch");
   return AS_OK;
@@ -855,26 +972,31 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
 // Batches of independent joins
 // ----------------------------------------------------------------------------
 
-static_assert(sizeof(BatchJoin) == 64, "BatchJoin layout");
+static_assert(sizeof(BatchJoin) == 96, "BatchJoin layout");
 
-// layout of a batch workspace: descriptors | slots | sigR | sigS | flags
+// layout of a batch workspace: descriptors (n_joins + 1) | slots | sigR | sigS | flags
 static bool batch_layout(const as_join_desc* descs, int nj, uint64_t mR, uint64_t nS, float lf,
-                         uint64_t* slots_total, uint64_t* bytes) {
+                         uint64_t* slots_total, uint64_t* vr, uint64_t* vs, uint64_t* bytes) {
   if (nj < 1 || !descs || !(lf > 0.0f && lf <= 1.0f) || mR >= 0xFFFFFFFFull) return false;
-  uint64_t tot = 0, prev_r = 0, prev_s = 0;
+  uint64_t tot = 0, prev_r = 0, prev_s = 0, sr = 0, ss = 0;
   for (int j = 0; j < nj; j++) {
     const as_join_desc& d = descs[j];
     if (d.r_begin > d.r_end || d.s_begin > d.s_end || d.r_end > mR || d.s_end > nS) return false;
-    if (d.r_begin < prev_r || d.s_begin < prev_s) return false;     // ordered, non-overlapping
+    if (d.r_begin < prev_r || d.s_begin < prev_s) return false;     // ordered, not overlapping
     prev_r = d.r_end;
     prev_s = d.s_end;
     uint64_t cap;
     uint32_t l2;
     if (!table_geometry(d.r_end - d.r_begin, lf, &cap, &l2)) return false;
     tot += cap;
+    sr += d.r_end - d.r_begin;
+    ss += d.s_end - d.s_begin;
   }
   *slots_total = tot;
-  *bytes = round256((uint64_t)nj * sizeof(BatchJoin)) + round256(tot * 16) + round256(mR * 8) + round256(nS * 8) + 256;
+  *vr = sr;
+  *vs = ss;
+  *bytes = round256((uint64_t)(nj + 1) * sizeof(BatchJoin)) + round256(tot * 16) + round256(sr * 8) +
+           round256(ss * 8) + 256;
   return true;
 }
 
@@ -967,16 +1089,16 @@ as_status as_baseline_join(const uint8_t* d_arenaR, const uint64_t* d_offR, cons
 }
 
 size_t as_join_batch_ws_bytes(const as_join_desc* descs, int n_joins, uint64_t mR, uint64_t nS, float load_factor) {
-  uint64_t tot, bytes;
-  if (!batch_layout(descs, n_joins, mR, nS, load_factor, &tot, &bytes)) return 0;
+  uint64_t tot, vr, vs, bytes;
+  if (!batch_layout(descs, n_joins, mR, nS, load_factor, &tot, &vr, &vs, &bytes)) return 0;
   return (size_t)bytes;
 }
 
 as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t mR, uint64_t nS, float load_factor,
                                 void* d_ws, size_t ws_bytes, as_batch* out, as_stream stream) {
   if (!out) return fail(AS_ERR_INVALID, "as_join_batch_prepare: null batch");
-  uint64_t tot, bytes;
-  if (!batch_layout(descs, n_joins, mR, nS, load_factor, &tot, &bytes))
+  uint64_t tot, vr, vs, bytes;
+  if (!batch_layout(descs, n_joins, mR, nS, load_factor, &tot, &vr, &vs, &bytes))
     return fail(AS_ERR_INVALID, "as_join_batch_prepare: bad descriptors or load factor");
   if (!d_ws || ws_bytes < bytes)
     return fail(AS_ERR_NOMEM, "as_join_batch_prepare: workspace of %zu bytes, need %llu", ws_bytes,
@@ -985,41 +1107,53 @@ as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t
   DeviceState* d = nullptr;
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
-  std::vector<BatchJoin> h(n_joins);
-  uint64_t off = 0;
+  std::vector<BatchJoin> h(n_joins + 1);
+  uint64_t off = 0, v_r = 0, v_s = 0;
   for (int j = 0; j < n_joins; j++) {
     uint64_t cap;
     uint32_t l2;
     table_geometry(descs[j].r_end - descs[j].r_begin, load_factor, &cap, &l2);
-    h[j].r_begin = descs[j].r_begin;
-    h[j].r_end = descs[j].r_end;
-    h[j].s_begin = descs[j].s_begin;
-    h[j].s_end = descs[j].s_end;
-    h[j].slot_off = off;
-    h[j].mask = cap - 1;
-    h[j].pair_off = descs[j].pair_offset;
-    h[j].pair_cap = descs[j].pair_cap;
+    BatchJoin& b = h[j];
+    b.r_begin = descs[j].r_begin;
+    b.r_end = descs[j].r_end;
+    b.s_begin = descs[j].s_begin;
+    b.s_end = descs[j].s_end;
+    b.vr = v_r;
+    b.vs = v_s;
+    b.vbr = b.vbs = 0;
+    b.slot_off = off;
+    b.mask = cap - 1;
+    b.pair_off = descs[j].pair_offset;
+    b.pair_cap = descs[j].pair_cap;
     off += cap;
+    v_r += b.r_end - b.r_begin;
+    v_s += b.s_end - b.s_begin;
   }
+  BatchJoin& t = h[n_joins];                       // totals
+  memset(&t, 0, sizeof(t));
+  t.vr = v_r;
+  t.vs = v_s;
+  t.r_begin = t.r_end = mR;
+  t.s_begin = t.s_end = nS;
   uint8_t* ws = (uint8_t*)d_ws;
   cudaError_t e;
-  if ((e = cudaMemcpyAsync(ws, h.data(), sizeof(BatchJoin) * n_joins, cudaMemcpyHostToDevice, (cudaStream_t)stream)) !=
-      cudaSuccess)
+  if ((e = cudaMemcpyAsync(ws, h.data(), sizeof(BatchJoin) * (n_joins + 1), cudaMemcpyHostToDevice,
+                           (cudaStream_t)stream)) != cudaSuccess)
     return cuda_fail(e, "batch descriptors");
   if ((e = cudaStreamSynchronize((cudaStream_t)stream)) != cudaSuccess) return cuda_fail(e, "batch descriptors");
-  uint64_t o = round256((uint64_t)n_joins * sizeof(BatchJoin));
+  uint64_t o = round256((uint64_t)(n_joins + 1) * sizeof(BatchJoin));
   out->descs = ws;
   out->slots = reinterpret_cast<uint64_t*>(ws + o);
   o += round256(tot * 16);
   out->sigR = reinterpret_cast<uint64_t*>(ws + o);
-  o += round256(mR * 8);
+  o += round256(vr * 8);
   out->sigS = reinterpret_cast<uint64_t*>(ws + o);
-  o += round256(nS * 8);
+  o += round256(vs * 8);
   out->flags = reinterpret_cast<uint32_t*>(ws + o);
   out->n_joins = (uint64_t)n_joins;
   out->slots_total = tot;
-  out->mR = mR;
-  out->nS = nS;
+  out->mR = vr;
+  out->nS = vs;
   return AS_OK;
 }
 
@@ -1027,9 +1161,8 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
                             const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint32_t* d_pairs,
                             uint64_t* d_counts, as_stream stream) {
   if (!b || !b->descs || !d_counts) return fail(AS_ERR_INVALID, "as_join_batch_run: null batch or counters");
-  if ((b->mR > 0 && (!d_arenaR || !d_offR)) || (b->nS > 0 && (!d_arenaS || !d_offS)))
-    return fail(AS_ERR_INVALID, "as_join_batch_run: null relation");
-  if ((b->mR > 0 && misaligned16(d_arenaR)) || (b->nS > 0 && misaligned16(d_arenaS)))
+  if (!d_arenaR || !d_offR || !d_arenaS || !d_offS) return fail(AS_ERR_INVALID, "as_join_batch_run: null relation");
+  if (misaligned16(d_arenaR) || misaligned16(d_arenaS))
     return fail(AS_ERR_INVALID, "as_join_batch_run: arena not 16-byte aligned");
   if (d_pairs && (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
     return fail(AS_ERR_INVALID, "as_join_batch_run: pair buffer not 8-byte aligned");
@@ -1038,22 +1171,22 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
   if (st != AS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
-  const BatchJoin* J = reinterpret_cast<const BatchJoin*>(b->descs);
+  BatchJoin* J = reinterpret_cast<BatchJoin*>(b->descs);
   const int nj = (int)b->n_joins;
   Slot* slots = reinterpret_cast<Slot*>(b->slots);
   if ((e = cudaMemsetAsync(slots, 0xFF, b->slots_total * 16, s)) != cudaSuccess) return cuda_fail(e, "table clear");
   if ((e = cudaMemsetAsync(b->flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
   if ((e = cudaMemsetAsync(d_counts, 0, 8 * b->n_joins, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  batch_bytes_kernel<<<1, 1024, 0, s>>>(J, nj, d_offR, d_offS);
   if (b->mR > 0) {
-    sig_kernel<<<walk_blocks(b->mR, d->sms), kThreads, kSmemSig, s>>>(d_arenaR, d_offR, b->mR, b->sigR);
+    sig_kernel<false><<<walk_blocks(b->mR, d->sms), kThreads, kSmemSig, s>>>(d_arenaR, d_offR, b->mR, b->sigR, J, nj);
     uint64_t blocks = (b->mR + 255) / 256;
     const uint64_t lim = (uint64_t)d->sms * 16;
     if (blocks > lim) blocks = lim;
     build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, 0, b->sigR, d_offR, b->mR, b->flags, J, nj);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch build launch");
   }
   if (b->nS > 0) {
-    sig_kernel<<<walk_blocks(b->nS, d->sms), kThreads, kSmemSig, s>>>(d_arenaS, d_offS, b->nS, b->sigS);
+    sig_kernel<true><<<walk_blocks(b->nS, d->sms), kThreads, kSmemSig, s>>>(d_arenaS, d_offS, b->nS, b->sigS, J, nj);
     VerifyParams P;
     P.slots = slots;
     P.mask = 0;
@@ -1075,8 +1208,8 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
     const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
     if (blocks > lim) blocks = lim;
     verify_kernel<<<(unsigned)blocks, kVThreads, 0, s>>>(P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch probe launch");
   }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch launch");
   return AS_OK;
 }
 

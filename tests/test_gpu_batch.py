@@ -71,3 +71,36 @@ def test_batch_graph_replay_and_ids(cuda, batch):
         want[:, 0] += rb
         want[:, 1] += sb
         assert np.array_equal(first[j].astype(np.int64), want)
+
+
+def test_batch_subset_of_pool(cuda, batch):
+    """A batch that picks a few joins out of the resident pool (gaps between
+    them, one join with no R rows, one with no S rows) reads only those rows."""
+    ag = cuda
+    Rd, Sd = dev(ag, batch.R), dev(ag, batch.S)
+    R = ag.DeviceRelation(Rd.arena, Rd.off, None)
+    S = ag.DeviceRelation(Sd.arena, Sd.off, None)
+    pick = [1, 4, 5, 11, 17, 23]
+    ranges = [batch.ranges[j] for j in pick]
+    r0, r1, s0, s1 = ranges[2]
+    ranges[2] = (r0, r0, s0, s1)                      # empty R side
+    r0, r1, s0, s1 = ranges[4]
+    ranges[4] = (r0, r1, s0, s0)                      # empty S side
+    caps = [max(64, 2 * batch.expected[j] + 64) for j in pick]
+    out = ag.join_batch(R, S, ranges, caps, load_factor=0.5)
+    for k, (rb, re_, sb, se) in enumerate(ranges):
+        Rj = workloads.relation_from_keys([batch.R.key(i) for i in range(rb, re_)])
+        Sj = workloads.relation_from_keys([batch.S.key(i) for i in range(sb, se)])
+        want = oracle.join_simple(Rj, Sj)
+        got = oracle.sort_pairs(out[k].cpu().numpy().view(np.uint32))
+        assert np.array_equal(got, want), k
+
+
+def test_batch_single_join_equals_join(cuda, batch):
+    ag = cuda
+    Rd, Sd = dev(ag, batch.R), dev(ag, batch.S)
+    R = ag.DeviceRelation(Rd.arena, Rd.off, None)
+    S = ag.DeviceRelation(Sd.arena, Sd.off, None)
+    solo = oracle.sort_pairs(ag.join(R, S).cpu().numpy().view(np.uint32))
+    got = ag.join_batch(R, S, [(0, R.n, 0, S.n)], [len(solo) + 64])[0]
+    assert np.array_equal(oracle.sort_pairs(got.cpu().numpy().view(np.uint32)), solo)

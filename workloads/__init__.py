@@ -24,7 +24,7 @@ _SO = os.path.join(_HERE, "_build", "libgen.so")
 _lock = threading.Lock()
 _lib = None
 
-ALPHABETS = {"printable": 0, "acgt": 1, "alnum": 2, "bytes": 3}
+ALPHABETS = {"printable": 0, "acgt": 1, "alnum": 2, "bytes": 3, "xml": 4}
 
 
 class _Spec(ctypes.Structure):

@@ -23,7 +23,7 @@ typedef struct {
     uint64_t m, n;                 /* |R|, |S| */
     uint32_t r_len_lo, r_len_hi;   /* R key length, uniform inclusive */
     uint32_t s_len_lo, s_len_hi;   /* fresh S key length, uniform inclusive */
-    int32_t alphabet;              /* 0 printable 0x20..0x7E, 1 ACGT, 2 alnum, 3 any byte */
+    int32_t alphabet;              /* 0 printable 0x20..0x7E, 1 ACGT, 2 alnum, 3 any byte, 4 XML-like text */
     double frac_copy;              /* S rows that are exact copies of an R key */
     double frac_near;              /* S rows that are near-duplicates of an R key */
     int32_t near_lo, near_hi;      /* changed byte positions of a near-duplicate */
@@ -86,9 +86,34 @@ static uint8_t letter(int alphabet, uint16_t u) {
     }
 }
 
+/* XML-like text: elements <t>text</t> with a tag t of 3..12 letters a..z and
+   alphanumeric text of 1..64 characters, concatenated while they fit, then
+   alphanumeric characters up to exactly len bytes */
+static void xml_bytes(const gen_spec* sp, uint64_t tagbase, uint64_t ident, uint8_t* dst, uint64_t len) {
+    uint64_t pos = 0, ctr = 0;
+    for (;;) {
+        uint64_t r = rnd(sp->seed, tagbase, ident, ctr++);
+        uint64_t tl = 3 + r % 10, cl = 1 + (r >> 8) % 64;
+        uint64_t need = 2 * tl + cl + 5;   /* <t> text </t> */
+        if (pos + need > len) break;
+        uint8_t tagname[12];
+        for (uint64_t i = 0; i < tl; i++) tagname[i] = (uint8_t)('a' + rnd(sp->seed, tagbase, ident, ctr++) % 26);
+        dst[pos++] = '<';
+        for (uint64_t i = 0; i < tl; i++) dst[pos++] = tagname[i];
+        dst[pos++] = '>';
+        for (uint64_t i = 0; i < cl; i++) dst[pos++] = letter(2, (uint16_t)rnd(sp->seed, tagbase, ident, ctr++));
+        dst[pos++] = '<';
+        dst[pos++] = '/';
+        for (uint64_t i = 0; i < tl; i++) dst[pos++] = tagname[i];
+        dst[pos++] = '>';
+    }
+    while (pos < len) dst[pos++] = letter(2, (uint16_t)rnd(sp->seed, tagbase, ident, ctr++));
+}
+
 /* bytes of the key with identity (rel, ident), written to dst[0..len) */
 static void key_bytes(const gen_spec* sp, uint64_t rel, uint64_t ident, uint8_t* dst, uint64_t len) {
     uint64_t tag = T_BYTE + 16 * rel;
+    if (sp->alphabet == 4) { xml_bytes(sp, tag, ident, dst, len); return; }
     for (uint64_t j = 0; j < len; j += 4) {
         uint64_t r = rnd(sp->seed, tag, ident, j >> 2);
         for (int q = 0; q < 4 && j + q < len; q++) dst[j + q] = letter(sp->alphabet, (uint16_t)(r >> (16 * q)));
