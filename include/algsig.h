@@ -258,6 +258,33 @@ as_status as_baseline_join(const uint8_t* d_arenaR, const uint64_t* d_offR, cons
                            float load_factor, int tagged, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
                            uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream);
 
+/*
+ * as_join_probe_noalloc -- as_join_probe with no workspace and no allocation
+ * of any kind.  The paper has no counterpart: it is an interface for callers
+ * that cannot allocate device memory at call time, e.g. a host engine that has
+ * handed all device memory to its own pool (a serving process whose admission
+ * budget accounts for every byte) or a latency-sensitive caller that must not
+ * reach cudaMalloc/cudaFree (cudaFree synchronises the whole device).
+ *
+ * S's signatures go to a fixed scratch array compiled into the library
+ * (AS_PROBE_NOALLOC_MAX_KEYS uint64 entries, 8 MiB per device), so:
+ *   n              : at most AS_PROBE_NOALLOC_MAX_KEYS; larger n is rejected
+ *                    with AS_ERR_INVALID before any device work
+ *   nothing has to start at zero: the scratch is written completely before
+ *   it is read, and d_count is cleared by the call itself
+ *   calls that overlap on one device (two streams, or two host threads)
+ *   share the scratch and race: serialise them, e.g. on one stream
+ * The first call on a device (with that device current) does one-time setup:
+ * the library's tables and kernel attributes, and the scratch address
+ * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * Other arguments, results and errors as for as_join_probe with
+ * d_sigS_out = NULL.
+ */
+#define AS_PROBE_NOALLOC_MAX_KEYS (1u << 20)
+as_status as_join_probe_noalloc(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                                const uint32_t* d_idS, uint64_t n, uint32_t* d_pairs, uint64_t cap_pairs,
+                                uint64_t* d_count, uint64_t* h_count, as_stream stream);
+
 #ifdef __cplusplus
 }
 #endif

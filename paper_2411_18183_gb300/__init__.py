@@ -196,6 +196,27 @@ def join_probe(t: Table, S: DeviceRelation, pairs: torch.Tensor, count: torch.Te
     return int(h.value) if sync else None
 
 
+PROBE_NOALLOC_MAX_KEYS = 1 << 20       # AS_PROBE_NOALLOC_MAX_KEYS
+
+
+def join_probe_noalloc(t: Table, S: DeviceRelation, pairs: torch.Tensor, count: torch.Tensor, sync: bool = True,
+                       stream=None) -> int | None:
+    """as_join_probe_noalloc: as join_probe, with S's signatures in the library's fixed
+    scratch (S.n <= PROBE_NOALLOC_MAX_KEYS); calls on one device must not overlap."""
+    lib = load()
+    f = lib.as_join_probe_noalloc
+    if not getattr(lib, "_noalloc_ready", False):
+        P, U64 = ctypes.c_void_p, ctypes.c_uint64
+        f.argtypes = [ctypes.POINTER(Table), P, P, P, U64, P, U64, P, P, P]
+        f.restype = ctypes.c_int
+        lib._noalloc_ready = True
+    cap = pairs.numel() // 2
+    h = ctypes.c_uint64(0)
+    _check(f(ctypes.byref(t), _ptr(S.arena), _ptr(S.off), _ptr(S.ids), S.n, _ptr(pairs),
+                                     cap, _ptr(count), ctypes.byref(h) if sync else None, _stream(stream)))
+    return int(h.value) if sync else None
+
+
 def join_into(R: DeviceRelation, S: DeviceRelation, ws: torch.Tensor, pairs: torch.Tensor, count: torch.Tensor,
               load_factor: float = 0.5, sync: bool = True, stream=None, allow_capacity: bool = False):
     """as_join into caller buffers.  Returns (status, count) when sync, else (status, None)."""

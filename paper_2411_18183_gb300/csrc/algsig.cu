@@ -1224,3 +1224,43 @@ as_status as_join_batch(const uint8_t* d_arenaR, const uint64_t* d_offR, const u
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Probe without workspace: S's signatures go to a fixed array in the module's
+// device memory instead of a caller workspace, for callers that cannot
+// allocate device memory at call time (all of it handed to their own pool, or
+// no cudaMalloc/cudaFree allowed on their path since cudaFree synchronises the
+// device).  The array is written completely before it is read, so it never
+// needs clearing; overlapping calls on one device share it and race.
+
+static __device__ __align__(256) uint64_t g_probe_noalloc_sig[AS_PROBE_NOALLOC_MAX_KEYS];
+static void* g_probe_noalloc_addr[algsig::kMaxDevices];   // per device, guarded by g_noalloc_mu
+static std::mutex g_noalloc_mu;
+
+extern "C" as_status as_join_probe_noalloc(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                                           const uint32_t* d_idS, uint64_t n, uint32_t* d_pairs,
+                                           uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count,
+                                           as_stream stream) {
+  using namespace algsig;
+  if (n > (uint64_t)AS_PROBE_NOALLOC_MAX_KEYS)
+    return fail(AS_ERR_INVALID, "as_join_probe_noalloc: %llu keys, the fixed scratch holds at most %u",
+                (unsigned long long)n, (unsigned)AS_PROBE_NOALLOC_MAX_KEYS);
+  int dev = -1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return fail(AS_ERR_UNSUPPORTED, "no CUDA device: %s", cudaGetErrorString(e));
+  if (dev < 0 || dev >= kMaxDevices) return fail(AS_ERR_UNSUPPORTED, "device index %d out of range", dev);
+  void* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_probe_noalloc_addr[dev]) {
+      // once per device, with that device current
+      if ((e = cudaGetSymbolAddress(&g_probe_noalloc_addr[dev], g_probe_noalloc_sig)) != cudaSuccess) {
+        g_probe_noalloc_addr[dev] = nullptr;
+        return cuda_fail(e, "scratch address");
+      }
+    }
+    scratch = g_probe_noalloc_addr[dev];
+  }
+  return as_join_probe(t, d_arenaS, d_offS, d_idS, n, static_cast<uint64_t*>(scratch), nullptr, 0, d_pairs,
+                       cap_pairs, d_count, h_count, stream);
+}
