@@ -186,6 +186,69 @@ def run_reference(args):
     return 0
 
 
+# --------------------------------------------------------------------------- batch and serving legs
+
+BATCH_SCALE = 100        # batch leg: the 512-join batch with relation sizes / 100
+SERVE_SCALE = 50         # serving leg: request relation sizes / 50
+SERVE_SECONDS = 2.0
+
+
+def batch_leg(ag, steps: int):
+    """512 independent joins (sizes log-normal, three key-length bands) in one
+    graph-captured launch sequence, load factor autotuned; S tuples/s."""
+    import torch
+    from paper_2411_18183_gb300 import tune
+    spec = workloads.BatchSpec().scaled(BATCH_SCALE)
+    bw = workloads.generate_batch(spec)
+    R = ag.DeviceRelation.from_host(bw.R.arena, bw.R.off, None)
+    S = ag.DeviceRelation.from_host(bw.S.arena, bw.S.off, None)
+    caps = [max(64, int(e * 1.25) + 64) for e in bw.expected]
+    gb, tried = tune.autotune(R, S, bw.ranges, caps)
+    gb.counts.zero_()
+    gb.replay()
+    torch.cuda.synchronize()
+    if gb.counts.cpu().tolist() != list(bw.expected):
+        raise SystemExit("batch leg: per-join pair counts differ from the generator's")
+    ms = gb.time_ms(reps=max(3, steps))
+    n = bw.S.n
+    return {"workload": f"{spec.n_joins} joins, |R| log-normal median {spec.r_median:g} in "
+                        f"[{spec.r_range[0]}, {spec.r_range[1]}], |S| = {spec.s_factor} |R|, key bands "
+                        f"{list(spec.bands)} B, {int(spec.frac_copy * 100)}% S copies (relation sizes of the "
+                        f"512-join batch / {BATCH_SCALE})",
+            "rows": {"R": bw.R.n, "S": n}, "key_bytes": bw.R.nbytes + bw.S.nbytes,
+            "load_factor": gb.lf, "tuning_ms": tried, "ms_per_batch": ms,
+            "joins_per_s": spec.n_joins / (ms * 1e-3), "tuples_per_s": n / (ms * 1e-3),
+            "gpu_launches_per_batch": 5, "cuda_graph": True}
+
+
+def serve_leg(ag):
+    """Poisson arrivals of join requests over a resident pool, admitted under
+    the device-memory bound, continuously batched on 4 streams."""
+    from paper_2411_18183_gb300 import serve
+    spec = workloads.SERVE_SPEC.scaled(SERVE_SCALE)
+    bw = workloads.generate_batch(spec)
+    pool = serve.DevicePool.from_batch(bw, lambda rel: ag.DeviceRelation.from_host(rel.arena, rel.off, None))
+    ex = serve.GpuExecutor(pool, n_slots=4, max_batch=64)
+    arrivals = serve.poisson_arrivals(workloads.SERVE_RATE, SERVE_SECONDS, pool.n, seed=spec.seed)
+    srv = serve.Server(ex, budget_bytes=workloads.SERVE_BUDGET_BYTES, max_batch=64)
+    srv.run(serve.poisson_arrivals(workloads.SERVE_RATE, 0.2, pool.n, seed=1))      # warm-up
+    reqs = srv.run(arrivals, timeout=120.0)
+    bad = [r.rid for r in reqs if r.count != pool.expected[r.pool_index]]
+    if bad:
+        raise SystemExit(f"serving leg: {len(bad)} requests got a wrong pair count")
+    s = serve.summarize(reqs)
+    tuples = sum(pool.ranges[r.pool_index][3] - pool.ranges[r.pool_index][2] for r in reqs)
+    s.update({"workload": f"Poisson {workloads.SERVE_RATE:g} joins/s for {SERVE_SECONDS:g} s over a pool of "
+                          f"{pool.n} joins: |R| log-normal median {spec.r_median:g}, |S| = "
+                          f"{spec.s_factor_range[0]}-{spec.s_factor_range[1]} |R|, XML-like keys "
+                          f"{spec.bands[0][0]}-{spec.bands[0][1]} B, {int(spec.frac_copy * 100)}% S copies "
+                          f"(request sizes / {SERVE_SCALE})",
+              "budget_bytes": workloads.SERVE_BUDGET_BYTES, "peak_admitted_bytes": srv.ledger.peak,
+              "batches": srv.batches, "streams": 4,
+              "tuples_per_s": tuples / s["span_s"] if s["span_s"] else None})
+    return s
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -241,23 +304,33 @@ def run_gpu(args):
     lf = args.load_factor
     ws = ag.alloc_ws(ag.join_ws_bytes(m, n, lf))
     tb = ag.join_table_bytes(m, lf)
-    pws = ws[tb + 256:]
     cap = int(max(1024, wl.expected_pairs() * 1.25 + 1024))
     pairs = torch.empty(2 * cap, dtype=torch.int32, device="cuda")
     count = ws[tb:tb + 8].view(torch.int64)
+    sigR = torch.empty(m, dtype=torch.int64, device="cuda")
+    sigS = torch.empty(n, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
 
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(args.steps)]
+    # one step = the whole signature join, as four library calls (one kernel each
+    # but the build): sig(R), build, sig(S), probe with the S signatures
+    PH = ("sig_R", "build", "sig_S", "verify")
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(PH) + 1)] for _ in range(args.steps)]
 
     def step(evs=None):
         if evs:
             evs[0].record(stream)
-        t = ag.join_build(dR, ws[:tb], lf, stream=stream)
+        ag.sig_compute(dR, sigR, stream=stream)
         if evs:
             evs[1].record(stream)
-        ag.join_probe(t, dS, pairs, count, ws=pws, sync=False, stream=stream)
+        t = ag.join_build(dR, ws[:tb], lf, sigR=sigR, stream=stream)
         if evs:
             evs[2].record(stream)
+        ag.sig_compute(dS, sigS, stream=stream)
+        if evs:
+            evs[3].record(stream)
+        ag.join_probe_sigs(t, dS, sigS, pairs, count, sync=False, stream=stream)
+        if evs:
+            evs[4].record(stream)
 
     # correctness of the timed configuration: total pairs = the generator's ground truth
     step()
@@ -283,9 +356,8 @@ def run_gpu(args):
     barrier()
     clk = clocks.stop()
     total_ms = t0.elapsed_time(t1)
-    build_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    probe_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    step_ms = [e[0].elapsed_time(e[2]) for e in ev]
+    phase_ms = {ph: [e[i].elapsed_time(e[i + 1]) for e in ev] for i, ph in enumerate(PH)}
+    step_ms = [e[0].elapsed_time(e[len(PH)]) for e in ev]
     total_ms = max_over_ranks(total_ms)
     ms_per_step = total_ms / args.steps
     value = world * n / (ms_per_step * 1e-3)
@@ -311,20 +383,7 @@ def run_gpu(args):
         baseline["tagged" if tagged else "plain"] = {"ms_per_join": bms, "tuples_per_s": n / (bms * 1e-3)}
     del bws
 
-    # signature kernel alone on S (key GB/s against HBM)
-    sig_out = torch.empty(n, dtype=torch.int64, device="cuda")
-    for _ in range(2):
-        ag.sig_compute(dS, sig_out, stream=stream)
-    s0, s1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
-    s0.record(stream)
-    for _ in range(reps):
-        ag.sig_compute(dS, sig_out, stream=stream)
-    s1.record(stream)
-    torch.cuda.synchronize()
-    sig_ms = s0.elapsed_time(s1) / reps
     hbm, peak_kind = peaks()
-    sig_gbps = (wl.S.nbytes + 16 * n) / (sig_ms * 1e-3) / 1e9
 
     # end to end through the C ABI from pinned host buffers: H2D of R and S,
     # the join, D2H of the count and the pairs
@@ -352,24 +411,39 @@ def run_gpu(args):
     e2e_s = max_over_ranks((time.perf_counter() - te) / e2e_steps)
     e2e_value = world * n / e2e_s
 
-    # roofline of the dominant kernel: the probe (S signatures + probe + verify + compaction)
-    probe_avg = statistics.mean(probe_ms)
-    lens = np.diff(wl.S.off)
+    # rooflines of the step's kernels from their live CUDA-event times (algorithmic bytes / launch)
+    lensS = np.diff(wl.S.off).astype(np.int64)
+    lensR = np.diff(wl.R.off).astype(np.int64)
     src = wl.s_src[wl.s_kind == 1]
-    verified_bytes = int((wl.r_mult[src].astype(np.int64) * lens[wl.s_kind == 1].astype(np.int64)).sum())
-    probe_alg = (wl.S.nbytes + 8 * (n + 1) + 4 * n          # S keys, offsets, ids
-                 + 8 * n                                     # one slot read per S key
-                 + total_pairs * (8 + 16 + 4)                # sigR, offR pair, idR per verified candidate
-                 + verified_bytes                            # R key bytes compared
-                 + 8 * total_pairs)                          # output pairs
-    achieved = probe_alg / (probe_avg * 1e-3) / 1e9
+    verified_bytes = int((wl.r_mult[src].astype(np.int64) * lensS[wl.s_kind == 1]).sum())
+    alg = {
+        "sig_R": wl.R.nbytes + 8 * (m + 1) + 8 * m,                    # keys, offsets, signatures out
+        "sig_S": wl.S.nbytes + 8 * (n + 1) + 8 * n,
+        "build": 8 * m + 8 * (m + 1) + 16 * m,                          # sigR, offsets, one slot per row
+        "verify": (8 * n + 8 * (n + 1) + 4 * n + 16 * n                # sig, offsets, id, first slot per S key
+                   + total_pairs * (16 + 4 + 8)                        # offR pair, idR, output pair
+                   + 2 * verified_bytes),                              # R and S key bytes compared
+    }
+    kernels = {}
+    for ph in PH:
+        avg = statistics.mean(phase_ms[ph])
+        kernels[ph] = {"ms": avg, "algorithmic_bytes": alg[ph], "gbps": alg[ph] / (avg * 1e-3) / 1e9,
+                       "frac_hbm": alg[ph] / (avg * 1e-3) / 1e9 / hbm}
+    dom = max(("sig_S", "verify"), key=lambda ph: kernels[ph]["ms"])
     traffic = None
-    tp = os.path.join(ROOT, "profiles", "probe_traffic.json")
+    tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
         with open(tp) as f:
             d = json.load(f)
-        if d.get("workload") == args.workload and d.get("kernel_rev") == KERNEL_REV:
-            traffic = d.get("bytes_per_launch")
+        ent = d.get(KERNEL_NAMES[dom], {})
+        if ent.get("kernel_rev") == KERNEL_REV and ent.get("per_byte_of_keys"):
+            keyb = wl.S.nbytes if dom == "sig_S" else 2 * verified_bytes
+            traffic = ent["per_byte_of_keys"] * keyb
+
+    extra = {}
+    if not args.no_extra:
+        extra["batch"] = batch_leg(ag, args.steps)
+        extra["serving"] = serve_leg(ag)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -386,21 +460,22 @@ def run_gpu(args):
                    "l2": f"inputs larger than L2 ({key_bytes / 1e9:.2f} GB of keys), no flush",
                    "parallelism": f"replicas{world}"},
         "p50_ms": pct(step_ms, 50), "p99_ms": pct(step_ms, 99),
-        "build_ms": statistics.mean(build_ms), "probe_ms": probe_avg,
-        "probe_only_tuples_per_s": n / (probe_avg * 1e-3),
+        "probe_tuples_per_s_probe_phase": n / ((kernels["sig_S"]["ms"] + kernels["verify"]["ms"]) * 1e-3),
         "key_gbps": key_bytes / (ms_per_step * 1e-3) / 1e9,
-        "sig_kernel": {"gbps": sig_gbps, "frac_hbm": sig_gbps / hbm, "ms": sig_ms},
+        "kernels": kernels,
         "fullstring_gpu_join": baseline,
         "speedup_vs_fullstring": {k: value / v["tuples_per_s"] for k, v in baseline.items()},
         "pairs": total_pairs,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "gpu_launches": 4 * args.steps,
-        "roofline": {"bound": "hbm", "kernel": "probe_kernel", "achieved": achieved, "peak": hbm,
-                     "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hbm, "traffic": traffic,
-                     "algorithmic_bytes": probe_alg},
+        "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": kernels[dom]["gbps"], "peak": hbm,
+                     "peak_kind": f"{peak_kind} (copy bandwidth, burst)", "unit": "GB/s",
+                     "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
+                     "algorithmic_bytes": alg[dom]},
         "cpu_baseline": cpu,
         "gen_s": t_gen,
+        **extra,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -409,7 +484,8 @@ def run_gpu(args):
     return 0
 
 
-KERNEL_REV = "v7"
+KERNEL_REV = "v8"
+KERNEL_NAMES = {"sig_R": "sig_kernel", "sig_S": "sig_kernel", "build": "build_kernel", "verify": "verify_kernel"}
 
 
 def main():
@@ -421,6 +497,7 @@ def main():
     ap.add_argument("--load-factor", type=float, default=0.5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
+    ap.add_argument("--no-extra", action="store_true", help="skip the batch and serving legs")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -169,6 +169,21 @@ as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64
                         uint32_t* d_pairs, uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count,
                         as_stream stream);
 
+/*
+ * as_join_probe_sigs -- as_join_probe with S's signatures already computed
+ * by as_sig_compute: the second half of the probe step of Section 4.1,
+ * formula 4 (compute sig(S_i), then probe H_sign with it), for callers that
+ * keep signatures with a relation or time the two halves apart.  Only the
+ * table walk, verification and compaction run.
+ *   d_sigS         : uint64[n] device buffer holding sig(S_i) for every row i
+ *                    (read only; wrong signatures only lose matches, the
+ *                    byte-exact verification still rejects non-matches)
+ * Other arguments, results and errors as for as_join_probe.
+ */
+as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                             const uint32_t* d_idS, uint64_t n, const uint64_t* d_sigS, uint32_t* d_pairs,
+                             uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream);
+
 /* Workspace of as_join for |R| = m and |S| = n: the table workspace, the pair
  * counter and the probe workspace. */
 size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor);

@@ -422,13 +422,14 @@ __device__ __forceinline__ void flush_stage_join(const uint64_t* stage, uint32_t
   __syncwarp();
 }
 
+template <bool BATCH>
 __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
   __shared__ uint64_t stage_all[kVWarps][kVStage];
   const int lane = threadIdx.x & 31;
   uint64_t* stage = stage_all[threadIdx.x >> 5];
   uint32_t np = 0;                                   // staged pairs (warp-uniform)
   int sj = -1;                                       // batch: join of the staged pairs
-  const bool batch = P.J != nullptr;
+  constexpr bool batch = BATCH;
   const uint64_t ngroups = (P.n + 31) / 32;
   const uint64_t nwarps = (uint64_t)gridDim.x * kVWarps;
   for (uint64_t grp = (uint64_t)blockIdx.x * kVWarps + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
@@ -740,7 +741,7 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaFuncSetAttribute(bl_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBHash)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.verify_blocks_per_sm, verify_kernel, kVThreads, 0)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.verify_blocks_per_sm, verify_kernel<false>, kVThreads, 0)) !=
         cudaSuccess)
       return cuda_fail(e, "occupancy query");
     if (d.verify_blocks_per_sm < 1) d.verify_blocks_per_sm = 1;
@@ -884,15 +885,73 @@ as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, co
 
 size_t as_join_probe_ws_bytes(uint64_t n) { return (size_t)(round256(n * 8) + 256); }
 
+// checks shared by the probe entry points
+static as_status probe_args(const char* fn, const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                            uint64_t n, uint32_t* d_pairs, uint64_t cap_pairs, uint64_t* d_count) {
+  if (!t || !t->slots || !t->flags || !d_count) return fail(AS_ERR_INVALID, "%s: null table or counter", fn);
+  if (n > 0 && (!d_arenaS || !d_offS)) return fail(AS_ERR_INVALID, "%s: null relation", fn);
+  if (cap_pairs > 0 && !d_pairs) return fail(AS_ERR_INVALID, "%s: null pair buffer", fn);
+  if (n > 0 && misaligned16(d_arenaS)) return fail(AS_ERR_INVALID, "%s: arena not 16-byte aligned", fn);
+  if (d_pairs && (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
+    return fail(AS_ERR_INVALID, "%s: pair buffer not 8-byte aligned", fn);
+  return AS_OK;
+}
+
+// table walk + verification + compaction of n S keys whose signatures are in sigS
+static as_status launch_verify(DeviceState* d, const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                               const uint32_t* d_idS, uint64_t n, const uint64_t* sigS, uint32_t* d_pairs,
+                               uint64_t cap_pairs, uint64_t* d_count, cudaStream_t s) {
+  VerifyParams P;
+  P.slots = reinterpret_cast<const Slot*>(t->slots);
+  P.mask = t->cap - 1;
+  P.arenaR = t->arenaR;
+  P.offR = t->offR;
+  P.idR = t->idR;
+  P.arenaS = d_arenaS;
+  P.offS = d_offS;
+  P.idS = d_idS;
+  P.sigS = sigS;
+  P.n = n;
+  P.pairs = d_pairs;
+  P.cap = cap_pairs;
+  P.count = reinterpret_cast<unsigned long long*>(d_count);
+  P.J = nullptr;
+  P.nj = 0;
+  P.counts = nullptr;
+  uint64_t blocks = (n + kVThreads - 1) / kVThreads;
+  const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
+  if (blocks > lim) blocks = lim;
+  verify_kernel<false><<<(unsigned)blocks, kVThreads, 0, s>>>(P);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "probe kernel launch");
+  return AS_OK;
+}
+
+// optional synchronous count readback and error-flag check
+static as_status finish_probe(const char* fn, const as_table* t, uint64_t cap_pairs, uint64_t* d_count,
+                              uint64_t* h_count, cudaStream_t s) {
+  if (!h_count) return AS_OK;
+  uint64_t cnt = 0;
+  uint32_t flags = 0;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(&cnt, d_count, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "count readback");
+  if ((e = cudaMemcpyAsync(&flags, t->flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+    return cuda_fail(e, "flag readback");
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "probe");
+  *h_count = cnt;
+  if (flags & kFlagTableFull) return fail(AS_ERR_TABLE_FULL, "%s: the build could not place every row", fn);
+  if (cnt > cap_pairs)
+    return fail(AS_ERR_CAPACITY, "%s: %llu pairs, capacity %llu", fn, (unsigned long long)cnt,
+                (unsigned long long)cap_pairs);
+  return AS_OK;
+}
+
 as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS,
                         uint64_t n, uint64_t* d_sigS_out, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
                         uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
-  if (!t || !t->slots || !t->flags || !d_count) return fail(AS_ERR_INVALID, "as_join_probe: null table or counter");
-  if (n > 0 && (!d_arenaS || !d_offS)) return fail(AS_ERR_INVALID, "as_join_probe: null relation");
-  if (cap_pairs > 0 && !d_pairs) return fail(AS_ERR_INVALID, "as_join_probe: null pair buffer");
-  if (n > 0 && misaligned16(d_arenaS)) return fail(AS_ERR_INVALID, "as_join_probe: arena not 16-byte aligned");
-  if (d_pairs && (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
-    return fail(AS_ERR_INVALID, "as_join_probe: pair buffer not 8-byte aligned");
+  as_status st = probe_args("as_join_probe", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
+  if (st != AS_OK) return st;
   uint64_t* sigS = d_sigS_out;
   if (!sigS && n > 0) {
     const size_t need = as_join_probe_ws_bytes(n);
@@ -903,7 +962,7 @@ as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64
     sigS = reinterpret_cast<uint64_t*>(d_ws);
   }
   DeviceState* d = nullptr;
-  as_status st = ensure_device(&d);
+  st = ensure_device(&d);
   if (st != AS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
@@ -911,44 +970,29 @@ as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64
   if (n > 0) {
     st = launch_sig(d_arenaS, d_offS, n, sigS, s);
     if (st != AS_OK) return st;
-    VerifyParams P;
-    P.slots = reinterpret_cast<const Slot*>(t->slots);
-    P.mask = t->cap - 1;
-    P.arenaR = t->arenaR;
-    P.offR = t->offR;
-    P.idR = t->idR;
-    P.arenaS = d_arenaS;
-    P.offS = d_offS;
-    P.idS = d_idS;
-    P.sigS = sigS;
-    P.n = n;
-    P.pairs = d_pairs;
-    P.cap = cap_pairs;
-    P.count = reinterpret_cast<unsigned long long*>(d_count);
-    P.J = nullptr;
-    P.nj = 0;
-    P.counts = nullptr;
-    uint64_t blocks = (n + kVThreads - 1) / kVThreads;
-    const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
-    if (blocks > lim) blocks = lim;
-    verify_kernel<<<(unsigned)blocks, kVThreads, 0, s>>>(P);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "probe kernel launch");
+    st = launch_verify(d, t, d_arenaS, d_offS, d_idS, n, sigS, d_pairs, cap_pairs, d_count, s);
+    if (st != AS_OK) return st;
   }
-  if (h_count) {
-    uint64_t cnt = 0;
-    uint32_t flags = 0;
-    if ((e = cudaMemcpyAsync(&cnt, d_count, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-      return cuda_fail(e, "count readback");
-    if ((e = cudaMemcpyAsync(&flags, t->flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
-      return cuda_fail(e, "flag readback");
-    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "probe");
-    *h_count = cnt;
-    if (flags & kFlagTableFull) return fail(AS_ERR_TABLE_FULL, "as_join_probe: the build could not place every row");
-    if (cnt > cap_pairs)
-      return fail(AS_ERR_CAPACITY, "as_join_probe: %llu pairs, capacity %llu", (unsigned long long)cnt,
-                  (unsigned long long)cap_pairs);
+  return finish_probe("as_join_probe", t, cap_pairs, d_count, h_count, s);
+}
+
+as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                             const uint32_t* d_idS, uint64_t n, const uint64_t* d_sigS, uint32_t* d_pairs,
+                             uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  as_status st = probe_args("as_join_probe_sigs", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
+  if (st != AS_OK) return st;
+  if (n > 0 && !d_sigS) return fail(AS_ERR_INVALID, "as_join_probe_sigs: null signatures");
+  DeviceState* d = nullptr;
+  st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(d_count, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  if (n > 0) {
+    st = launch_verify(d, t, d_arenaS, d_offS, d_idS, n, d_sigS, d_pairs, cap_pairs, d_count, s);
+    if (st != AS_OK) return st;
   }
-  return AS_OK;
+  return finish_probe("as_join_probe_sigs", t, cap_pairs, d_count, h_count, s);
 }
 
 as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
@@ -1207,7 +1251,7 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
     uint64_t blocks = (b->nS + kVThreads - 1) / kVThreads;
     const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
     if (blocks > lim) blocks = lim;
-    verify_kernel<<<(unsigned)blocks, kVThreads, 0, s>>>(P);
+    verify_kernel<true><<<(unsigned)blocks, kVThreads, 0, s>>>(P);
   }
   if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "batch launch");
   return AS_OK;

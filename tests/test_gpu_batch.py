@@ -104,3 +104,22 @@ def test_batch_single_join_equals_join(cuda, batch):
     solo = oracle.sort_pairs(ag.join(R, S).cpu().numpy().view(np.uint32))
     got = ag.join_batch(R, S, [(0, R.n, 0, S.n)], [len(solo) + 64])[0]
     assert np.array_equal(oracle.sort_pairs(got.cpu().numpy().view(np.uint32)), solo)
+
+
+def test_autotuned_graph_batch(cuda, batch):
+    from paper_2411_18183_gb300 import tune
+    ag = cuda
+    Rd, Sd = dev(ag, batch.R), dev(ag, batch.S)
+    R = ag.DeviceRelation(Rd.arena, Rd.off, None)
+    S = ag.DeviceRelation(Sd.arena, Sd.off, None)
+    caps = [max(64, 2 * e + 64) for e in batch.expected]
+    gb, times = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1)
+    assert set(times) == {0.4, 0.8} and gb.lf in times and gb.graph is not None
+    gb.counts.zero_()
+    gb.replay()
+    torch.cuda.synchronize()
+    assert gb.counts.cpu().tolist() == list(batch.expected)
+    for j in (0, len(batch.ranges) // 2, len(batch.ranges) - 1):
+        Rj, Sj = batch.join_relations(j)
+        got = oracle.sort_pairs(gb.result(j).cpu().numpy().view(np.uint32))
+        assert np.array_equal(got, oracle.join_simple(Rj, Sj))

@@ -148,3 +148,24 @@ def test_baseline_join_matches_oracle(cuda, tagged):
         assert np.array_equal(gpu_baseline(cuda, R, S, tagged, lf), oracle.join_simple(R, S))
     wl = workloads.generate(workloads.CONFIGS["large"].scaled(5_000, 50_000))
     assert np.array_equal(gpu_baseline(cuda, wl.R, wl.S, tagged), oracle.join_simple(wl.R, wl.S))
+
+
+def test_probe_with_given_signatures(cuda):
+    """as_join_probe_sigs with signatures from as_sig_compute gives the join;
+    signatures that are wrong for some rows only lose those rows' matches."""
+    ag = cuda
+    wl = workloads.generate(workloads.CONFIGS["plain"].scaled(2000, 25_000))
+    R, S = dev(ag, wl.R), dev(ag, wl.S)
+    ws = ag.alloc_ws(ag.join_table_bytes(R.n, 0.5))         # the table lives in ws: keep it
+    t = ag.join_build(R, ws, 0.5)
+    pairs = torch.empty(2 * 20_000, dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    sigS = ag.sig_compute(S)
+    cnt = ag.join_probe_sigs(t, S, sigS, pairs, count)
+    want = oracle.join_simple(wl.R, wl.S)
+    assert np.array_equal(oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32)), want)
+    bad = sigS.clone()
+    bad[::2] ^= 1                                   # corrupt even rows' signatures
+    cnt = ag.join_probe_sigs(t, S, bad, pairs, count)
+    got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
+    assert np.array_equal(got, want[want[:, 1] % 2 == 1])

@@ -256,6 +256,7 @@ class BatchSpec:
     frac_copy: float = 0.25
     alphabet: str = "printable"
     seed: int = 20084
+    s_factor_range: tuple | None = None     # (lo, hi): |S_j| / |R_j| uniform per join instead of s_factor
 
     def scaled(self, factor: float, n_joins: int | None = None) -> "BatchSpec":
         """Relation sizes divided by `factor` (the shape is kept)."""
@@ -269,13 +270,26 @@ class BatchSpec:
         sizes = np.exp(rng.normal(np.log(self.r_median), self.sigma, self.n_joins))
         sizes = np.clip(np.rint(sizes), self.r_range[0], self.r_range[1]).astype(np.int64)
         bands = rng.integers(0, len(self.bands), self.n_joins)
+        if self.s_factor_range is None:
+            factors = [self.s_factor] * self.n_joins
+        else:
+            factors = rng.integers(self.s_factor_range[0], self.s_factor_range[1] + 1, self.n_joins).tolist()
         out = []
         for j in range(self.n_joins):
             lo, hi = self.bands[bands[j]]
             m = int(sizes[j])
-            out.append(JoinSpec(m=m, n=self.s_factor * m, r_len=(lo, hi), s_len=(lo, hi), alphabet=self.alphabet,
+            out.append(JoinSpec(m=m, n=int(factors[j]) * m, r_len=(lo, hi), s_len=(lo, hi), alphabet=self.alphabet,
                                 frac_copy=self.frac_copy, seed=self.seed * 1_000_003 + j))
         return out
+
+
+# Requests of the serving loop: |R| log-normal (median 50,000), |S| = 4-16 |R|,
+# XML-like keys of 200-2000 bytes, 20% of S copies an R key.  The pool holds
+# the distinct joins that requests ask for.
+SERVE_SPEC = BatchSpec(n_joins=64, r_median=50_000, sigma=1.0, r_range=(1_000, 1_000_000), s_factor_range=(4, 16),
+                       bands=((200, 2000),), frac_copy=0.20, alphabet="xml", seed=20085)
+SERVE_RATE = 2000.0                 # mean arrivals per second (Poisson)
+SERVE_BUDGET_BYTES = 120 * 10 ** 9  # admission bound on device memory
 
 
 @dataclasses.dataclass
