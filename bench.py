@@ -249,6 +249,56 @@ def serve_leg(ag):
     return s
 
 
+SWEEP_LENGTHS = (16, 64, 256, 1024, 4096, 8192)
+
+
+def length_sweep_leg(ag, reps: int = 5):
+    """Whole-join S tuples/s of the signature join and of the full-string GPU join
+    (plain and tagged slots) for fixed key lengths, |R| = 10,000, |S| = 100,000,
+    30% of S copies an R key (the plain workload's shape at one length)."""
+    import torch
+    out = []
+    for i, L in enumerate(SWEEP_LENGTHS):
+        spec = workloads.JoinSpec(m=10_000, n=100_000, r_len=(L, L), s_len=(L, L), alphabet="printable",
+                                  frac_copy=0.30, seed=20181 + i)
+        wl = workloads.generate(spec)
+        R = ag.DeviceRelation.from_host(wl.R.arena, wl.R.off, wl.R.ids)
+        S = ag.DeviceRelation.from_host(wl.S.arena, wl.S.off, wl.S.ids)
+        pairs = torch.empty(2 * (wl.expected_pairs() + 1024), dtype=torch.int32, device="cuda")
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+        ws = ag.alloc_ws(ag.join_ws_bytes(R.n, S.n, 0.5))
+        bws = ag.alloc_ws(ag.baseline_ws_bytes(R.n, S.n, 0.5))
+        stream = torch.cuda.current_stream()
+        runs = {"signature": lambda: ag.join_into(R, S, ws, pairs, count, 0.5, sync=False, stream=stream),
+                "fullstring_plain": lambda: ag.baseline_join_into(R, S, bws, pairs, count, 0.5, tagged=False,
+                                                                  sync=False, stream=stream),
+                "fullstring_tagged": lambda: ag.baseline_join_into(R, S, bws, pairs, count, 0.5, tagged=True,
+                                                                   sync=False, stream=stream)}
+        row = {"key_bytes": L}
+        for name, f in runs.items():
+            f()
+            torch.cuda.synchronize()
+            if int(count.item()) != wl.expected_pairs():
+                raise SystemExit(f"length sweep: {name} found {int(count.item())} pairs at {L} B")
+            for _ in range(2):
+                f()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                f()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            row[name] = {"ms": ms, "tuples_per_s": S.n / (ms * 1e-3)}
+        row["speedup_vs_plain"] = row["fullstring_plain"]["ms"] / row["signature"]["ms"]
+        row["speedup_vs_tagged"] = row["fullstring_tagged"]["ms"] / row["signature"]["ms"]
+        out.append(row)
+        del R, S, ws, bws, pairs
+    return {"workload": "|R| = 10,000 x |S| = 100,000 printable keys of one fixed length, 30% S copies; "
+                        "whole join (both relations' signatures or hashes, build, probe, verify, compaction)",
+            "rows": out}
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -444,6 +494,7 @@ def run_gpu(args):
     if not args.no_extra:
         extra["batch"] = batch_leg(ag, args.steps)
         extra["serving"] = serve_leg(ag)
+        extra["length_sweep"] = length_sweep_leg(ag)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
