@@ -184,6 +184,34 @@ as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const u
                              const uint32_t* d_idS, uint64_t n, const uint64_t* d_sigS, uint32_t* d_pairs,
                              uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream);
 
+/*
+ * Output modes of as_join_probe_mode (the left, right and semi-join variants
+ * that Section 5 lists as extensions; R is the build side, S the probe side).
+ *   AS_JOIN_INNER   : the (r_id, s_id) pairs, as as_join_probe
+ *   AS_JOIN_SEMI    : one (AS_NO_ROW, s_id) per S row with at least one match
+ *   AS_JOIN_ANTI    : one (AS_NO_ROW, s_id) per S row with no match
+ *   AS_JOIN_OUTER_S : the inner pairs plus one (AS_NO_ROW, s_id) per S row
+ *                     with no match (outer join preserving S)
+ */
+enum {
+    AS_JOIN_INNER = 0,
+    AS_JOIN_SEMI = 1,
+    AS_JOIN_ANTI = 2,
+    AS_JOIN_OUTER_S = 3
+};
+#define AS_NO_ROW 0xFFFFFFFFu
+
+/*
+ * as_join_probe_mode -- as_join_probe_sigs (S's signatures given, from
+ * as_sig_compute) with an output mode.  Matches are exact (byte-verified) in
+ * every mode.  d_pairs receives the mode's output records as (r_id, s_id)
+ * pairs in unspecified order; d_count / h_count count them.  Errors as for
+ * as_join_probe, and AS_ERR_INVALID for an unknown mode.
+ */
+as_status as_join_probe_mode(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                             const uint32_t* d_idS, uint64_t n, const uint64_t* d_sigS, int mode, uint32_t* d_pairs,
+                             uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream);
+
 /* Workspace of as_join for |R| = m and |S| = n: the table workspace, the pair
  * counter and the probe workspace. */
 size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor);

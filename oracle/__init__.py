@@ -174,3 +174,30 @@ def join_simple(R, S) -> np.ndarray:
 
 def join_grace(R, S, log2_parts: int = 8, nthreads: int = 4) -> np.ndarray:
     return _run_join(_load().or_join_grace, R, S, extra=(log2_parts, nthreads))
+
+
+NO_ROW = 0xFFFFFFFF
+MODES = {"inner": 0, "semi": 1, "anti": 2, "outer_s": 3}
+
+
+def join_mode(R, S, mode: str) -> np.ndarray:
+    """The join's output in one of the modes of the left/right/semi-join
+    extensions (Section 5), by their plain definitions on the exact inner join
+    T: semi = {(NO_ROW, s.id) : s has a partner in T}, anti = the S rows without
+    one, outer_s = T plus the anti rows.  Sorted like sort_pairs."""
+    T = join_simple(R, S)
+    matched_ids = set(T[:, 1].tolist())
+    sids = [int(x) for x in S.ids]
+    semi = [(NO_ROW, s) for s in sids if s in matched_ids]
+    anti = [(NO_ROW, s) for s in sids if s not in matched_ids]
+    if mode == "inner":
+        out = T
+    elif mode == "semi":
+        out = np.array(semi, dtype=np.uint32).reshape(-1, 2)
+    elif mode == "anti":
+        out = np.array(anti, dtype=np.uint32).reshape(-1, 2)
+    elif mode == "outer_s":
+        out = np.concatenate([T, np.array(anti, dtype=np.uint32).reshape(-1, 2)])
+    else:
+        raise ValueError(mode)
+    return sort_pairs(out)

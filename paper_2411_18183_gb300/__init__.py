@@ -31,7 +31,7 @@ AS_ERR_CUDA = 5
 AS_ERR_UNSUPPORTED = 6
 
 EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_join_table_bytes",
-           "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_probe_sigs", "as_join_ws_bytes", "as_join",
+           "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_probe_sigs", "as_join_probe_mode", "as_join_ws_bytes", "as_join",
            "as_baseline_ws_bytes", "as_baseline_join")
 
 
@@ -82,6 +82,8 @@ def load(path: str | None = None):
         lib.as_join_probe.restype = S
         lib.as_join_probe_sigs.argtypes = [ctypes.POINTER(Table), P, P, P, U64, P, P, U64, P, P, P]
         lib.as_join_probe_sigs.restype = S
+        lib.as_join_probe_mode.argtypes = [ctypes.POINTER(Table), P, P, P, U64, P, S, P, U64, P, P, P]
+        lib.as_join_probe_mode.restype = S
         lib.as_join.argtypes = [P, P, P, U64, P, P, P, U64, F, P, SZ, P, U64, P, P, P]
         lib.as_join.restype = S
         lib.as_baseline_ws_bytes.argtypes = [U64, U64, F]
@@ -206,6 +208,23 @@ def join_probe_sigs(t: Table, S: DeviceRelation, sigS: torch.Tensor, pairs: torc
     h = ctypes.c_uint64(0)
     _check(lib.as_join_probe_sigs(ctypes.byref(t), _ptr(S.arena), _ptr(S.off), _ptr(S.ids), S.n, _ptr(sigS),
                                   _ptr(pairs), cap, _ptr(count), ctypes.byref(h) if sync else None, _stream(stream)))
+    return int(h.value) if sync else None
+
+
+JOIN_MODES = {"inner": 0, "semi": 1, "anti": 2, "outer_s": 3}    # AS_JOIN_*
+NO_ROW = 0xFFFFFFFF                                                  # AS_NO_ROW
+
+
+def join_probe_mode(t: Table, S: DeviceRelation, sigS: torch.Tensor, pairs: torch.Tensor, count: torch.Tensor,
+                    mode: str = "inner", sync: bool = True, stream=None) -> int | None:
+    """as_join_probe_mode: inner pairs, or per-S-row (NO_ROW, s_id) records (semi, anti), or
+    inner pairs plus the unmatched S rows (outer_s)."""
+    lib = load()
+    cap = pairs.numel() // 2
+    h = ctypes.c_uint64(0)
+    _check(lib.as_join_probe_mode(ctypes.byref(t), _ptr(S.arena), _ptr(S.off), _ptr(S.ids), S.n, _ptr(sigS),
+                                  JOIN_MODES[mode], _ptr(pairs), cap, _ptr(count), ctypes.byref(h) if sync else None,
+                                  _stream(stream)))
     return int(h.value) if sync else None
 
 

@@ -345,6 +345,7 @@ struct VerifyParams {
   uint32_t* pairs;
   uint64_t cap;
   unsigned long long* count;
+  int mode;                    // AS_JOIN_INNER / SEMI / ANTI / OUTER_S (single joins)
   // batch mode (J != nullptr): per-join tables, output regions and counters
   const BatchJoin* J;
   int nj;
@@ -447,6 +448,8 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
     }
     uint64_t sig = 0, start = 0, len = 0, b = 0, steps = 0;
     uint32_t l32 = 0;
+    bool matched = false;                            // the lane's S row has a verified match
+    const bool row_live = live;
     if (live) {
       sig = __ldg(P.sigS + vi);
       start = __ldg(P.offS + i);
@@ -481,6 +484,8 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         const uint64_t rs = __ldg(P.offR + rj);
         const uint64_t rl = __ldg(P.offR + rj + 1) - rs;
         if (rl == lj && warp_equal(P.arenaR + rs, P.arenaS + stj, lj)) {
+          if (lane == j) matched = true;
+          if (!batch && (P.mode == AS_JOIN_SEMI || P.mode == AS_JOIN_ANTI)) continue;   // rows, not pairs
           const int jj = __shfl_sync(kFull, jn, j);
           if (batch && np && jj != sj) {              // the stage holds one join's pairs
             flush_stage_join(stage, np, P, sj);
@@ -498,6 +503,22 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
             np = 0;
           }
         }
+      }
+    }
+    if (!batch && P.mode != AS_JOIN_INNER) {         // one (AS_NO_ROW, s_id) per selected S row
+      const bool emit = row_live && (P.mode == AS_JOIN_SEMI ? matched : !matched);
+      const uint32_t em = __ballot_sync(kFull, emit);
+      if (em) {
+        if (np + (uint32_t)__popc(em) > (uint32_t)kVStage) {
+          flush_stage(stage, np, P);
+          np = 0;
+        }
+        if (emit) {
+          const uint32_t sid = P.idS ? __ldg(P.idS + i) : (uint32_t)i;
+          stage[np + __popc(em & lanemask_lt())] = (uint64_t)AS_NO_ROW | ((uint64_t)sid << 32);
+        }
+        np += (uint32_t)__popc(em);
+        __syncwarp();
       }
     }
   }
@@ -900,7 +921,7 @@ static as_status probe_args(const char* fn, const as_table* t, const uint8_t* d_
 // table walk + verification + compaction of n S keys whose signatures are in sigS
 static as_status launch_verify(DeviceState* d, const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
                                const uint32_t* d_idS, uint64_t n, const uint64_t* sigS, uint32_t* d_pairs,
-                               uint64_t cap_pairs, uint64_t* d_count, cudaStream_t s) {
+                               uint64_t cap_pairs, uint64_t* d_count, cudaStream_t s, int mode = AS_JOIN_INNER) {
   VerifyParams P;
   P.slots = reinterpret_cast<const Slot*>(t->slots);
   P.mask = t->cap - 1;
@@ -915,6 +936,7 @@ static as_status launch_verify(DeviceState* d, const as_table* t, const uint8_t*
   P.pairs = d_pairs;
   P.cap = cap_pairs;
   P.count = reinterpret_cast<unsigned long long*>(d_count);
+  P.mode = mode;
   P.J = nullptr;
   P.nj = 0;
   P.counts = nullptr;
@@ -993,6 +1015,26 @@ as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const u
     if (st != AS_OK) return st;
   }
   return finish_probe("as_join_probe_sigs", t, cap_pairs, d_count, h_count, s);
+}
+
+as_status as_join_probe_mode(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                             const uint32_t* d_idS, uint64_t n, const uint64_t* d_sigS, int mode, uint32_t* d_pairs,
+                             uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  as_status st = probe_args("as_join_probe_mode", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
+  if (st != AS_OK) return st;
+  if (mode < AS_JOIN_INNER || mode > AS_JOIN_OUTER_S) return fail(AS_ERR_INVALID, "as_join_probe_mode: mode %d", mode);
+  if (n > 0 && !d_sigS) return fail(AS_ERR_INVALID, "as_join_probe_mode: null signatures");
+  DeviceState* d = nullptr;
+  st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(d_count, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  if (n > 0) {
+    st = launch_verify(d, t, d_arenaS, d_offS, d_idS, n, d_sigS, d_pairs, cap_pairs, d_count, s, mode);
+    if (st != AS_OK) return st;
+  }
+  return finish_probe("as_join_probe_mode", t, cap_pairs, d_count, h_count, s);
 }
 
 as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
@@ -1245,6 +1287,7 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
     P.pairs = d_pairs;
     P.cap = 0;
     P.count = nullptr;
+    P.mode = AS_JOIN_INNER;
     P.J = J;
     P.nj = nj;
     P.counts = reinterpret_cast<unsigned long long*>(d_counts);

@@ -169,3 +169,27 @@ def test_probe_with_given_signatures(cuda):
     cnt = ag.join_probe_sigs(t, S, bad, pairs, count)
     got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
     assert np.array_equal(got, want[want[:, 1] % 2 == 1])
+
+
+@pytest.mark.parametrize("mode", ["inner", "semi", "anti", "outer_s"])
+def test_probe_modes_match_oracle(cuda, mode):
+    """as_join_probe_mode against the oracle's definitions, on a scaled large-workload
+    relation pair (duplicate R keys) and on the edge keys."""
+    ag = cuda
+    cases = []
+    wl = workloads.generate(workloads.CONFIGS["large"].scaled(3000, 20_000))
+    cases.append((wl.R, wl.S))
+    keys = edge_keys()
+    cases.append((workloads.relation_from_keys(keys[::2] + keys[:5]),
+                  workloads.relation_from_keys(keys, ids=[5 * i + 1 for i in range(len(keys))])))
+    for Rh, Sh in cases:
+        R, S = dev(ag, Rh), dev(ag, Sh)
+        ws = ag.alloc_ws(ag.join_table_bytes(R.n, 0.5))
+        t = ag.join_build(R, ws, 0.5)
+        sigS = ag.sig_compute(S)
+        want = oracle.join_mode(Rh, Sh, mode)
+        pairs = torch.zeros(2 * (len(want) + 64), dtype=torch.int32, device="cuda")
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+        cnt = ag.join_probe_mode(t, S, sigS, pairs, count, mode=mode)
+        got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
+        assert np.array_equal(got, want), (mode, Rh.n, Sh.n)

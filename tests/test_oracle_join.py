@@ -98,3 +98,27 @@ def test_large_workload_ground_truth_scaled():
     got = oracle.join_grace(wl.R, wl.S, log2_parts=8, nthreads=4)
     assert len(got) == wl.expected_pairs()
     assert (wl.r_mult > 1).any()
+
+
+def test_join_modes_by_definition_and_brute_force():
+    """semi / anti / outer_s of the oracle against a brute-force statement on
+    small relations with duplicates, empty keys and ids that are not rows."""
+    import random
+    rng = random.Random(11)
+    pool = [b"", b"a", b"ab", b"abc", b"xyz" * 5, bytes(range(40))]
+    rk = [rng.choice(pool) for _ in range(25)]
+    sk = [rng.choice(pool + [b"q", b"zz"]) for _ in range(40)]
+    R = workloads.relation_from_keys(rk, ids=[1000 + i for i in range(len(rk))])
+    S = workloads.relation_from_keys(sk, ids=[7 * i + 3 for i in range(len(sk))])
+    NO = oracle.NO_ROW
+    inner = sorted((1000 + i, 7 * j + 3) for j, s in enumerate(sk) for i, r in enumerate(rk) if r == s)
+    has = {j for j, s in enumerate(sk) if s in rk}
+    want = {
+        "inner": inner,
+        "semi": sorted((NO, 7 * j + 3) for j in range(len(sk)) if j in has),
+        "anti": sorted((NO, 7 * j + 3) for j in range(len(sk)) if j not in has),
+        "outer_s": sorted(inner + [(NO, 7 * j + 3) for j in range(len(sk)) if j not in has]),
+    }
+    for mode, w in want.items():
+        got = [tuple(int(x) for x in row) for row in oracle.join_mode(R, S, mode)]
+        assert got == w, mode
