@@ -435,31 +435,32 @@ def run_gpu(args):
 
     hbm, peak_kind = peaks()
 
-    # end to end through the C ABI from pinned host buffers: H2D of R and S,
-    # the join, D2H of the count and the pairs
-    def e2e_step():
-        dR.arena.copy_(hR[0], non_blocking=True)
-        dR.off.copy_(hR[1], non_blocking=True)
-        dR.ids.copy_(hR[2], non_blocking=True)
-        dS.arena.copy_(hS[0], non_blocking=True)
-        dS.off.copy_(hS[1], non_blocking=True)
-        dS.ids.copy_(hS[2], non_blocking=True)
-        st, cnt = ag.join_into(dR, dS, ws, pairs, count, lf, sync=True, stream=stream)
-        out = pairs[: 2 * cnt].cpu()
-        return cnt, out.numel() * 4
-
-    h2d = sum(int(t.numel() * t.element_size()) for t in (*hR, *hS))
+    # end to end from pinned host buffers through the package's host-relation join
+    # (stream.HostStreamJoin: copies of S chunks overlapped with the kernels of the
+    # previous chunk; the pairs come back to pinned host memory)
+    from paper_2411_18183_gb300.stream import HostStreamJoin
+    target = 512 << 20                                  # about 512 MB of S keys per chunk
+    chunk_rows = max(1, min(n, int(n * target / max(1, wl.S.nbytes))))
+    chunk_bytes = int(1.1 * wl.S.nbytes * chunk_rows / max(1, n)) + (1 << 20)
+    sj = HostStreamJoin(max_m=m, max_r_bytes=hR[0].numel(), max_chunk_rows=chunk_rows, max_chunk_bytes=chunk_bytes,
+                        cap_pairs=int(2 * expected + (1 << 16)), max_chunks=4096, load_factor=lf)
+    cuts = sj.chunks(wl.S.off)
+    out_host = torch.empty(2 * sj.cap, dtype=torch.int32).pin_memory()
+    h2d = (sum(int(t.numel() * t.element_size()) for t in hR)
+           + sum((((int(wl.S.off[b]) + 15) & ~15) + 16 - (int(wl.S.off[a]) & ~15)) + 8 * (b - a + 1) + 4 * (b - a)
+                 for a, b in zip(cuts, cuts[1:])))
     e2e_steps = max(2, min(args.steps, 5))
-    e2e_step()
+    if sj.run(hR, hS, cuts, out_host) != expected:
+        raise SystemExit("end-to-end join: wrong pair count")
     barrier()
     te = time.perf_counter()
-    d2h = 0
     for _ in range(e2e_steps):
-        cnt, nb = e2e_step()
-        d2h = nb + 8
+        cnt = sj.run(hR, hS, cuts, out_host)
     barrier()
     e2e_s = max_over_ranks((time.perf_counter() - te) / e2e_steps)
     e2e_value = world * n / e2e_s
+    d2h = 8 * cnt + 8 * (len(cuts) - 1)
+    del sj
 
     # rooflines of the step's kernels from their live CUDA-event times (algorithmic bytes / launch)
     lensS = np.diff(wl.S.off).astype(np.int64)
@@ -486,7 +487,7 @@ def run_gpu(args):
         with open(tp) as f:
             d = json.load(f)
         ent = d.get(KERNEL_NAMES[dom], {})
-        if ent.get("kernel_rev") == KERNEL_REV and ent.get("per_byte_of_keys"):
+        if ent.get("kernel_rev") == KERNEL_REVS[KERNEL_NAMES[dom]] and ent.get("per_byte_of_keys"):
             keyb = wl.S.nbytes if dom == "sig_S" else 2 * verified_bytes
             traffic = ent["per_byte_of_keys"] * keyb
 
@@ -518,7 +519,9 @@ def run_gpu(args):
         "speedup_vs_fullstring": {k: value / v["tuples_per_s"] for k, v in baseline.items()},
         "pairs": total_pairs,
         "clocks": clk,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "ms_per_step": e2e_s * 1e3, "chunks": len(cuts) - 1,
+                "path": "stream.HostStreamJoin: pinned host R and S, S copied in chunks under the kernels"},
         "gpu_launches": 4 * args.steps,
         "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": kernels[dom]["gbps"], "peak": hbm,
                      "peak_kind": f"{peak_kind} (copy bandwidth, burst)", "unit": "GB/s",
@@ -535,7 +538,8 @@ def run_gpu(args):
     return 0
 
 
-KERNEL_REV = "v8"
+# revision of each kernel's code; profiles/traffic.json holds counters per revision
+KERNEL_REVS = {"sig_kernel": "v8", "build_kernel": "v8", "verify_kernel": "v9"}
 KERNEL_NAMES = {"sig_R": "sig_kernel", "sig_S": "sig_kernel", "build": "build_kernel", "verify": "verify_kernel"}
 
 
