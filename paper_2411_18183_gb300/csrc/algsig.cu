@@ -169,20 +169,30 @@ __device__ __forceinline__ void sig_walk(const uint8_t* __restrict__ arena, cons
     const Plan nn = plan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
     issue_span(buf, arena, nn);
     const uint64_t V = scan_round(cur, cur.active ? pack4(a1, a2, a3, a4) : 0ull, ctab);
-    if (pd.valid) {                                 // finish the previous round's deferred product
-      const uint64_t P = pending_value(pd);
-      if (pd.complete) {
-        const uint64_t s = lo_correct(ctab, P, pd.lo, rc);
-        if (lane == 0) sig_out[pd.key + out_shift] = s;
-      } else {
-        carry = P;
-      }
-      pd.valid = false;
-    }
+    // Keys that finish here: the head lane of every key whose tiles all lie in
+    // this round, and the previous round's deferred key if it is complete (taken
+    // by a lane without a head job); one lo_correct for all of them.
     const bool head = cur.active && (uint32_t)lane == cur.slot0;
     const bool fresh = cur.q != 0 || cur.tc == 0;   // the key's first tile is in this round
-    if (head && fresh && cur.slot0 + cur.rq <= 32u)
-      sig_out[cur.kc + (uint64_t)cur.q + out_shift] = lo_correct(ctab, V, cur.lo, rc);
+    const bool hjob = head && fresh && cur.slot0 + cur.rq <= 32u;
+    uint64_t P = 0;
+    bool pjob = false;
+    if (pd.valid) {                                 // finish the previous round's deferred product
+      P = pending_value(pd);
+      if (pd.complete) pjob = true; else carry = P;
+      pd.valid = false;
+    }
+    const uint32_t hm = __ballot_sync(kFull, hjob);
+    const int plane = pjob ? __ffs(~hm) - 1 : -1;
+    if (pjob && plane < 0) {                        // every lane has a head job (rare)
+      const uint64_t s = lo_correct(ctab, P, pd.lo, rc);
+      if (lane == 0) sig_out[pd.key + out_shift] = s;
+      pjob = false;
+    }
+    const bool mine = pjob && lane == plane;
+    const uint64_t fin = lo_correct(ctab, hjob ? V : P, hjob ? cur.lo : pd.lo, rc);
+    if (hjob) sig_out[cur.kc + (uint64_t)cur.q + out_shift] = fin;
+    else if (mine) sig_out[pd.key + out_shift] = fin;
     if (cur.tc > 0) {                               // group 0 continues a key: x^(k e) B, finished next round
       pd.valid = true;
       pd.key = cur.kc;

@@ -182,12 +182,12 @@ __device__ __forceinline__ Plan plan_round(const PlanLoad& L, uint64_t kc, uint6
     if (lane >= d) cum += t;
   }
   const uint32_t total = __shfl_sync(kFull, cum, 31);
-  int q = 0;                        // first q with cum[q] > lane
-#pragma unroll
-  for (int d = 16; d >= 1; d >>= 1) {
-    const uint32_t cv = __shfl_sync(kFull, cum, q + d - 1);
-    if (cv <= (uint32_t)lane) q += d;
-  }
+  // owner of each lane's tile: the last key whose first tile slot is at or
+  // before the lane (every loaded key has at least one tile)
+  const uint32_t first = cum - rc;
+  const uint32_t starts = __reduce_or_sync(kFull, rc != 0u && first < 32u ? 1u << first : 0u);
+  int q = __popc(starts & ((2u << lane) - 1u)) - 1;
+  if (q < 0) q = 0;
   p.active = p.valid && (uint32_t)lane < total;
   const uint32_t cq = __shfl_sync(kFull, cum, q);
   p.rq = __shfl_sync(kFull, rc, q);
@@ -405,34 +405,37 @@ struct Pending {
   uint64_t key;
   uint64_t carry;    // partial signature of the key before that round
   uint32_t lo;
-  uint32_t l1, l2, l3, l4;   // log(B_k) + k e, or ~0 for B_k = 0 (then: antilogs)
+  uint32_t l1, l2, l3, l4;   // log(B_k) as loaded (then: antilogs of log(B_k) + k e)
+  uint32_t e1;               // e mod 65535
+  uint32_t zero;             // bit k-1: B_k = 0
 };
 
-__device__ __forceinline__ uint32_t log_plus(uint32_t b, uint32_t e) {
-  return b ? (uint32_t)__ldg(&g_log[b]) + e : 0xFFFFFFFFu;
-}
 __device__ __forceinline__ uint32_t alog_of(uint32_t l) {
-  if (l == 0xFFFFFFFFu) return 0;
   if (l >= kOrder) l -= kOrder;
   return __ldg(&g_alog[l]);
 }
 
-// start the product x^(k e) B: logs (the caller later turns them into antilogs)
+// start the product x^(k e) B: the log loads only; nothing waits for them
+// before pending_alogs, one round later
 __device__ __forceinline__ void pending_logs(Pending& pd, uint64_t B, uint64_t tile0) {
-  const uint32_t e1 = (uint32_t)(tile0 % kOrder) * (uint32_t)(kTile / 2) % kOrder;
+  pd.e1 = (uint32_t)(tile0 % kOrder) * (uint32_t)(kTile / 2) % kOrder;
+  const uint32_t b1 = (uint32_t)B & 0xFFFFu, b2 = (uint32_t)(B >> 16) & 0xFFFFu;
+  const uint32_t b3 = (uint32_t)(B >> 32) & 0xFFFFu, b4 = (uint32_t)(B >> 48) & 0xFFFFu;
+  pd.zero = (b1 ? 0u : 1u) | (b2 ? 0u : 2u) | (b3 ? 0u : 4u) | (b4 ? 0u : 8u);
+  pd.l1 = __ldg(&g_log[b1]);
+  pd.l2 = __ldg(&g_log[b2]);
+  pd.l3 = __ldg(&g_log[b3]);
+  pd.l4 = __ldg(&g_log[b4]);
+}
+__device__ __forceinline__ void pending_alogs(Pending& pd) {
+  const uint32_t e1 = pd.e1;
   uint32_t e2 = e1 * 2u; if (e2 >= kOrder) e2 -= kOrder;
   uint32_t e3 = e2 + e1; if (e3 >= kOrder) e3 -= kOrder;
   uint32_t e4 = e2 * 2u; if (e4 >= kOrder) e4 -= kOrder;
-  pd.l1 = log_plus((uint32_t)B & 0xFFFFu, e1);
-  pd.l2 = log_plus((uint32_t)(B >> 16) & 0xFFFFu, e2);
-  pd.l3 = log_plus((uint32_t)(B >> 32) & 0xFFFFu, e3);
-  pd.l4 = log_plus((uint32_t)(B >> 48) & 0xFFFFu, e4);
-}
-__device__ __forceinline__ void pending_alogs(Pending& pd) {
-  pd.l1 = alog_of(pd.l1);
-  pd.l2 = alog_of(pd.l2);
-  pd.l3 = alog_of(pd.l3);
-  pd.l4 = alog_of(pd.l4);
+  pd.l1 = (pd.zero & 1u) ? 0u : alog_of(pd.l1 + e1);
+  pd.l2 = (pd.zero & 2u) ? 0u : alog_of(pd.l2 + e2);
+  pd.l3 = (pd.zero & 4u) ? 0u : alog_of(pd.l3 + e3);
+  pd.l4 = (pd.zero & 8u) ? 0u : alog_of(pd.l4 + e4);
 }
 __device__ __forceinline__ uint64_t pending_value(const Pending& pd) {
   return pd.carry ^ pack4(pd.l1, pd.l2, pd.l3, pd.l4);
