@@ -362,47 +362,47 @@ struct VerifyParams {
   unsigned long long* counts;
 };
 
-// aligned 8-byte word i of a key region whose first aligned word is `w`, or 0
-// if the word holds no key byte (region end `end` counted from w in bytes)
-__device__ __forceinline__ uint64_t word_or0(const uint64_t* w, uint64_t i, uint64_t end) {
-  return 8 * i < end ? __ldg(w + i) : 0ull;
+__device__ __forceinline__ uint4 ld16(const uint8_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
+__device__ __forceinline__ uint64_t lo64(uint4 v) { return (uint64_t)v.x | ((uint64_t)v.y << 32); }
+__device__ __forceinline__ uint64_t hi64(uint4 v) { return (uint64_t)v.z | ((uint64_t)v.w << 32); }
+// bytes sh/8 .. sh/8 + 7 of the 16-byte pair (lo, hi), sh in {0, 8, ..., 56}
+__device__ __forceinline__ uint64_t fsh64(uint64_t lo, uint64_t hi, uint32_t sh) {
+  return sh ? (lo >> sh) | (hi << (64u - sh)) : lo;
 }
-
-__device__ __forceinline__ uint64_t funnel64(uint64_t lo, uint64_t hi, uint32_t o) {
-  return o ? (lo >> (8 * o)) | (hi << (64 - 8 * o)) : lo;
+// keep bytes [b0, b1) of an 8-byte word (0 <= b0, b1 <= 8)
+__device__ __forceinline__ uint64_t bytes_mask(int b0, int b1) {
+  if (b1 <= b0) return 0ull;
+  const uint64_t hi = b1 >= 8 ? ~0ull : ((1ull << (8 * b1)) - 1ull);
+  return hi & (~0ull << (8 * b0));
 }
-
-// Byte equality of two keys of length len by the whole warp: lane l compares
-// bytes [8l, 8l+8) and [8l+256, 8l+264) of each 512-byte step, with both
-// steps' loads in flight together.  Only aligned 8-byte words that hold a key
-// byte are read.
-__device__ __forceinline__ bool warp_equal(const uint8_t* r, const uint8_t* s, uint64_t len) {
+// Byte equality of the len-byte keys at aR + r0 and aS + s0 by the whole
+// warp, 512 bytes per step: lane l compares the 16-byte aligned S chunk l of
+// the step with the 16 R bytes under it (from the two aligned R chunks that
+// hold them).  Only aligned chunks that hold a key byte are read; the first R
+// chunk is clamped to the arena's start (its bytes before the key are masked).
+__device__ __forceinline__ bool warp_equal(const uint8_t* __restrict__ aR, uint64_t r0,
+                                           const uint8_t* __restrict__ aS, uint64_t s0, uint64_t len) {
   const int lane = threadIdx.x & 31;
-  const uintptr_t ra = reinterpret_cast<uintptr_t>(r), sa = reinterpret_cast<uintptr_t>(s);
-  const uint32_t ro = (uint32_t)(ra & 7u), so = (uint32_t)(sa & 7u);
-  const uint64_t* rw = reinterpret_cast<const uint64_t*>(ra - ro);
-  const uint64_t* sw = reinterpret_cast<const uint64_t*>(sa - so);
-  const uint64_t rend = ro + len, send = so + len;
-  for (uint64_t b = 0; b < len; b += 512) {
-    const uint64_t wa = (b >> 3) + (uint64_t)lane, wb = wa + 32;
-    const uint64_t ra0 = word_or0(rw, wa, rend), rb0 = word_or0(rw, wb, rend);
-    const uint64_t sa0 = word_or0(sw, wa, send), sb0 = word_or0(sw, wb, send);
-    const uint64_t rtail = lane == 31 ? word_or0(rw, wb + 1, rend) : 0;
-    const uint64_t stail = lane == 31 ? word_or0(sw, wb + 1, send) : 0;
-    uint64_t ra1 = __shfl_down_sync(kFull, ra0, 1), sa1 = __shfl_down_sync(kFull, sa0, 1);
-    uint64_t rb1 = __shfl_down_sync(kFull, rb0, 1), sb1 = __shfl_down_sync(kFull, sb0, 1);
-    const uint64_t rnext = __shfl_sync(kFull, rb0, 0), snext = __shfl_sync(kFull, sb0, 0);
-    if (lane == 31) {
-      ra1 = rnext; sa1 = snext;
-      rb1 = rtail; sb1 = stail;
+  const uint64_t se = s0 + len, re = r0 + len;
+  const uint32_t d = (uint32_t)((r0 - s0) & 15u);
+  const uint32_t hsel = d >> 3, sh = 8u * (d & 7u);
+  for (uint64_t base = s0 & ~15ull; base < se; base += 512) {
+    const uint64_t c = base + 16 * (uint64_t)lane;
+    const int64_t q = (int64_t)(c + r0 - s0) - (int64_t)d;
+    const uint4 sw = c < se ? ld16(aS + c) : make_uint4(0, 0, 0, 0);
+    const uint4 ra = (q + 16 > (int64_t)r0 && q < (int64_t)re) ? ld16(aR + (q < 0 ? 0 : q)) : make_uint4(0, 0, 0, 0);
+    const uint4 rb = (q + 16 < (int64_t)re) ? ld16(aR + q + 16) : make_uint4(0, 0, 0, 0);
+    const uint64_t A0 = lo64(ra), A1 = hi64(ra), B0 = lo64(rb), B1 = hi64(rb);
+    const uint64_t p0 = hsel ? A1 : A0, p1 = hsel ? B0 : A1, p2 = hsel ? B1 : B0;
+    uint64_t x0 = fsh64(p0, p1, sh) ^ lo64(sw);
+    uint64_t x1 = fsh64(p1, p2, sh) ^ hi64(sw);
+    if (c < s0 || c + 16 > se) {
+      const int b0 = c < s0 ? (int)(s0 - c) : 0;
+      const int b1 = c >= se ? 0 : (c + 16 > se ? (int)(se - c) : 16);
+      x0 &= bytes_mask(b0, b1 < 8 ? b1 : 8);
+      x1 &= bytes_mask(b0 > 8 ? b0 - 8 : 0, b1 > 8 ? b1 - 8 : 0);
     }
-    const uint64_t pa = b + 8 * (uint64_t)lane, pb = pa + 256;
-    const uint64_t na = len > pa ? len - pa : 0, nb = len > pb ? len - pb : 0;
-    const uint64_t ma = na >= 8 ? ~0ull : ((1ull << (8 * na)) - 1ull);
-    const uint64_t mb = nb >= 8 ? ~0ull : ((1ull << (8 * nb)) - 1ull);
-    const bool eq = ((funnel64(ra0, ra1, ro) ^ funnel64(sa0, sa1, so)) & ma) == 0 &&
-                    ((funnel64(rb0, rb1, ro) ^ funnel64(sb0, sb1, so)) & mb) == 0;
-    if (!__all_sync(kFull, eq)) return false;
+    if (!__all_sync(kFull, (x0 | x1) == 0)) return false;
   }
   return true;
 }
@@ -493,7 +493,7 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         const uint64_t srow = __shfl_sync(kFull, i, j);
         const uint64_t rs = __ldg(P.offR + rj);
         const uint64_t rl = __ldg(P.offR + rj + 1) - rs;
-        if (rl == lj && warp_equal(P.arenaR + rs, P.arenaS + stj, lj)) {
+        if (rl == lj && warp_equal(P.arenaR, rs, P.arenaS, stj, lj)) {
           if (lane == j) matched = true;
           if (!batch && (P.mode == AS_JOIN_SEMI || P.mode == AS_JOIN_ANTI)) continue;   // rows, not pairs
           const int jj = __shfl_sync(kFull, jn, j);
@@ -671,7 +671,7 @@ __global__ void __launch_bounds__(kVThreads, 4) bl_verify_kernel(BVerifyParams P
         const uint64_t lj = __shfl_sync(kFull, len, j);
         const uint64_t sj = __shfl_sync(kFull, start, j);
         const uint64_t rsj = __shfl_sync(kFull, rs, j);
-        if (warp_equal(P.arenaR + rsj, P.arenaS + sj, lj)) {
+        if (warp_equal(P.arenaR, rsj, P.arenaS, sj, lj)) {
           if (lane == 0) {
             const uint64_t srow = grp * 32 + (uint64_t)j;
             const uint32_t rid = P.idR ? __ldg(P.idR + rj) : rj;
