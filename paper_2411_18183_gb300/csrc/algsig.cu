@@ -16,6 +16,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "../../include/algsig.h"
@@ -144,10 +145,11 @@ __global__ void batch_bytes_kernel(BatchJoin* J, int nj, const uint64_t* __restr
 
 // Signatures of actual keys [k_lo, k_hi) of one relation; key k's signature
 // goes to sig_out[k + out_shift] (out_shift = virtual minus actual row).
+template <class Cursor>
 __device__ __forceinline__ void sig_walk(const uint8_t* __restrict__ arena, const uint64_t* __restrict__ off,
                                          uint64_t k_lo, uint64_t k_hi, uint64_t out_shift,
                                          uint64_t* __restrict__ sig_out, uint8_t* bufs, const uint16_t* ctab,
-                                         const RedCursor& rc) {
+                                         const Cursor& rc) {
   const int lane = threadIdx.x & 31;
   // rounds r and r+1 are in flight before round r is computed
   Plan cur = plan_round(plan_load(off, k_lo, k_hi), k_lo, k_hi, 0);
@@ -226,9 +228,18 @@ __device__ __forceinline__ uint64_t vcut_in_join(const BatchJoin* J, const uint6
   return v0 + (k - b);
 }
 
+// Shared-memory address of the start of dynamic shared memory (one probe per
+// device decides whether the tables can be addressed at the fixed 0x400).
+__device__ uint32_t g_dyn_smem_base;
+__global__ void dyn_smem_base_kernel() {
+  extern __shared__ __align__(16) uint8_t smem[];
+  if (threadIdx.x == 0) g_dyn_smem_base = (uint32_t)__cvta_generic_to_shared(smem);
+}
+
 // Signatures of all keys of a relation (J == nullptr), or of the rows of a
 // batch's joins (S_SIDE picks the relation), byte-balanced over the warps.
-template <bool S_SIDE>
+// AT400: the reduction tables sit at shared address 0x400 (RedCursorAt400).
+template <bool S_SIDE, bool AT400>
 __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restrict__ arena,
                                                           const uint64_t* __restrict__ off, uint64_t n,
                                                           uint64_t* __restrict__ sig_out,
@@ -240,7 +251,9 @@ __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restr
     reinterpret_cast<uint32_t*>(ctab)[i] = reinterpret_cast<const uint32_t*>(g_const)[i];
   init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
   const int wib = threadIdx.x >> 5;
-  const RedCursor rc = red_cursor(red);
+  using Cursor = typename std::conditional<AT400, RedCursorAt400, RedCursor>::type;
+  Cursor rc;
+  if constexpr (AT400) rc = red_cursor_at400(); else rc = red_cursor(red);
   uint8_t* bufs = smem + kSmemTables + kConstBytes + (size_t)wib * 2 * kBufBytes;
   const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
   const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
@@ -714,7 +727,18 @@ struct DeviceState {
   bool ready = false;
   int sms = 0;
   int verify_blocks_per_sm = 1;
+  bool tables_at400 = false;   // dynamic shared memory starts at shared address 0x400
 };
+
+// launch the signature kernel instantiation that matches the device
+template <bool S_SIDE>
+static void launch_sig_kernel(const DeviceState* d, unsigned blocks, cudaStream_t s, const uint8_t* arena,
+                              const uint64_t* off, uint64_t n, uint64_t* out, const BatchJoin* J, int nj) {
+  if (d->tables_at400)
+    sig_kernel<S_SIDE, true><<<blocks, kThreads, kSmemSig, s>>>(arena, off, n, out, J, nj);
+  else
+    sig_kernel<S_SIDE, false><<<blocks, kThreads, kSmemSig, s>>>(arena, off, n, out, J, nj);
+}
 
 static std::mutex g_dev_mu;
 static DeviceState g_dev[kMaxDevices];
@@ -763,12 +787,25 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaMemcpyToSymbol(g_const, h_const, sizeof(h_const))) != cudaSuccess) return cuda_fail(e, "table setup");
     if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return cuda_fail(e, "device query");
-    if ((e = cudaFuncSetAttribute(sig_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
+    {
+      const void* fns[4] = {reinterpret_cast<const void*>(sig_kernel<false, false>),
+                            reinterpret_cast<const void*>(sig_kernel<false, true>),
+                            reinterpret_cast<const void*>(sig_kernel<true, false>),
+                            reinterpret_cast<const void*>(sig_kernel<true, true>)};
+      for (const void* f : fns)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) != cudaSuccess)
+          return cuda_fail(e, "kernel attribute");
+    }
+    // where dynamic shared memory starts (the tables are its first bytes)
+    if ((e = cudaFuncSetAttribute(dyn_smem_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
-    if ((e = cudaFuncSetAttribute(sig_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
-        cudaSuccess)
-      return cuda_fail(e, "kernel attribute");
+    dyn_smem_base_kernel<<<1, 32, kSmemSig>>>();
+    uint32_t base = 0;
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "shared memory probe");
+    if ((e = cudaMemcpyFromSymbol(&base, g_dyn_smem_base, sizeof(base))) != cudaSuccess)
+      return cuda_fail(e, "shared memory probe");
+    d.tables_at400 = base == kTablesAt400;
     if ((e = cudaFuncSetAttribute(bl_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBHash)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
@@ -815,7 +852,7 @@ static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t 
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
   if (n == 0) return AS_OK;
-  sig_kernel<false><<<walk_blocks(n, d->sms), kThreads, kSmemSig, s>>>(arena, off, n, out, nullptr, 0);
+  launch_sig_kernel<false>(d, walk_blocks(n, d->sms), s, arena, off, n, out, nullptr, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "signature kernel launch");
   return AS_OK;
@@ -1275,14 +1312,14 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
   if ((e = cudaMemsetAsync(d_counts, 0, 8 * b->n_joins, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
   batch_bytes_kernel<<<1, 1024, 0, s>>>(J, nj, d_offR, d_offS);
   if (b->mR > 0) {
-    sig_kernel<false><<<walk_blocks(b->mR, d->sms), kThreads, kSmemSig, s>>>(d_arenaR, d_offR, b->mR, b->sigR, J, nj);
+    launch_sig_kernel<false>(d, walk_blocks(b->mR, d->sms), s, d_arenaR, d_offR, b->mR, b->sigR, J, nj);
     uint64_t blocks = (b->mR + 255) / 256;
     const uint64_t lim = (uint64_t)d->sms * 16;
     if (blocks > lim) blocks = lim;
     build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, 0, b->sigR, d_offR, b->mR, b->flags, J, nj);
   }
   if (b->nS > 0) {
-    sig_kernel<true><<<walk_blocks(b->nS, d->sms), kThreads, kSmemSig, s>>>(d_arenaS, d_offS, b->nS, b->sigS, J, nj);
+    launch_sig_kernel<true>(d, walk_blocks(b->nS, d->sms), s, d_arenaS, d_offS, b->nS, b->sigS, J, nj);
     VerifyParams P;
     P.slots = slots;
     P.mask = 0;

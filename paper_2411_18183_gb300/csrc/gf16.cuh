@@ -70,17 +70,38 @@ __device__ __forceinline__ uint32_t tab_index(uint32_t u, uint32_t base, uint32_
   return r;
 }
 
-// Per-lane table cursor: shared byte address of the tables, the lane's two
-// offsets (4*l and 4*l + 128) and the PRMT selectors.
+// Per-lane table cursors: the lane's two offsets (4*l and 4*l + 128), and
+// the load of the word at byte offset idx of the tables.  RedCursor takes the
+// tables' shared address at run time; RedCursorAt400 has it as the load's
+// immediate offset (one add less per lookup), valid when the tables start the
+// dynamic shared memory and that begins right after the 1 KB every block
+// reserves (shared address 0x400; the host checks this once per device).
 struct RedCursor {
   uint32_t tab;       // shared byte address of the tables
   uint32_t off16;     // 4*lane
   uint32_t off24;     // 4*lane + 128
+  __device__ __forceinline__ uint32_t load(uint32_t idx) const { return lds32(tab + idx); }
 };
+struct RedCursorAt400 {
+  uint32_t off16;
+  uint32_t off24;
+  __device__ __forceinline__ uint32_t load(uint32_t idx) const {
+    uint32_t v;
+    asm volatile("ld.shared.u32 %0, [%1+1024];" : "=r"(v) : "r"(idx));
+    return v;
+  }
+};
+constexpr uint32_t kTablesAt400 = 0x400u;
 
 __device__ __forceinline__ RedCursor red_cursor(const uint32_t* red) {
   RedCursor c;
   c.tab = (uint32_t)__cvta_generic_to_shared(red);
+  c.off16 = 4u * (threadIdx.x & 31u);
+  c.off24 = c.off16 + 128u;
+  return c;
+}
+__device__ __forceinline__ RedCursorAt400 red_cursor_at400() {
+  RedCursorAt400 c;
   c.off16 = 4u * (threadIdx.x & 31u);
   c.off24 = c.off16 + 128u;
   return c;
@@ -92,23 +113,26 @@ constexpr uint32_t kSel16 = 0x5524u;
 constexpr uint32_t kSel24 = 0x5534u;
 
 // 32-bit unreduced value -> 16-bit residue mod P
-__device__ __forceinline__ uint32_t red32(uint32_t u, const RedCursor& c) {
-  const uint32_t t16 = lds32(c.tab + tab_index(u, c.off16, kSel16));
-  const uint32_t t24 = lds32(c.tab + tab_index(u, c.off24, kSel24));
+template <class Cursor>
+__device__ __forceinline__ uint32_t red32(uint32_t u, const Cursor& c) {
+  const uint32_t t16 = c.load(tab_index(u, c.off16, kSel16));
+  const uint32_t t24 = c.load(tab_index(u, c.off24, kSel24));
   return u ^ t16 ^ t24;
 }
 
 // value < 2^24 -> 16-bit residue (only bits 16..23 to clear)
-__device__ __forceinline__ uint32_t red24(uint32_t u, const RedCursor& c) {
-  return u ^ lds32(c.tab + tab_index(u, c.off16, kSel16));
+template <class Cursor>
+__device__ __forceinline__ uint32_t red24(uint32_t u, const Cursor& c) {
+  return u ^ c.load(tab_index(u, c.off16, kSel16));
 }
 
 // One Horner step over a 16-byte chunk: acc_k <- acc_k * x^(8k) + sum_j q_j x^(kj),
 // where q_{2t} = low half of word t and q_{2t+1} = high half of word t.
 // Accumulators enter and leave reduced (< 2^16).
+template <class Cursor>
 __device__ __forceinline__ void horner_chunk(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
                                              uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& a4,
-                                             const RedCursor& rc) {
+                                             const Cursor& rc) {
   const uint32_t l0 = v0 & 0xFFFFu, h0 = v0 >> 16;
   const uint32_t l1 = v1 & 0xFFFFu, h1 = v1 >> 16;
   const uint32_t l2 = v2 & 0xFFFFu, h2 = v2 >> 16;

@@ -280,8 +280,9 @@ __device__ __forceinline__ void keep_below(uint32_t e, uint64_t& lo64, uint64_t&
 
 // Unreduced-free tile signature: a_k = sum over the tile's slots t of q_t x^(k t)
 // (slot 0 = first byte pair of the tile's first realigned chunk), reduced to 16 bits.
+template <class Cursor>
 __device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t span_lo, const Plan& p,
-                                                const RedCursor& redl, uint32_t& a1, uint32_t& a2,
+                                                const Cursor& redl, uint32_t& a1, uint32_t& a2,
                                                 uint32_t& a3, uint32_t& a4) {
   a1 = a2 = a3 = a4 = 0;
   if (p.nc == 0) return;
@@ -362,7 +363,8 @@ __device__ __forceinline__ uint64_t mul_scan(const uint16_t* ctab, uint64_t v, i
 }
 
 // x^-(k lo/2) * P, component-wise
-__device__ __forceinline__ uint64_t lo_correct(const uint16_t* ctab, uint64_t P, uint32_t lo, const RedCursor& rc) {
+template <class Cursor>
+__device__ __forceinline__ uint64_t lo_correct(const uint16_t* ctab, uint64_t P, uint32_t lo, const Cursor& rc) {
   const uint16_t* inv32 = ctab + 20 * 512;
   uint64_t out = 0;
 #pragma unroll
