@@ -420,37 +420,54 @@ __device__ __forceinline__ bool warp_equal(const uint8_t* __restrict__ aR, uint6
   return true;
 }
 
-__device__ __forceinline__ void flush_stage(const uint64_t* stage, uint32_t np, const VerifyParams& P) {
+// Verified pairs staged per warp as rows; their ids are looked up when the
+// stage is flushed, by all lanes at once (a per-pair lookup would make the
+// warp wait on memory once more per pair).
+struct Stage {
+  uint32_t r[kVStage];     // R row, or AS_NO_ROW
+  uint64_t s[kVStage];     // S row
+};
+
+// ids of a staged pair; without ids the rows count from rb / sb
+__device__ __forceinline__ uint64_t pair_ids(uint32_t r, uint64_t s, const uint32_t* idR, const uint32_t* idS,
+                                             uint64_t rb, uint64_t sb) {
+  const uint32_t rid = r == AS_NO_ROW ? AS_NO_ROW : (idR ? __ldg(idR + r) : (uint32_t)(r - rb));
+  const uint32_t sid = idS ? __ldg(idS + s) : (uint32_t)(s - sb);
+  return (uint64_t)rid | ((uint64_t)sid << 32);
+}
+
+__device__ __forceinline__ void flush_stage(const Stage& st, uint32_t np, const VerifyParams& P) {
   const int lane = threadIdx.x & 31;
   unsigned long long base = 0;
   if (lane == 0) base = atomicAdd(P.count, (unsigned long long)np);
   base = __shfl_sync(kFull, base, 0);
   for (uint32_t i = (uint32_t)lane; i < np; i += 32) {
     const unsigned long long idx = base + i;
-    if (idx < P.cap) reinterpret_cast<uint64_t*>(P.pairs)[idx] = stage[i];
+    if (idx < P.cap) reinterpret_cast<uint64_t*>(P.pairs)[idx] = pair_ids(st.r[i], st.s[i], P.idR, P.idS, 0, 0);
   }
   __syncwarp();
 }
 
 // flush for join j of a batch: its counter, region and capacity
-__device__ __forceinline__ void flush_stage_join(const uint64_t* stage, uint32_t np, const VerifyParams& P, int j) {
+__device__ __forceinline__ void flush_stage_join(const Stage& st, uint32_t np, const VerifyParams& P, int j) {
   const int lane = threadIdx.x & 31;
   unsigned long long base = 0;
   if (lane == 0) base = atomicAdd(P.counts + j, (unsigned long long)np);
   base = __shfl_sync(kFull, base, 0);
   const uint64_t off = __ldg(&P.J[j].pair_off), cap = __ldg(&P.J[j].pair_cap);
+  const uint64_t rb = __ldg(&P.J[j].r_begin), sb = __ldg(&P.J[j].s_begin);
   for (uint32_t i = (uint32_t)lane; i < np; i += 32) {
     const unsigned long long idx = base + i;
-    if (idx < cap) reinterpret_cast<uint64_t*>(P.pairs)[off + idx] = stage[i];
+    if (idx < cap) reinterpret_cast<uint64_t*>(P.pairs)[off + idx] = pair_ids(st.r[i], st.s[i], P.idR, P.idS, rb, sb);
   }
   __syncwarp();
 }
 
 template <bool BATCH>
 __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
-  __shared__ uint64_t stage_all[kVWarps][kVStage];
+  __shared__ Stage stage_all[kVWarps];
   const int lane = threadIdx.x & 31;
-  uint64_t* stage = stage_all[threadIdx.x >> 5];
+  Stage& stage = stage_all[threadIdx.x >> 5];
   uint32_t np = 0;                                   // staged pairs (warp-uniform)
   int sj = -1;                                       // batch: join of the staged pairs
   constexpr bool batch = BATCH;
@@ -516,9 +533,8 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
           }
           sj = jj;
           if (lane == 0) {
-            const uint32_t rid = P.idR ? __ldg(P.idR + rj) : (uint32_t)(rj - (batch ? __ldg(&P.J[jj].r_begin) : 0));
-            const uint32_t sid = P.idS ? __ldg(P.idS + srow) : (uint32_t)(srow - (batch ? __ldg(&P.J[jj].s_begin) : 0));
-            stage[np] = (uint64_t)rid | ((uint64_t)sid << 32);
+            stage.r[np] = rj;
+            stage.s[np] = srow;
           }
           __syncwarp();
           if (++np == (uint32_t)kVStage) {
@@ -537,8 +553,9 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
           np = 0;
         }
         if (emit) {
-          const uint32_t sid = P.idS ? __ldg(P.idS + i) : (uint32_t)i;
-          stage[np + __popc(em & lanemask_lt())] = (uint64_t)AS_NO_ROW | ((uint64_t)sid << 32);
+          const uint32_t pos = np + __popc(em & lanemask_lt());
+          stage.r[pos] = AS_NO_ROW;
+          stage.s[pos] = i;
         }
         np += (uint32_t)__popc(em);
         __syncwarp();
@@ -638,13 +655,15 @@ struct BVerifyParams {
 };
 
 __global__ void __launch_bounds__(kVThreads, 4) bl_verify_kernel(BVerifyParams P) {
-  __shared__ uint64_t stage_all[kVWarps][kVStage];
+  __shared__ Stage stage_all[kVWarps];
   const int lane = threadIdx.x & 31;
-  uint64_t* stage = stage_all[threadIdx.x >> 5];
+  Stage& stage = stage_all[threadIdx.x >> 5];
   VerifyParams VP;                                  // for flush_stage
   VP.pairs = P.pairs;
   VP.cap = P.cap;
   VP.count = P.count;
+  VP.idR = P.idR;
+  VP.idS = P.idS;
   uint32_t np = 0;
   const uint64_t ngroups = (P.n + 31) / 32;
   const uint64_t nwarps = (uint64_t)gridDim.x * kVWarps;
@@ -686,10 +705,8 @@ __global__ void __launch_bounds__(kVThreads, 4) bl_verify_kernel(BVerifyParams P
         const uint64_t rsj = __shfl_sync(kFull, rs, j);
         if (warp_equal(P.arenaR, rsj, P.arenaS, sj, lj)) {
           if (lane == 0) {
-            const uint64_t srow = grp * 32 + (uint64_t)j;
-            const uint32_t rid = P.idR ? __ldg(P.idR + rj) : rj;
-            const uint32_t sid = P.idS ? __ldg(P.idS + srow) : (uint32_t)srow;
-            stage[np] = (uint64_t)rid | ((uint64_t)sid << 32);
+            stage.r[np] = rj;
+            stage.s[np] = grp * 32 + (uint64_t)j;
           }
           __syncwarp();
           if (++np == (uint32_t)kVStage) {
