@@ -299,6 +299,23 @@ def length_sweep_leg(ag, reps: int = 5):
             "rows": out}
 
 
+# --------------------------------------------------------------------------- replicas on N GPUs
+
+def max_over_ranks(dist, x: float, device) -> float:
+    """The largest x over the ranks (the slowest replica's time); x itself on one rank."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_value(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job throughput of `world` replicas: all ranks' units over the slowest rank's time."""
+    return world * units_per_rank / (max_ms * 1e-3)
+
+
 # --------------------------------------------------------------------------- GPU arm
 
 def run_gpu(args):
@@ -321,12 +338,8 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(x: float) -> float:
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    def ranks_max(x: float) -> float:
+        return max_over_ranks(dist, x, "cuda")
 
     spec = workloads.CONFIGS[args.workload]
     t_gen = time.perf_counter()
@@ -408,9 +421,9 @@ def run_gpu(args):
     total_ms = t0.elapsed_time(t1)
     phase_ms = {ph: [e[i].elapsed_time(e[i + 1]) for e in ev] for i, ph in enumerate(PH)}
     step_ms = [e[0].elapsed_time(e[len(PH)]) for e in ev]
-    total_ms = max_over_ranks(total_ms)
+    total_ms = ranks_max(total_ms)
     ms_per_step = total_ms / args.steps
-    value = world * n / (ms_per_step * 1e-3)
+    value = replica_value(n, world, ms_per_step)
 
     # the same-GPU comparison join on full strings (plain and tagged variants)
     bws = ag.alloc_ws(ag.baseline_ws_bytes(m, n, lf))
@@ -457,8 +470,8 @@ def run_gpu(args):
     for _ in range(e2e_steps):
         cnt = sj.run(hR, hS, cuts, out_host)
     barrier()
-    e2e_s = max_over_ranks((time.perf_counter() - te) / e2e_steps)
-    e2e_value = world * n / e2e_s
+    e2e_s = ranks_max((time.perf_counter() - te) / e2e_steps)
+    e2e_value = replica_value(n, world, e2e_s * 1e3)
     d2h = 8 * cnt + 8 * (len(cuts) - 1)
     del sj
 
