@@ -389,12 +389,13 @@ __device__ __forceinline__ uint64_t bytes_mask(int b0, int b1) {
   return hi & (~0ull << (8 * b0));
 }
 // Byte equality of the len-byte keys at aR + r0 and aS + s0 by the whole
-// warp, 512 bytes per step: lane l compares the 16-byte aligned S chunk l of
-// the step with the 16 R bytes under it (from the two aligned R chunks that
-// hold them).  Only aligned chunks that hold a key byte are read; the first R
-// chunk is clamped to the arena's start (its bytes before the key are masked).
-__device__ __forceinline__ bool warp_equal(const uint8_t* __restrict__ aR, uint64_t r0,
-                                           const uint8_t* __restrict__ aS, uint64_t s0, uint64_t len) {
+// warp, 512 bytes per step, in 64-bit offsets (keys of 2^32 - 64 bytes and
+// more): lane l compares the 16-byte aligned S chunk l of the step with the 16
+// R bytes under it (from the two aligned R chunks that hold them).  Only
+// aligned chunks that hold a key byte are read; the first R chunk is clamped
+// to the arena's start (its bytes before the key are masked).
+__device__ __noinline__ bool warp_equal_wide(const uint8_t* __restrict__ aR, uint64_t r0,
+                                             const uint8_t* __restrict__ aS, uint64_t s0, uint64_t len) {
   const int lane = threadIdx.x & 31;
   const uint64_t se = s0 + len, re = r0 + len;
   const uint32_t d = (uint32_t)((r0 - s0) & 15u);
@@ -416,6 +417,78 @@ __device__ __forceinline__ bool warp_equal(const uint8_t* __restrict__ aR, uint6
       x1 &= bytes_mask(b0 > 8 ? b0 - 8 : 0, b1 > 8 ? b1 - 8 : 0);
     }
     if (!__all_sync(kFull, (x0 | x1) == 0)) return false;
+  }
+  return true;
+}
+
+// Keys below this length are compared with 32-bit offsets (warp_equal).
+constexpr uint32_t kNarrowLen = 0xFFFFFFC0u;
+
+// emask[e]: the first e bytes of a 16-byte chunk (e = 0..16), in shared memory.
+__device__ __forceinline__ void fill_emask(uint4* emask) {
+  for (int e = threadIdx.x; e <= 16; e += blockDim.x) {
+    uint32_t w[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int b = e - 4 * j;
+      w[j] = b <= 0 ? 0u : (b >= 4 ? ~0u : ((1u << (8 * b)) - 1u));
+    }
+    emask[e] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
+}
+
+// Byte equality of the len-byte keys at pR and pS (len < kNarrowLen) by the
+// whole warp, 512 bytes per step.  Offsets count from the aligned chunk bS
+// that holds the S key's first byte: S key bytes are [sa, sa + len); bR is
+// the aligned R chunk that holds the R byte matching bS + 0 minus its
+// misalignment d, so that lane l's S chunk [off, off + 16) meets the R bytes
+// [off + d, off + d + 16) of the two aligned R chunks at bR + off and
+// bR + off + 16, realigned by a funnel shift of d bytes (the word part of d is
+// warp-uniform).  Only aligned chunks that hold a key byte are read.  Only the
+// steps that hold the key's first or last byte apply byte masks.
+__device__ __forceinline__ bool warp_equal(const uint8_t* __restrict__ pR, const uint8_t* __restrict__ pS,
+                                           uint32_t len, const uint4* __restrict__ emask) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t sa = (uint32_t)reinterpret_cast<uintptr_t>(pS) & 15u;
+  const uint32_t d = (uint32_t)(reinterpret_cast<uintptr_t>(pR) - sa) & 15u;
+  const uint8_t* bS = pS - sa;
+  const uint8_t* bR = pR - sa - d;
+  const uint32_t sh = 8u * (d & 3u);
+  const uint32_t kend = sa + len;                  // S key bytes: [sa, kend) from bS
+  const uint32_t rlo = sa + d, rend = kend + d;    // R key bytes: [rlo, rend) from bR
+  for (uint32_t base = 0; base < kend; base += 512u) {
+    const uint32_t off = base + 16u * lane;
+    uint4 sv = make_uint4(0, 0, 0, 0), ra = sv, rb = sv;
+    if (off < kend) sv = ld16(bS + off);
+    if (off + 16u > rlo && off < rend) ra = ld16(bR + off);
+    if (off + 16u < rend) rb = ld16(bR + off + 16u);
+    uint32_t r0, r1, r2, r3;
+    switch (d >> 2) {                              // warp-uniform
+      case 0:
+        r0 = __funnelshift_r(ra.x, ra.y, sh); r1 = __funnelshift_r(ra.y, ra.z, sh);
+        r2 = __funnelshift_r(ra.z, ra.w, sh); r3 = __funnelshift_r(ra.w, rb.x, sh);
+        break;
+      case 1:
+        r0 = __funnelshift_r(ra.y, ra.z, sh); r1 = __funnelshift_r(ra.z, ra.w, sh);
+        r2 = __funnelshift_r(ra.w, rb.x, sh); r3 = __funnelshift_r(rb.x, rb.y, sh);
+        break;
+      case 2:
+        r0 = __funnelshift_r(ra.z, ra.w, sh); r1 = __funnelshift_r(ra.w, rb.x, sh);
+        r2 = __funnelshift_r(rb.x, rb.y, sh); r3 = __funnelshift_r(rb.y, rb.z, sh);
+        break;
+      default:
+        r0 = __funnelshift_r(ra.w, rb.x, sh); r1 = __funnelshift_r(rb.x, rb.y, sh);
+        r2 = __funnelshift_r(rb.y, rb.z, sh); r3 = __funnelshift_r(rb.z, rb.w, sh);
+        break;
+    }
+    uint32_t x0 = r0 ^ sv.x, x1 = r1 ^ sv.y, x2 = r2 ^ sv.z, x3 = r3 ^ sv.w;
+    if ((base == 0u && sa != 0u) || base + 512u > kend) {   // warp-uniform: the key's first or last byte
+      const uint32_t lo = off < sa ? sa - off : 0u;
+      const uint32_t hi = off < kend ? (kend - off < 16u ? kend - off : 16u) : 0u;
+      const uint4 mh = emask[hi], ml = emask[lo];
+      x0 &= mh.x & ~ml.x; x1 &= mh.y & ~ml.y; x2 &= mh.z & ~ml.z; x3 &= mh.w & ~ml.w;
+    }
+    if (__any_sync(kFull, (x0 | x1 | x2 | x3) != 0u)) return false;
   }
   return true;
 }
@@ -466,6 +539,9 @@ __device__ __forceinline__ void flush_stage_join(const Stage& st, uint32_t np, c
 template <bool BATCH>
 __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
   __shared__ Stage stage_all[kVWarps];
+  __shared__ uint4 emask[17];
+  fill_emask(emask);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   Stage& stage = stage_all[threadIdx.x >> 5];
   uint32_t np = 0;                                   // staged pairs (warp-uniform)
@@ -518,12 +594,18 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         const int j = __ffs(cm) - 1;
         cm &= cm - 1;
         const uint32_t rj = __shfl_sync(kFull, row, j);
-        const uint64_t lj = __shfl_sync(kFull, len, j);
+        const uint32_t lj = __shfl_sync(kFull, l32, j);   // the slot holds the same length
         const uint64_t stj = __shfl_sync(kFull, start, j);
-        const uint64_t srow = __shfl_sync(kFull, i, j);
         const uint64_t rs = __ldg(P.offR + rj);
-        const uint64_t rl = __ldg(P.offR + rj + 1) - rs;
-        if (rl == lj && warp_equal(P.arenaR, rs, P.arenaS, stj, lj)) {
+        bool eq;
+        if (lj < kNarrowLen) {
+          eq = warp_equal(P.arenaR + rs, P.arenaS + stj, lj, emask);
+        } else {                                      // lengths that the slot's 32-bit field saturates
+          const uint64_t ls = __shfl_sync(kFull, len, j);
+          eq = __ldg(P.offR + rj + 1) - rs == ls && warp_equal_wide(P.arenaR, rs, P.arenaS, stj, ls);
+        }
+        if (eq) {
+          const uint64_t srow = __shfl_sync(kFull, i, j);
           if (lane == j) matched = true;
           if (!batch && (P.mode == AS_JOIN_SEMI || P.mode == AS_JOIN_ANTI)) continue;   // rows, not pairs
           const int jj = __shfl_sync(kFull, jn, j);
@@ -656,6 +738,9 @@ struct BVerifyParams {
 
 __global__ void __launch_bounds__(kVThreads, 4) bl_verify_kernel(BVerifyParams P) {
   __shared__ Stage stage_all[kVWarps];
+  __shared__ uint4 emask[17];
+  fill_emask(emask);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
   Stage& stage = stage_all[threadIdx.x >> 5];
   VerifyParams VP;                                  // for flush_stage
@@ -703,7 +788,9 @@ __global__ void __launch_bounds__(kVThreads, 4) bl_verify_kernel(BVerifyParams P
         const uint64_t lj = __shfl_sync(kFull, len, j);
         const uint64_t sj = __shfl_sync(kFull, start, j);
         const uint64_t rsj = __shfl_sync(kFull, rs, j);
-        if (warp_equal(P.arenaR, rsj, P.arenaS, sj, lj)) {
+        const bool eq = lj < kNarrowLen ? warp_equal(P.arenaR + rsj, P.arenaS + sj, (uint32_t)lj, emask)
+                                        : warp_equal_wide(P.arenaR, rsj, P.arenaS, sj, lj);
+        if (eq) {
           if (lane == 0) {
             stage.r[np] = rj;
             stage.s[np] = grp * 32 + (uint64_t)j;

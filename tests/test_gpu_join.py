@@ -193,3 +193,28 @@ def test_probe_modes_match_oracle(cuda, mode):
         cnt = ag.join_probe_mode(t, S, sigS, pairs, count, mode=mode)
         got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
         assert np.array_equal(got, want), (mode, Rh.n, Sh.n)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_signature_collisions_rejected_at_every_alignment(cuda, seed):
+    """Equal-length keys that share all four signature components but differ
+    in five symbols reach the byte comparison as candidates; at any start
+    alignment of either key (random gap keys of 0..16 bytes before each key),
+    with differences in the first and last symbols and across 512-byte
+    comparison steps, and at odd lengths, only exact copies may join."""
+    from packing import interleave_gaps
+    rng = random.Random(1000 + seed)
+    shapes = [(5, (0, 1, 2, 3, 4)), (8, (0, 2, 4, 6, 7)), (24, (1, 4, 9, 15, 22)),
+              (256, (0, 100, 200, 254, 255)), (257, (3, 255, 256, 100, 7)), (520, (0, 255, 256, 511, 519)),
+              (700, (10, 300, 512, 600, 650))]
+    rkeys, skeys = [], []
+    for n_sym, pos in shapes:
+        a, b = five_symbol_collision(n_sym, pos, seed=rng.randrange(1 << 30))
+        rkeys += [a]
+        skeys += [b, a]
+        if max(pos) < n_sym - 1:                      # odd length: drop the last (equal) byte of both
+            rkeys += [a[:-1]]
+            skeys += [b[:-1], a[:-1]]
+    R = relation_garbage_tail(interleave_gaps(rkeys, seed=rng.randrange(1 << 30)), seed=seed)
+    S = relation_garbage_tail(interleave_gaps(skeys, seed=rng.randrange(1 << 30)), seed=seed + 1)
+    check(cuda, R, S)
