@@ -446,6 +446,44 @@ def run_gpu(args):
         baseline["tagged" if tagged else "plain"] = {"ms_per_join": bms, "tuples_per_s": n / (bms * 1e-3)}
     del bws
 
+    # the paper's own variants on the same resident inputs: the probe of Figure 2 on
+    # signatures only (no byte verification; its extra pairs are signature collisions),
+    # with four components and with the paper's two (sig_{alpha,2}), and the exact
+    # join on two-component signatures
+    def variant(ncomp, mode):
+        def run():
+            ag.sig_compute(dR, sigR, stream=stream, n_components=ncomp)
+            t = ag.join_build(dR, ws[:tb], lf, sigR=sigR, stream=stream)
+            ag.sig_compute(dS, sigS, stream=stream, n_components=ncomp)
+            ag.join_probe_mode(t, dS, sigS, pairs, count, mode=mode, sync=False, stream=stream)
+        run()
+        torch.cuda.synchronize()
+        cnt = int(count.item())
+        if cnt < total_pairs or (mode == "inner" and cnt != total_pairs):
+            raise SystemExit(f"variant n={ncomp} {mode}: {cnt} pairs, exact join {total_pairs}")
+        for _ in range(2):
+            run()
+        v0, v1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        vreps = max(3, min(10, args.steps))
+        v0.record(stream)
+        for _ in range(vreps):
+            run()
+        v1.record(stream)
+        torch.cuda.synchronize()
+        vms = v0.elapsed_time(v1) / vreps
+        return {"ms_per_join": vms, "tuples_per_s": n / (vms * 1e-3), "pairs": cnt,
+                "collision_pairs": cnt - total_pairs,
+                "speedup_vs_fullstring": {k: (n / (vms * 1e-3)) / v["tuples_per_s"] for k, v in baseline.items()}}
+
+    paper_variants = {
+        "note": "Figure 2's probe outputs on a signature match; these runs time it on the same inputs "
+                "(signatures of R, build, signatures of S, probe) and count the pairs it adds to the "
+                "exact join (signature collisions)",
+        "sig_only_n4": variant(4, "sig_only"),
+        "sig_only_n2": variant(2, "sig_only"),
+        "exact_n2": variant(2, "inner"),
+    }
+
     hbm, peak_kind = peaks()
 
     # end to end from pinned host buffers through the package's host-relation join
@@ -530,6 +568,7 @@ def run_gpu(args):
         "kernels": kernels,
         "fullstring_gpu_join": baseline,
         "speedup_vs_fullstring": {k: value / v["tuples_per_s"] for k, v in baseline.items()},
+        "paper_variants": paper_variants,
         "pairs": total_pairs,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

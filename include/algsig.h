@@ -90,6 +90,20 @@ as_status as_sig_compute(const uint8_t* d_arena, const uint64_t* d_off, uint64_t
                          uint64_t* d_sig_out, as_stream stream);
 
 /*
+ * as_sig_compute_n -- as_sig_compute with n_components = n of Section 3.1:
+ * 4 (the same result as as_sig_compute) or 2 (the paper's two-symbol
+ * signature sig_{alpha,2} of Sections 3.1 and 4.3, 4 bytes: components 1 and 2
+ * in bits 0..31, bits 32..63 zero).  A join on two-component signatures is
+ * as_join_build with d_sigR and as_join_probe_mode with d_sigS, both from
+ * this call with n_components = 2; the table and probe compare the 64-bit
+ * words, so only the two components take part.
+ * Errors: as for as_sig_compute, and AS_ERR_INVALID for n_components other
+ * than 2 or 4.
+ */
+as_status as_sig_compute_n(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, int n_components,
+                           uint64_t* d_sig_out, as_stream stream);
+
+/*
  * Hash table of R's signatures (H_sign of Figure 2).  Open addressing with
  * linear probing over cap = next power of two >= max(64, m / load_factor)
  * slots of 16 bytes: the R row's 64-bit signature, then one uint64 holding
@@ -192,19 +206,28 @@ as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const u
  *   AS_JOIN_ANTI    : one (AS_NO_ROW, s_id) per S row with no match
  *   AS_JOIN_OUTER_S : the inner pairs plus one (AS_NO_ROW, s_id) per S row
  *                     with no match (outer join preserving S)
+ *   AS_JOIN_SIG_ONLY: the probe of Figure 2 as the paper runs it: one
+ *                     (r_id, s_id) pair per slot whose signature and key
+ *                     length equal the S key's, with no byte comparison.
+ *                     NOT exact: two different keys of equal length and equal
+ *                     signatures are paired (keys that differ in at most n
+ *                     symbols, n the signature's components, never are:
+ *                     Section 3.1); its count minus the INNER count is the
+ *                     number of signature collisions among the candidates.
  */
 enum {
     AS_JOIN_INNER = 0,
     AS_JOIN_SEMI = 1,
     AS_JOIN_ANTI = 2,
-    AS_JOIN_OUTER_S = 3
+    AS_JOIN_OUTER_S = 3,
+    AS_JOIN_SIG_ONLY = 4
 };
 #define AS_NO_ROW 0xFFFFFFFFu
 
 /*
  * as_join_probe_mode -- as_join_probe_sigs (S's signatures given, from
  * as_sig_compute) with an output mode.  Matches are exact (byte-verified) in
- * every mode.  d_pairs receives the mode's output records as (r_id, s_id)
+ * every mode but AS_JOIN_SIG_ONLY.  d_pairs receives the mode's output records as (r_id, s_id)
  * pairs in unspecified order; d_count / h_count count them.  Errors as for
  * as_join_probe, and AS_ERR_INVALID for an unknown mode.
  */

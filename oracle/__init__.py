@@ -9,6 +9,9 @@ It wraps oracle.c, a plain C statement of:
     (Section 3.1 of the paper);
   * the 4-component algebraic signature sig^k(P) = sum_i p_i x^(k i), once by
     the table definition and once by Horner's rule (Section 3.1);
+  * the n-component signature (the first n of the four components) and the
+    signature-only join of Figure 2 (pairs of equal signature and length, no
+    byte comparison; not exact, kept to count collisions), in Python;
   * the exact equi-join T = {(r.id, s.id) : key(r) == key(s)} by a nested loop,
     a simple hash join on full strings and a Grace (partitioned) hash join
     (Section 2; Figure 2 without the signature shortcut, since the result must
@@ -122,6 +125,14 @@ def components(s: int):
     return tuple((s >> (16 * k)) & 0xFFFF for k in range(4))
 
 
+def component_mask(n_components: int) -> int:
+    """Bits of the packed signature that hold components 1..n (Section 3.1: the
+    n-symbol signature is the vector of the first n components)."""
+    if n_components not in (1, 2, 3, 4):
+        raise ValueError(n_components)
+    return (1 << (16 * n_components)) - 1
+
+
 def sig_batch(arena: np.ndarray, off: np.ndarray, method: str = "tables", nthreads: int = 1) -> np.ndarray:
     lib = _load()
     n = off.shape[0] - 1
@@ -201,3 +212,23 @@ def join_mode(R, S, mode: str) -> np.ndarray:
     else:
         raise ValueError(mode)
     return sort_pairs(out)
+
+
+def join_sig_only(R, S, n_components: int = 4) -> np.ndarray:
+    """The probe of Figure 2 as the paper states it (output on a signature
+    match, Section 3.2): every (r.id, s.id) whose n-component signatures and
+    key lengths are equal, with no byte comparison.  Plain definition: group R
+    by (signature, length) and look every S key up.  Sorted like sort_pairs."""
+    mask = np.uint64(component_mask(n_components))
+    sR = sig_batch(R.arena, R.off) & mask
+    sS = sig_batch(S.arena, S.off) & mask
+    lR = np.diff(np.asarray(R.off, dtype=np.uint64))
+    lS = np.diff(np.asarray(S.off, dtype=np.uint64))
+    groups = {}
+    for i in range(len(sR)):
+        groups.setdefault((int(sR[i]), int(lR[i])), []).append(int(R.ids[i]))
+    out = []
+    for j in range(len(sS)):
+        for rid in groups.get((int(sS[j]), int(lS[j])), ()):
+            out.append((rid, int(S.ids[j])))
+    return sort_pairs(np.array(out, dtype=np.uint32).reshape(-1, 2))

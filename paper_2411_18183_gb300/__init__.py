@@ -30,7 +30,7 @@ AS_ERR_TABLE_FULL = 4
 AS_ERR_CUDA = 5
 AS_ERR_UNSUPPORTED = 6
 
-EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_join_table_bytes",
+EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_sig_compute_n", "as_join_table_bytes",
            "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_probe_sigs", "as_join_probe_mode", "as_join_ws_bytes", "as_join",
            "as_baseline_ws_bytes", "as_baseline_join")
 
@@ -70,6 +70,8 @@ def load(path: str | None = None):
         lib.as_version.restype = S
         lib.as_sig_compute.argtypes = [P, P, U64, P, P]
         lib.as_sig_compute.restype = S
+        lib.as_sig_compute_n.argtypes = [P, P, U64, S, P, P]
+        lib.as_sig_compute_n.restype = S
         lib.as_join_table_bytes.argtypes = [U64, F]
         lib.as_join_table_bytes.restype = SZ
         lib.as_join_ws_bytes.argtypes = [U64, U64, F]
@@ -149,13 +151,18 @@ def version() -> int:
     return int(load().as_version())
 
 
-def sig_compute(rel: DeviceRelation, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
-    """as_sig_compute: uint64 signature of every key (returned as int64 bits)."""
+def sig_compute(rel: DeviceRelation, out: torch.Tensor | None = None, stream=None,
+                n_components: int = 4) -> torch.Tensor:
+    """as_sig_compute (n_components = 4) or as_sig_compute_n (2: the paper's two-symbol
+    signature, components 3 and 4 zero): uint64 signature of every key (as int64 bits)."""
     lib = load()
     n = rel.n
     if out is None:
         out = torch.empty(max(n, 0), dtype=torch.int64, device=rel.arena.device)
-    _check(lib.as_sig_compute(_ptr(rel.arena), _ptr(rel.off), n, _ptr(out), _stream(stream)))
+    if n_components == 4:
+        _check(lib.as_sig_compute(_ptr(rel.arena), _ptr(rel.off), n, _ptr(out), _stream(stream)))
+    else:
+        _check(lib.as_sig_compute_n(_ptr(rel.arena), _ptr(rel.off), n, n_components, _ptr(out), _stream(stream)))
     return out
 
 
@@ -211,14 +218,15 @@ def join_probe_sigs(t: Table, S: DeviceRelation, sigS: torch.Tensor, pairs: torc
     return int(h.value) if sync else None
 
 
-JOIN_MODES = {"inner": 0, "semi": 1, "anti": 2, "outer_s": 3}    # AS_JOIN_*
+JOIN_MODES = {"inner": 0, "semi": 1, "anti": 2, "outer_s": 3, "sig_only": 4}    # AS_JOIN_*
 NO_ROW = 0xFFFFFFFF                                                  # AS_NO_ROW
 
 
 def join_probe_mode(t: Table, S: DeviceRelation, sigS: torch.Tensor, pairs: torch.Tensor, count: torch.Tensor,
                     mode: str = "inner", sync: bool = True, stream=None) -> int | None:
     """as_join_probe_mode: inner pairs, or per-S-row (NO_ROW, s_id) records (semi, anti), or
-    inner pairs plus the unmatched S rows (outer_s)."""
+    inner pairs plus the unmatched S rows (outer_s), or the signature-only pairs of the
+    paper's probe without byte verification (sig_only; not exact)."""
     lib = load()
     cap = pairs.numel() // 2
     h = ctypes.c_uint64(0)

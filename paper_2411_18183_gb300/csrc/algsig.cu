@@ -145,7 +145,7 @@ __global__ void batch_bytes_kernel(BatchJoin* J, int nj, const uint64_t* __restr
 
 // Signatures of actual keys [k_lo, k_hi) of one relation; key k's signature
 // goes to sig_out[k + out_shift] (out_shift = virtual minus actual row).
-template <class Cursor>
+template <int NCOMP, class Cursor>
 __device__ __forceinline__ void sig_walk(const uint8_t* __restrict__ arena, const uint64_t* __restrict__ off,
                                          uint64_t k_lo, uint64_t k_hi, uint64_t out_shift,
                                          uint64_t* __restrict__ sig_out, uint8_t* bufs, const uint16_t* ctab,
@@ -165,7 +165,7 @@ __device__ __forceinline__ void sig_walk(const uint8_t* __restrict__ arena, cons
     __syncwarp();
     uint8_t* buf = bufs + (r & 1) * kBufBytes;
     uint32_t a1, a2, a3, a4;
-    tile_accumulate(buf, cur.span_lo, cur, rc, a1, a2, a3, a4);
+    tile_accumulate<NCOMP>(buf, cur.span_lo, cur, rc, a1, a2, a3, a4);
     if (pd.valid) pending_alogs(pd);                // its logs were loaded one round ago
     __syncwarp();                                   // buf is free: refill it with round r+2
     const Plan nn = plan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
@@ -239,7 +239,9 @@ __global__ void dyn_smem_base_kernel() {
 // Signatures of all keys of a relation (J == nullptr), or of the rows of a
 // batch's joins (S_SIDE picks the relation), byte-balanced over the warps.
 // AT400: the reduction tables sit at shared address 0x400 (RedCursorAt400).
-template <bool S_SIDE, bool AT400>
+// NCOMP: components computed (4, or 2 for the two-symbol signature; the
+// others are 0); batches always use 4.
+template <bool S_SIDE, bool AT400, int NCOMP = 4>
 __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restrict__ arena,
                                                           const uint64_t* __restrict__ off, uint64_t n,
                                                           uint64_t* __restrict__ sig_out,
@@ -260,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restr
   if (!J) {
     uint64_t k_lo, k_hi;
     warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
-    sig_walk(arena, off, k_lo, k_hi, 0, sig_out, bufs, ctab, rc);
+    sig_walk<NCOMP>(arena, off, k_lo, k_hi, 0, sig_out, bufs, ctab, rc);
     return;
   }
   // batch: this warp's share of the virtual bytes, as virtual rows [v_lo, v_hi)
@@ -282,7 +284,7 @@ __global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restr
     const uint64_t e = S_SIDE ? __ldg(&J[j].s_end) : __ldg(&J[j].r_end);
     const uint64_t v0 = S_SIDE ? __ldg(&J[j].vs) : __ldg(&J[j].vr);
     const uint64_t vend = v0 + (e - b) < v_hi ? v0 + (e - b) : v_hi;
-    sig_walk(arena, off, b + (v - v0), b + (vend - v0), v0 - b, sig_out, bufs, ctab, rc);
+    sig_walk<NCOMP>(arena, off, b + (v - v0), b + (vend - v0), v0 - b, sig_out, bufs, ctab, rc);
     v = vend;
   }
 }
@@ -368,7 +370,7 @@ struct VerifyParams {
   uint32_t* pairs;
   uint64_t cap;
   unsigned long long* count;
-  int mode;                    // AS_JOIN_INNER / SEMI / ANTI / OUTER_S (single joins)
+  int mode;                    // AS_JOIN_INNER / SEMI / ANTI / OUTER_S / SIG_ONLY (single joins)
   // batch mode (J != nullptr): per-join tables, output regions and counters
   const BatchJoin* J;
   int nj;
@@ -597,12 +599,13 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         const uint32_t lj = __shfl_sync(kFull, l32, j);   // the slot holds the same length
         const uint64_t stj = __shfl_sync(kFull, start, j);
         const uint64_t rs = __ldg(P.offR + rj);
+        const bool verify = batch || P.mode != AS_JOIN_SIG_ONLY;   // signature-only: no byte comparison
         bool eq;
         if (lj < kNarrowLen) {
-          eq = warp_equal(P.arenaR + rs, P.arenaS + stj, lj, emask);
+          eq = !verify || warp_equal(P.arenaR + rs, P.arenaS + stj, lj, emask);
         } else {                                      // lengths that the slot's 32-bit field saturates
           const uint64_t ls = __shfl_sync(kFull, len, j);
-          eq = __ldg(P.offR + rj + 1) - rs == ls && warp_equal_wide(P.arenaR, rs, P.arenaS, stj, ls);
+          eq = __ldg(P.offR + rj + 1) - rs == ls && (!verify || warp_equal_wide(P.arenaR, rs, P.arenaS, stj, ls));
         }
         if (eq) {
           const uint64_t srow = __shfl_sync(kFull, i, j);
@@ -626,7 +629,7 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         }
       }
     }
-    if (!batch && P.mode != AS_JOIN_INNER) {         // one (AS_NO_ROW, s_id) per selected S row
+    if (!batch && P.mode != AS_JOIN_INNER && P.mode != AS_JOIN_SIG_ONLY) {   // one (AS_NO_ROW, s_id) per selected S row
       const bool emit = row_live && (P.mode == AS_JOIN_SEMI ? matched : !matched);
       const uint32_t em = __ballot_sync(kFull, emit);
       if (em) {
@@ -835,13 +838,13 @@ struct DeviceState {
 };
 
 // launch the signature kernel instantiation that matches the device
-template <bool S_SIDE>
+template <bool S_SIDE, int NCOMP = 4>
 static void launch_sig_kernel(const DeviceState* d, unsigned blocks, cudaStream_t s, const uint8_t* arena,
                               const uint64_t* off, uint64_t n, uint64_t* out, const BatchJoin* J, int nj) {
   if (d->tables_at400)
-    sig_kernel<S_SIDE, true><<<blocks, kThreads, kSmemSig, s>>>(arena, off, n, out, J, nj);
+    sig_kernel<S_SIDE, true, NCOMP><<<blocks, kThreads, kSmemSig, s>>>(arena, off, n, out, J, nj);
   else
-    sig_kernel<S_SIDE, false><<<blocks, kThreads, kSmemSig, s>>>(arena, off, n, out, J, nj);
+    sig_kernel<S_SIDE, false, NCOMP><<<blocks, kThreads, kSmemSig, s>>>(arena, off, n, out, J, nj);
 }
 
 static std::mutex g_dev_mu;
@@ -892,10 +895,12 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return cuda_fail(e, "device query");
     {
-      const void* fns[4] = {reinterpret_cast<const void*>(sig_kernel<false, false>),
+      const void* fns[6] = {reinterpret_cast<const void*>(sig_kernel<false, false>),
                             reinterpret_cast<const void*>(sig_kernel<false, true>),
                             reinterpret_cast<const void*>(sig_kernel<true, false>),
-                            reinterpret_cast<const void*>(sig_kernel<true, true>)};
+                            reinterpret_cast<const void*>(sig_kernel<true, true>),
+                            reinterpret_cast<const void*>(sig_kernel<false, false, 2>),
+                            reinterpret_cast<const void*>(sig_kernel<false, true, 2>)};
       for (const void* f : fns)
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) != cudaSuccess)
           return cuda_fail(e, "kernel attribute");
@@ -951,12 +956,16 @@ static bool table_geometry(uint64_t m, float lf, uint64_t* cap, uint32_t* log2ca
   return true;
 }
 
-static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t n, uint64_t* out, cudaStream_t s) {
+static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t n, uint64_t* out, cudaStream_t s,
+                            int ncomp = 4) {
   DeviceState* d = nullptr;
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
   if (n == 0) return AS_OK;
-  launch_sig_kernel<false>(d, walk_blocks(n, d->sms), s, arena, off, n, out, nullptr, 0);
+  if (ncomp == 2)
+    launch_sig_kernel<false, 2>(d, walk_blocks(n, d->sms), s, arena, off, n, out, nullptr, 0);
+  else
+    launch_sig_kernel<false>(d, walk_blocks(n, d->sms), s, arena, off, n, out, nullptr, 0);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "signature kernel launch");
   return AS_OK;
@@ -990,6 +999,15 @@ as_status as_sig_compute(const uint8_t* d_arena, const uint64_t* d_off, uint64_t
   if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute: null pointer");
   if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute: arena not 16-byte aligned");
   return launch_sig(d_arena, d_off, n, d_sig_out, (cudaStream_t)stream);
+}
+
+as_status as_sig_compute_n(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, int n_components,
+                           uint64_t* d_sig_out, as_stream stream) {
+  if (n_components != 2 && n_components != 4)
+    return fail(AS_ERR_INVALID, "as_sig_compute_n: n_components must be 2 or 4 (got %d)", n_components);
+  if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute_n: null pointer");
+  if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute_n: arena not 16-byte aligned");
+  return launch_sig(d_arena, d_off, n, d_sig_out, (cudaStream_t)stream, n_components);
 }
 
 size_t as_join_table_bytes(uint64_t m, float load_factor) {
@@ -1173,7 +1191,7 @@ as_status as_join_probe_mode(const as_table* t, const uint8_t* d_arenaS, const u
                              uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
   as_status st = probe_args("as_join_probe_mode", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
   if (st != AS_OK) return st;
-  if (mode < AS_JOIN_INNER || mode > AS_JOIN_OUTER_S) return fail(AS_ERR_INVALID, "as_join_probe_mode: mode %d", mode);
+  if (mode < AS_JOIN_INNER || mode > AS_JOIN_SIG_ONLY) return fail(AS_ERR_INVALID, "as_join_probe_mode: mode %d", mode);
   if (n > 0 && !d_sigS) return fail(AS_ERR_INVALID, "as_join_probe_mode: null signatures");
   DeviceState* d = nullptr;
   st = ensure_device(&d);

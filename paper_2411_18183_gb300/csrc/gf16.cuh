@@ -128,8 +128,9 @@ __device__ __forceinline__ uint32_t red24(uint32_t u, const Cursor& c) {
 
 // One Horner step over a 16-byte chunk: acc_k <- acc_k * x^(8k) + sum_j q_j x^(kj),
 // where q_{2t} = low half of word t and q_{2t+1} = high half of word t.
-// Accumulators enter and leave reduced (< 2^16).
-template <class Cursor>
+// Accumulators enter and leave reduced (< 2^16).  NCOMP = 2 computes only
+// components 1 and 2 (the paper's two-symbol signature); a3, a4 stay as given.
+template <int NCOMP = 4, class Cursor>
 __device__ __forceinline__ void horner_chunk(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
                                              uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& a4,
                                              const Cursor& rc) {
@@ -144,6 +145,7 @@ __device__ __forceinline__ void horner_chunk(uint32_t v0, uint32_t v1, uint32_t 
   // k = 2: 8 symbols, growth 16 bits
   u = (a2 << 16) ^ l0 ^ (h0 << 2) ^ (l1 << 4) ^ (h1 << 6) ^ (l2 << 8) ^ (h2 << 10) ^ (l3 << 12) ^ (h3 << 14);
   a2 = red32(u, rc);
+  if constexpr (NCOMP == 2) return;
   // k = 3: two halves of 4 symbols, growth 12 bits each (upper half first)
   u = (a3 << 12) ^ l2 ^ (h2 << 3) ^ (l3 << 6) ^ (h3 << 9);
   a3 = red32(u, rc);

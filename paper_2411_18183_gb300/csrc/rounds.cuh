@@ -280,7 +280,7 @@ __device__ __forceinline__ void keep_below(uint32_t e, uint64_t& lo64, uint64_t&
 
 // Unreduced-free tile signature: a_k = sum over the tile's slots t of q_t x^(k t)
 // (slot 0 = first byte pair of the tile's first realigned chunk), reduced to 16 bits.
-template <class Cursor>
+template <int NCOMP = 4, class Cursor>
 __device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t span_lo, const Plan& p,
                                                 const Cursor& redl, uint32_t& a1, uint32_t& a2,
                                                 uint32_t& a3, uint32_t& a4) {
@@ -304,12 +304,12 @@ __device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t spa
     const uint32_t v1 = __funnelshift_r(w.y, w.z, sh) & (uint32_t)(ml >> 32);
     const uint32_t v2 = __funnelshift_r(w.z, w.w, sh) & (uint32_t)mh;
     const uint32_t v3 = __funnelshift_r(w.w, nxt0, sh) & (uint32_t)(mh >> 32);
-    horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, redl);
+    horner_chunk<NCOMP>(v0, v1, v2, v3, a1, a2, a3, a4, redl);
     nxt0 = w.x;
   }
   for (--c; c >= 1; --c) {
     const uint4 w = chunk_at(buf, rel0 + 16u * (uint32_t)c);
-    horner_chunk(__funnelshift_r(w.x, w.y, sh), __funnelshift_r(w.y, w.z, sh), __funnelshift_r(w.z, w.w, sh),
+    horner_chunk<NCOMP>(__funnelshift_r(w.x, w.y, sh), __funnelshift_r(w.y, w.z, sh), __funnelshift_r(w.z, w.w, sh),
                  __funnelshift_r(w.w, nxt0, sh), a1, a2, a3, a4, redl);
     nxt0 = w.x;
   }
@@ -319,7 +319,7 @@ __device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t spa
     const uint32_t v1 = __funnelshift_r(w.y, w.z, sh) & (uint32_t)(hl >> 32);
     const uint32_t v2 = __funnelshift_r(w.z, w.w, sh) & (uint32_t)hh;
     const uint32_t v3 = __funnelshift_r(w.w, nxt0, sh) & (uint32_t)(hh >> 32);
-    horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, redl);
+    horner_chunk<NCOMP>(v0, v1, v2, v3, a1, a2, a3, a4, redl);
   }
 }
 

@@ -218,3 +218,34 @@ def test_signature_collisions_rejected_at_every_alignment(cuda, seed):
     R = relation_garbage_tail(interleave_gaps(rkeys, seed=rng.randrange(1 << 30)), seed=seed)
     S = relation_garbage_tail(interleave_gaps(skeys, seed=rng.randrange(1 << 30)), seed=seed + 1)
     check(cuda, R, S)
+
+
+@pytest.mark.parametrize("n_components", [4, 2])
+def test_signature_only_probe_matches_oracle(cuda, n_components):
+    """AS_JOIN_SIG_ONLY (the probe of Figure 2 without byte verification) with
+    n-component signatures on both sides against the oracle's definition: the
+    exact pairs plus the constructed collisions (five symbols for n = 4, three
+    for n = 2), and the exact join still rejects them."""
+    from cases import symbol_collision
+    ag = cuda
+    a4, b4 = five_symbol_collision()
+    a2, b2 = symbol_collision(2, 12, (0, 5, 11), seed=3)
+    wl = workloads.generate(workloads.CONFIGS["large"].scaled(2000, 10_000))
+    keys_r = [wl.R.key(i) for i in range(wl.R.n)] + [a4, a2]
+    keys_s = [wl.S.key(i) for i in range(wl.S.n)] + [b4, b2, a4]
+    Rh = relation_garbage_tail(keys_r, seed=1)
+    Sh = relation_garbage_tail(keys_s, seed=2)
+    R, S = dev(ag, Rh), dev(ag, Sh)
+    sigR = ag.sig_compute(R, n_components=n_components)
+    sigS = ag.sig_compute(S, n_components=n_components)
+    ws = ag.alloc_ws(ag.join_table_bytes(R.n, 0.5))
+    t = ag.join_build(R, ws, 0.5, sigR=sigR)
+    for mode, want in (("sig_only", oracle.join_sig_only(Rh, Sh, n_components)),
+                       ("inner", oracle.join_simple(Rh, Sh))):
+        pairs = torch.zeros(2 * (len(want) + 64), dtype=torch.int32, device="cuda")
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+        cnt = ag.join_probe_mode(t, S, sigS, pairs, count, mode=mode)
+        got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
+        assert np.array_equal(got, want), (mode, n_components)
+    extra = len(oracle.join_sig_only(Rh, Sh, n_components)) - len(oracle.join_simple(Rh, Sh))
+    assert extra == (1 if n_components == 4 else 2)

@@ -73,3 +73,23 @@ def test_collision_config_scaled(cuda):
 def test_large_config_scaled(cuda):
     wl = workloads.generate(workloads.CONFIGS["large"].scaled(10_000, 100_000))
     check(cuda, wl.S)
+
+
+def test_two_component_signatures(cuda):
+    """as_sig_compute_n with n = 2 (the paper's two-symbol signature): the first
+    two components of the oracle's signature, bits 32..63 zero, at every
+    alignment, over tile boundaries and on a scaled large-workload relation."""
+    ag = cuda
+    rng = random.Random(44)
+    keys = edge_keys() + [bytes(rng.randrange(256) for _ in range(n)) for n in
+                          list(range(0, 70)) + [255, 256, 257, 511, 512, 513, 4095, 4097, 9000]]
+    rels = [relation_garbage_tail(interleave_gaps(keys, seed=s), seed=s) for s in range(3)]
+    rels.append(workloads.generate(workloads.CONFIGS["large"].scaled(1000, 5000)).S)
+    mask = np.uint64(oracle.component_mask(2))
+    for rel in rels:
+        D = ag.DeviceRelation.from_host(rel.arena, rel.off, rel.ids)
+        got = ag.sig_compute(D, n_components=2).cpu().numpy().view(np.uint64)
+        want = oracle.sig_batch(rel.arena, rel.off, nthreads=8) & mask
+        assert np.array_equal(got, want)
+    with pytest.raises(ag.AlgsigError):
+        ag.sig_compute(ag.DeviceRelation.from_host(rels[0].arena, rels[0].off, rels[0].ids), n_components=3)

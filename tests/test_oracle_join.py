@@ -8,6 +8,7 @@ import pytest
 import oracle
 import workloads
 from cases import edge_keys, five_symbol_collision
+from workloads import relation_from_keys
 
 
 def brute(rkeys, skeys, rids=None, sids=None):
@@ -122,3 +123,33 @@ def test_join_modes_by_definition_and_brute_force():
     for mode, w in want.items():
         got = [tuple(int(x) for x in row) for row in oracle.join_mode(R, S, mode)]
         assert got == w, mode
+
+
+def test_signature_only_join_by_definition():
+    """The signature-only join of Figure 2 (no byte comparison) equals the
+    exact join when no two different keys share a signature and length, and
+    adds exactly the colliding pairs otherwise: the five-symbol collision for
+    four components, a three-symbol collision for the paper's two components
+    (which four components separate).  Checked against a nested loop over
+    (signature, length)."""
+    from cases import symbol_collision
+    rng = random.Random(31)
+    keys = [bytes(rng.randrange(256) for _ in range(rng.randrange(0, 40))) for _ in range(80)]
+    R = relation_from_keys(keys + keys[:10])
+    S = relation_from_keys(keys[5:] + [b"", b"\0"])
+    assert np.array_equal(oracle.join_sig_only(R, S), oracle.join_simple(R, S))
+    assert np.array_equal(oracle.join_sig_only(R, S, 2), oracle.join_simple(R, S))
+    a4, b4 = five_symbol_collision()
+    a2, b2 = symbol_collision(2, 12, (0, 5, 11), seed=3)
+    R = relation_from_keys([a4, a2])
+    S = relation_from_keys([b4, b2, a4])
+    assert oracle.join_simple(R, S).tolist() == [[0, 2]]
+    assert oracle.join_sig_only(R, S, 4).tolist() == [[0, 0], [0, 2]]
+    assert oracle.join_sig_only(R, S, 2).tolist() == [[0, 0], [0, 2], [1, 1]]
+    # brute force over (signature, length)
+    sR, sS = oracle.sig_batch(R.arena, R.off), oracle.sig_batch(S.arena, S.off)
+    lR, lS = np.diff(R.off), np.diff(S.off)
+    for n in (2, 4):
+        m = np.uint64(oracle.component_mask(n))
+        brute = [[i, j] for i in range(R.n) for j in range(S.n) if (sR[i] & m) == (sS[j] & m) and lR[i] == lS[j]]
+        assert oracle.join_sig_only(R, S, n).tolist() == brute

@@ -6,7 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
-from cases import edge_keys, five_symbol_collision
+from cases import edge_keys, five_symbol_collision, symbol_collision
 from gfpoly import gmul, gpow, sig_by_polynomial, symbols
 
 
@@ -129,3 +129,29 @@ def test_batch_matches_single():
     for method in ("tables", "horner"):
         out = oracle.sig_batch(rel.arena, rel.off, method=method, nthreads=3)
         assert out.tolist() == [oracle.sig(k) for k in keys]
+
+
+def test_two_component_signature_guarantee_and_tightness():
+    """The paper's two-symbol signature (n = 2, Section 3.1): keys that differ
+    in one or two symbols never share it (the 2x2 Vandermonde minors
+    x^(i+j) (x^j - x^i) are non-zero for distinct positions), while a
+    three-symbol difference can (constructed by solving the 2x3 system);
+    the same pair still differs in the four-component signature here."""
+    from gfpoly import gmul, gpow
+    mask2 = oracle.component_mask(2)
+    for i in range(40):
+        for j in range(i + 1, 40):
+            det = gmul(gpow(2, i), gpow(2, 2 * j)) ^ gmul(gpow(2, j), gpow(2, 2 * i))
+            assert det != 0
+    rng = random.Random(12)
+    for _ in range(200):
+        key = bytes(rng.randrange(256) for _ in range(2 * rng.randrange(2, 30)))
+        ps = list(key)
+        for pos in rng.sample(range(len(key) // 2), min(2, len(key) // 2)):
+            ps[2 * pos] ^= rng.randrange(1, 256)
+        other = bytes(ps)
+        assert oracle.sig(key) & mask2 != oracle.sig(other) & mask2
+    a, b = symbol_collision(2, 12, (0, 5, 11), seed=3)
+    assert oracle.sig(a) & mask2 == oracle.sig(b) & mask2
+    assert oracle.sig(a) != oracle.sig(b)
+    assert oracle.component_mask(4) == (1 << 64) - 1
