@@ -484,6 +484,42 @@ def run_gpu(args):
         "exact_n2": variant(2, "inner"),
     }
 
+    # cumulative (prefix) signatures of S at 256-byte blocks: the layout pass and the
+    # signatures pass, timed apart (keys / CUDA-event time)
+    def cumulative(block_bytes=256, reps=5):
+        lib = ag.load()
+        pref = torch.empty(n + 1, dtype=torch.int64, device="cuda")
+        pws = ag.alloc_ws(int(lib.as_sig_prefix_ws_bytes(n)))
+        offs = lambda: lib.as_sig_prefix_offsets(dS.off.data_ptr(), n, block_bytes, pref.data_ptr(), pws.data_ptr(),
+                                                 pws.numel(), stream.cuda_stream)
+        if offs() != 0:
+            raise SystemExit("prefix offsets failed")
+        torch.cuda.synchronize()
+        total = int(pref[n].item())
+        pout = torch.empty(max(1, total), dtype=torch.int64, device="cuda")
+        sigs = lambda: lib.as_sig_prefixes(dS.arena.data_ptr(), dS.off.data_ptr(), n, block_bytes, pref.data_ptr(),
+                                           pout.data_ptr(), stream.cuda_stream)
+        res = {"block_bytes": block_bytes, "entries": total}
+        for name, f in (("offsets", offs), ("prefixes", sigs)):
+            for _ in range(2):
+                f()
+            c0, c1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            for _ in range(reps):
+                f()
+            c1.record(stream)
+            torch.cuda.synchronize()
+            res[name + "_ms"] = c0.elapsed_time(c1) / reps
+        last = pout[(pref[1:] - 1)]                     # each key's last entry is its signature
+        res["last_equals_signature"] = bool(torch.equal(last, sigS_exact))
+        res["key_gbps"] = wl.S.nbytes / (res["prefixes_ms"] * 1e-3) / 1e9
+        return res
+
+    ag.sig_compute(dS, sigS, stream=stream)
+    sigS_exact = sigS.clone()
+    cumulative_sigs = cumulative()
+    del sigS_exact
+
     hbm, peak_kind = peaks()
 
     # end to end from pinned host buffers through the package's host-relation join
@@ -569,6 +605,7 @@ def run_gpu(args):
         "fullstring_gpu_join": baseline,
         "speedup_vs_fullstring": {k: value / v["tuples_per_s"] for k, v in baseline.items()},
         "paper_variants": paper_variants,
+        "cumulative_signatures": cumulative_sigs,
         "pairs": total_pairs,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

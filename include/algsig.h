@@ -104,6 +104,34 @@ as_status as_sig_compute_n(const uint8_t* d_arena, const uint64_t* d_off, uint64
                            uint64_t* d_sig_out, as_stream stream);
 
 /*
+ * Cumulative (prefix) signatures (Section 5 lists them, after the paper's
+ * reference [7], as the way to signatures of prefixes and substrings).  For a
+ * block size B (a positive multiple of 16 bytes) key i of length len gets
+ * max(1, ceil(len / B)) entries
+ *     C_j = sig(key[0 .. min((j+1) B, len))),   j = 0, 1, ...
+ * (a single 0 for the empty key); its last entry is sig(key).  By the
+ * concatenation rule of Section 3.1, the signature of any substring starting
+ * at an even byte a < b is x^(-k a/2) (C(b) + C(a)) component-wise, with C(a)
+ * the signature of the a-byte prefix (a block boundary when a is a multiple
+ * of B).
+ *
+ * as_sig_prefix_offsets -- layout of the entries: d_pref_off[i] (uint64[n+1],
+ *   device) receives the index of key i's first entry, d_pref_off[n] the total
+ *   count.  d_ws: device workspace of as_sig_prefix_ws_bytes(n) bytes.
+ *   Errors: AS_ERR_INVALID (block size, null pointers), AS_ERR_NOMEM, AS_ERR_CUDA.
+ * as_sig_prefixes -- the entries: d_out (uint64[d_pref_off[n]], device)
+ *   receives key i's entries at d_out[d_pref_off[i] ...], packed like
+ *   as_sig_compute.  d_pref_off as written by as_sig_prefix_offsets with the
+ *   same block size.  Errors: as for as_sig_compute, and AS_ERR_INVALID for a
+ *   block size that is not a positive multiple of 16.
+ */
+size_t as_sig_prefix_ws_bytes(uint64_t n);
+as_status as_sig_prefix_offsets(const uint64_t* d_off, uint64_t n, uint32_t block_bytes, uint64_t* d_pref_off,
+                                void* d_ws, size_t ws_bytes, as_stream stream);
+as_status as_sig_prefixes(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, uint32_t block_bytes,
+                          const uint64_t* d_pref_off, uint64_t* d_out, as_stream stream);
+
+/*
  * Hash table of R's signatures (H_sign of Figure 2).  Open addressing with
  * linear probing over cap = next power of two >= max(64, m / load_factor)
  * slots of 16 bytes: the R row's 64-bit signature, then one uint64 holding

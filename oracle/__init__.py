@@ -9,6 +9,8 @@ It wraps oracle.c, a plain C statement of:
     (Section 3.1 of the paper);
   * the 4-component algebraic signature sig^k(P) = sum_i p_i x^(k i), once by
     the table definition and once by Horner's rule (Section 3.1);
+  * cumulative signatures (the signatures of a key's block prefixes), by
+    definition from the signature routine, in Python;
   * the n-component signature (the first n of the four components) and the
     signature-only join of Figure 2 (pairs of equal signature and length, no
     byte comparison; not exact, kept to count collisions), in Python;
@@ -232,3 +234,14 @@ def join_sig_only(R, S, n_components: int = 4) -> np.ndarray:
         for rid in groups.get((int(sS[j]), int(lS[j])), ()):
             out.append((rid, int(S.ids[j])))
     return sort_pairs(np.array(out, dtype=np.uint32).reshape(-1, 2))
+
+
+def sig_prefixes(key: bytes, block_bytes: int) -> list:
+    """Cumulative signatures by their definition: sig of the prefixes of
+    block_bytes, 2 block_bytes, ... bytes (the last one the whole key; [0] for
+    the empty key)."""
+    key = bytes(key)
+    if not key:
+        return [0]
+    nb = (len(key) + block_bytes - 1) // block_bytes
+    return [sig(key[:min((j + 1) * block_bytes, len(key))]) for j in range(nb)]

@@ -30,7 +30,8 @@ AS_ERR_TABLE_FULL = 4
 AS_ERR_CUDA = 5
 AS_ERR_UNSUPPORTED = 6
 
-EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_sig_compute_n", "as_join_table_bytes",
+EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_sig_compute_n",
+           "as_sig_prefix_ws_bytes", "as_sig_prefix_offsets", "as_sig_prefixes", "as_join_table_bytes",
            "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_probe_sigs", "as_join_probe_mode", "as_join_ws_bytes", "as_join",
            "as_baseline_ws_bytes", "as_baseline_join")
 
@@ -72,6 +73,12 @@ def load(path: str | None = None):
         lib.as_sig_compute.restype = S
         lib.as_sig_compute_n.argtypes = [P, P, U64, S, P, P]
         lib.as_sig_compute_n.restype = S
+        lib.as_sig_prefix_ws_bytes.argtypes = [U64]
+        lib.as_sig_prefix_ws_bytes.restype = SZ
+        lib.as_sig_prefix_offsets.argtypes = [P, U64, ctypes.c_uint32, P, P, SZ, P]
+        lib.as_sig_prefix_offsets.restype = S
+        lib.as_sig_prefixes.argtypes = [P, P, U64, ctypes.c_uint32, P, P, P]
+        lib.as_sig_prefixes.restype = S
         lib.as_join_table_bytes.argtypes = [U64, F]
         lib.as_join_table_bytes.restype = SZ
         lib.as_join_ws_bytes.argtypes = [U64, U64, F]
@@ -164,6 +171,25 @@ def sig_compute(rel: DeviceRelation, out: torch.Tensor | None = None, stream=Non
     else:
         _check(lib.as_sig_compute_n(_ptr(rel.arena), _ptr(rel.off), n, n_components, _ptr(out), _stream(stream)))
     return out
+
+
+def sig_prefixes(rel: DeviceRelation, block_bytes: int, stream=None):
+    """as_sig_prefix_offsets + as_sig_prefixes: (pref_off int64[n+1], entries int64[total]);
+    key i's cumulative signatures are entries[pref_off[i]:pref_off[i+1]] (prefixes of
+    block_bytes, 2 * block_bytes, ... bytes, the last one the whole key).  Reads the
+    total count back (synchronises the stream)."""
+    lib = load()
+    n = rel.n
+    dev = rel.arena.device
+    pref = torch.empty(n + 1, dtype=torch.int64, device=dev)
+    ws = alloc_ws(int(lib.as_sig_prefix_ws_bytes(n)), dev)
+    _check(lib.as_sig_prefix_offsets(_ptr(rel.off), n, block_bytes, _ptr(pref), _ptr(ws), ws.numel(),
+                                     _stream(stream)))
+    total = int(pref[n].item())
+    out = torch.empty(max(total, 1), dtype=torch.int64, device=dev)
+    _check(lib.as_sig_prefixes(_ptr(rel.arena), _ptr(rel.off), n, block_bytes, _ptr(pref), _ptr(out),
+                               _stream(stream)))
+    return pref, out[:total]
 
 
 def join_table_bytes(m: int, load_factor: float = 0.5) -> int:

@@ -652,6 +652,12 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
   }
 }
 
+}  // namespace algsig
+
+#include "prefix.cuh"
+
+namespace algsig {
+
 // ----------------------------------------------------------------------------
 // Comparison join on full strings (baseline.cuh): hash, build, probe
 // ----------------------------------------------------------------------------
@@ -915,6 +921,9 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaMemcpyFromSymbol(&base, g_dyn_smem_base, sizeof(base))) != cudaSuccess)
       return cuda_fail(e, "shared memory probe");
     d.tables_at400 = base == kTablesAt400;
+    if ((e = cudaFuncSetAttribute(prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPrefix)) !=
+        cudaSuccess)
+      return cuda_fail(e, "kernel attribute");
     if ((e = cudaFuncSetAttribute(bl_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBHash)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
@@ -999,6 +1008,55 @@ as_status as_sig_compute(const uint8_t* d_arena, const uint64_t* d_off, uint64_t
   if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute: null pointer");
   if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute: arena not 16-byte aligned");
   return launch_sig(d_arena, d_off, n, d_sig_out, (cudaStream_t)stream);
+}
+
+size_t as_sig_prefix_ws_bytes(uint64_t n) {
+  return (size_t)round256(8 * ((n + kPKeysPerBlock - 1) / kPKeysPerBlock + 1));
+}
+
+as_status as_sig_prefix_offsets(const uint64_t* d_off, uint64_t n, uint32_t block_bytes, uint64_t* d_pref_off,
+                                void* d_ws, size_t ws_bytes, as_stream stream) {
+  if (block_bytes == 0 || block_bytes % 16 != 0)
+    return fail(AS_ERR_INVALID, "as_sig_prefix_offsets: block_bytes %u is not a positive multiple of 16", block_bytes);
+  if (!d_pref_off || (n > 0 && (!d_off || !d_ws))) return fail(AS_ERR_INVALID, "as_sig_prefix_offsets: null pointer");
+  if (n > 0 && ws_bytes < as_sig_prefix_ws_bytes(n))
+    return fail(AS_ERR_NOMEM, "as_sig_prefix_offsets: workspace of %zu bytes, %zu needed", ws_bytes,
+                as_sig_prefix_ws_bytes(n));
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  if (n == 0) {
+    if ((e = cudaMemsetAsync(d_pref_off, 0, sizeof(uint64_t), s)) != cudaSuccess) return cuda_fail(e, "prefix offsets");
+    return AS_OK;
+  }
+  const uint64_t nblocks = (n + kPKeysPerBlock - 1) / kPKeysPerBlock;
+  uint64_t* sums = reinterpret_cast<uint64_t*>(d_ws);
+  prefix_count_kernel<<<(unsigned)nblocks, kPThreads, 0, s>>>(d_off, n, block_bytes, d_pref_off, sums);
+  prefix_total_kernel<<<1, kPThreads, 0, s>>>(sums, nblocks, d_pref_off, n);
+  prefix_offset_kernel<<<(unsigned)nblocks, kPThreads, 0, s>>>(d_pref_off, n, sums);
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "prefix offsets launch");
+  return AS_OK;
+}
+
+as_status as_sig_prefixes(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, uint32_t block_bytes,
+                          const uint64_t* d_pref_off, uint64_t* d_out, as_stream stream) {
+  if (block_bytes == 0 || block_bytes % 16 != 0)
+    return fail(AS_ERR_INVALID, "as_sig_prefixes: block_bytes %u is not a positive multiple of 16", block_bytes);
+  if (n > 0 && (!d_arena || !d_off || !d_pref_off || !d_out)) return fail(AS_ERR_INVALID, "as_sig_prefixes: null pointer");
+  if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_prefixes: arena not 16-byte aligned");
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  if (n == 0) return AS_OK;
+  const uint64_t want = (n + kPThreads / 32 - 1) / (kPThreads / 32);
+  const unsigned blocks = (unsigned)(want < (uint64_t)d->sms * 8 ? want : (uint64_t)d->sms * 8);
+  prefix_kernel<<<blocks, kPThreads, kSmemPrefix, (cudaStream_t)stream>>>(d_arena, d_off, n, block_bytes, d_pref_off,
+                                                                          d_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "prefix kernel launch");
+  return AS_OK;
 }
 
 as_status as_sig_compute_n(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, int n_components,

@@ -1,0 +1,205 @@
+// prefix.cuh -- cumulative (prefix) signatures of every key.
+//
+// For a key P and a block size B (a multiple of 16 bytes) the cumulative
+// signatures are the signatures of its prefixes
+//     C_j = sig(P[0 .. min((j+1) B, len))),   j = 0 .. ceil(len / B) - 1
+// (one entry, 0, for the empty key).  The last entry is sig(P).  By the
+// concatenation rule of Section 3.1 (sig(A || B) = sig(A) + x^(k |A|/2) sig(B)
+// for an even byte length |A|), the signature of any substring that starts
+// on an even byte a follows from two of them:
+//     sig(P[a .. b)) = x^(-k a/2) (sig(P[0 .. b)) + sig(P[0 .. a))).
+//
+// Kernels.  prefix_count_kernel / prefix_total_kernel / prefix_offset_kernel
+// lay out the output: key i's entries start at pref_off[i], an exclusive scan
+// of max(1, ceil(len_i / B)).  prefix_kernel computes the entries: one warp per
+// key, 512 key bytes per step, lane l taking the key's 16-byte chunk c = 32 s + l
+// (realigned to the key's first byte from two aligned chunks, the word part of
+// the realignment warp-uniform).  The chunk's value T_c = sum_j q_j x^(k j) is a
+// Horner step from zero (gf16.cuh); its term of the prefix sums is
+// x^(8 k c) T_c, formed through the log / antilog tables; an inclusive XOR scan
+// over the lanes plus the running total of the earlier steps gives C at every
+// chunk end, and the lanes whose chunk ends a block (or the key) store it.
+#pragma once
+#include <cstdint>
+
+namespace algsig {
+
+constexpr int kPThreads = 256;          // threads per block of the prefix kernels
+constexpr int kPItems = 4;              // keys per thread in the count / offset kernels
+constexpr int kPKeysPerBlock = kPThreads * kPItems;
+
+__device__ __forceinline__ uint64_t prefix_entries(uint64_t len, uint32_t block_bytes) {
+  return len == 0 ? 1 : (len + block_bytes - 1) / block_bytes;
+}
+
+// block-wide exclusive scan of one value per thread; returns the block total in *total
+__device__ __forceinline__ uint64_t block_exclusive_scan(uint64_t v, uint64_t* total) {
+  __shared__ uint64_t warp_tot[kPThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint64_t inc = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, inc, d);
+    if (lane >= d) inc += t;
+  }
+  if (lane == 31) warp_tot[w] = inc;
+  __syncthreads();
+  uint64_t before = 0, all = 0;
+  for (int i = 0; i < kPThreads / 32; i++) {
+    if (i < w) before += warp_tot[i];
+    all += warp_tot[i];
+  }
+  __syncthreads();
+  *total = all;
+  return before + inc - v;
+}
+
+// pass 1: pref_off[i] = exclusive prefix of the entry counts inside the key's
+// block of kPKeysPerBlock keys; block_sums[b] = the block's total
+__global__ void __launch_bounds__(kPThreads) prefix_count_kernel(const uint64_t* __restrict__ off, uint64_t n,
+                                                                 uint32_t block_bytes, uint64_t* __restrict__ pref_off,
+                                                                 uint64_t* __restrict__ block_sums) {
+  const uint64_t k0 = (uint64_t)blockIdx.x * kPKeysPerBlock + (uint64_t)threadIdx.x * kPItems;
+  uint64_t cnt[kPItems], s = 0;
+#pragma unroll
+  for (int j = 0; j < kPItems; j++) {
+    const uint64_t k = k0 + j;
+    cnt[j] = k < n ? prefix_entries(off[k + 1] - off[k], block_bytes) : 0;
+    s += cnt[j];
+  }
+  uint64_t total;
+  uint64_t run = block_exclusive_scan(s, &total);
+#pragma unroll
+  for (int j = 0; j < kPItems; j++) {
+    const uint64_t k = k0 + j;
+    if (k < n) pref_off[k] = run;
+    run += cnt[j];
+  }
+  if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+// pass 2 (one block): exclusive scan of the block totals in place; pref_off[n] = the total
+__global__ void __launch_bounds__(kPThreads) prefix_total_kernel(uint64_t* __restrict__ block_sums, uint64_t nblocks,
+                                                                 uint64_t* __restrict__ pref_off, uint64_t n) {
+  uint64_t carry = 0;
+  for (uint64_t b0 = 0; b0 < nblocks; b0 += kPThreads) {
+    const uint64_t b = b0 + threadIdx.x;
+    const uint64_t v = b < nblocks ? block_sums[b] : 0;
+    uint64_t total;
+    const uint64_t ex = block_exclusive_scan(v, &total);
+    if (b < nblocks) block_sums[b] = carry + ex;
+    carry += total;
+  }
+  if (threadIdx.x == 0) pref_off[n] = carry;
+}
+
+// pass 3: add each block's start
+__global__ void __launch_bounds__(kPThreads) prefix_offset_kernel(uint64_t* __restrict__ pref_off, uint64_t n,
+                                                                  const uint64_t* __restrict__ block_sums) {
+  const uint64_t k0 = (uint64_t)blockIdx.x * kPKeysPerBlock + (uint64_t)threadIdx.x * kPItems;
+  const uint64_t add = block_sums[blockIdx.x];
+#pragma unroll
+  for (int j = 0; j < kPItems; j++)
+    if (k0 + j < n) pref_off[k0 + j] += add;
+}
+
+// x^(8 k c) T, component-wise, through the log / antilog tables
+__device__ __forceinline__ uint64_t shift_chunk_value(uint32_t t1, uint32_t t2, uint32_t t3, uint32_t t4, uint64_t c) {
+  const uint32_t e1 = (uint32_t)((8u * (c % kOrder)) % kOrder);
+  uint32_t e = e1;
+  uint64_t out = 0;
+  const uint32_t t[4] = {t1, t2, t3, t4};
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    if (t[k]) {
+      uint32_t l = (uint32_t)__ldg(&g_log[t[k]]) + e;
+      if (l >= kOrder) l -= kOrder;
+      out |= (uint64_t)__ldg(&g_alog[l]) << (16 * k);
+    }
+    e += e1;
+    if (e >= kOrder) e -= kOrder;
+  }
+  return out;
+}
+
+template <class Cursor>
+__device__ __forceinline__ void prefix_key(const uint8_t* __restrict__ arena, uint64_t s0, uint64_t len,
+                                           uint32_t chunks_per_block, uint64_t* __restrict__ o,
+                                           const uint4* __restrict__ emask, const Cursor& rc) {
+  const uint32_t lane = threadIdx.x & 31u;
+  if (len == 0) {
+    if (lane == 0) o[0] = 0;
+    return;
+  }
+  const uint8_t* p = arena + s0;
+  const uint32_t a = (uint32_t)reinterpret_cast<uintptr_t>(p) & 15u;
+  const uint8_t* base = p - a;                       // aligned; key bytes are [a, a + len) from here
+  const uint32_t sh = 8u * (a & 3u);
+  const uint64_t nchunks = (len + 15) / 16;
+  uint64_t carry = 0;
+  for (uint64_t c0 = 0; c0 < nchunks; c0 += 32) {
+    const uint64_t c = c0 + lane;
+    uint64_t W = 0;
+    if (c < nchunks) {
+      const uint64_t o16 = 16 * c;                   // aligned offset of the chunk's first aligned chunk
+      const uint4 ra = ld16(base + o16);
+      const uint4 rb = o16 + 16 < a + len ? ld16(base + o16 + 16) : make_uint4(0, 0, 0, 0);
+      uint32_t v0, v1, v2, v3;
+      switch (a >> 2) {                              // warp-uniform
+        case 0:
+          v0 = __funnelshift_r(ra.x, ra.y, sh); v1 = __funnelshift_r(ra.y, ra.z, sh);
+          v2 = __funnelshift_r(ra.z, ra.w, sh); v3 = __funnelshift_r(ra.w, rb.x, sh);
+          break;
+        case 1:
+          v0 = __funnelshift_r(ra.y, ra.z, sh); v1 = __funnelshift_r(ra.z, ra.w, sh);
+          v2 = __funnelshift_r(ra.w, rb.x, sh); v3 = __funnelshift_r(rb.x, rb.y, sh);
+          break;
+        case 2:
+          v0 = __funnelshift_r(ra.z, ra.w, sh); v1 = __funnelshift_r(ra.w, rb.x, sh);
+          v2 = __funnelshift_r(rb.x, rb.y, sh); v3 = __funnelshift_r(rb.y, rb.z, sh);
+          break;
+        default:
+          v0 = __funnelshift_r(ra.w, rb.x, sh); v1 = __funnelshift_r(rb.x, rb.y, sh);
+          v2 = __funnelshift_r(rb.y, rb.z, sh); v3 = __funnelshift_r(rb.z, rb.w, sh);
+          break;
+      }
+      const uint64_t rest = len - o16;               // key bytes from this chunk on
+      const uint4 m = emask[rest < 16 ? rest : 16];
+      v0 &= m.x; v1 &= m.y; v2 &= m.z; v3 &= m.w;
+      uint32_t t1 = 0, t2 = 0, t3 = 0, t4 = 0;
+      horner_chunk(v0, v1, v2, v3, t1, t2, t3, t4, rc);
+      W = shift_chunk_value(t1, t2, t3, t4, c);
+    }
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, W, d);
+      if (lane >= (uint32_t)d) W ^= t;
+    }
+    const uint64_t P = carry ^ W;
+    if (c < nchunks && ((c + 1) % chunks_per_block == 0 || c + 1 == nchunks)) o[c / chunks_per_block] = P;
+    carry = __shfl_sync(0xFFFFFFFFu, P, 31);
+  }
+}
+
+__global__ void __launch_bounds__(kPThreads) prefix_kernel(const uint8_t* __restrict__ arena,
+                                                           const uint64_t* __restrict__ off, uint64_t n,
+                                                           uint32_t block_bytes,
+                                                           const uint64_t* __restrict__ pref_off,
+                                                           uint64_t* __restrict__ out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint4 emask[17];
+  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  fill_emask(emask);
+  init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
+  const RedCursor rc = red_cursor(red);
+  const uint32_t cpb = block_bytes / 16u;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (kPThreads / 32);
+  for (uint64_t i = (uint64_t)blockIdx.x * (kPThreads / 32) + (threadIdx.x >> 5); i < n; i += nwarps) {
+    const uint64_t s0 = off[i];
+    prefix_key(arena, s0, off[i + 1] - s0, cpb, out + pref_off[i], emask, rc);
+  }
+}
+
+constexpr size_t kSmemPrefix = (size_t)kRedBytes + 512 * 4;
+
+}  // namespace algsig

@@ -93,3 +93,30 @@ def test_two_component_signatures(cuda):
         assert np.array_equal(got, want)
     with pytest.raises(ag.AlgsigError):
         ag.sig_compute(ag.DeviceRelation.from_host(rels[0].arena, rels[0].off, rels[0].ids), n_components=3)
+
+
+@pytest.mark.parametrize("block_bytes", [16, 48, 256, 4096])
+def test_cumulative_signatures(cuda, block_bytes):
+    """as_sig_prefix_offsets / as_sig_prefixes against the oracle's definition:
+    the layout (an exclusive scan of max(1, ceil(len / B))) and every prefix
+    signature, for keys of 0..100 bytes, around the 256- and 512-byte marks and
+    longer, at every alignment, and on a scaled large-workload relation."""
+    ag = cuda
+    rng = random.Random(block_bytes)
+    keys = [bytes(rng.randrange(256) for _ in range(n)) for n in
+            list(range(0, 101)) + [255, 256, 257, 511, 512, 513, 1023, 5000, 20000]]
+    rels = [relation_garbage_tail(interleave_gaps(keys, seed=s), seed=s) for s in range(2)]
+    rels.append(workloads.generate(workloads.CONFIGS["large"].scaled(500, 3000)).S)
+    for rel in rels:
+        D = ag.DeviceRelation.from_host(rel.arena, rel.off, rel.ids)
+        pref, out = ag.sig_prefixes(D, block_bytes)
+        pref = pref.cpu().numpy()
+        out = out.cpu().numpy().view(np.uint64)
+        lens = np.diff(rel.off.astype(np.int64))
+        cnt = np.maximum(1, (lens + block_bytes - 1) // block_bytes)
+        assert np.array_equal(pref, np.concatenate([[0], np.cumsum(cnt)]))
+        for i in range(rel.n):
+            want = oracle.sig_prefixes(rel.key(i), block_bytes)
+            assert out[pref[i]:pref[i + 1]].tolist() == want, (i, int(lens[i]))
+    with pytest.raises(ag.AlgsigError):
+        ag.sig_prefixes(ag.DeviceRelation.from_host(rels[0].arena, rels[0].off, rels[0].ids), 24)

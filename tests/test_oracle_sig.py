@@ -155,3 +155,29 @@ def test_two_component_signature_guarantee_and_tightness():
     assert oracle.sig(a) & mask2 == oracle.sig(b) & mask2
     assert oracle.sig(a) != oracle.sig(b)
     assert oracle.component_mask(4) == (1 << 64) - 1
+
+
+def test_cumulative_signatures_and_substring_rule():
+    """Cumulative signatures (the signatures of a key's block prefixes): the
+    last entry is the key's signature, and any substring starting on an even
+    byte a follows from two prefixes by the concatenation rule,
+    sig(P[a..b)) = x^(-k a/2) (sig(P[0..b)) + sig(P[0..a))), with the GF
+    arithmetic taken from the textbook routines of gfpoly."""
+    rng = random.Random(77)
+    assert oracle.sig_prefixes(b"", 16) == [0]
+    for _ in range(60):
+        key = rand_key(rng, rng.randrange(1, 300))
+        B = rng.choice([16, 32, 64, 256])
+        C = oracle.sig_prefixes(key, B)
+        assert len(C) == (len(key) + B - 1) // B
+        assert C[-1] == oracle.sig(key)
+        assert C[:-1] == [oracle.sig(key[:(j + 1) * B]) for j in range(len(C) - 1)]
+        a = 2 * rng.randrange(0, len(key) // 2 + 1)
+        b = rng.randrange(a, len(key) + 1)
+        full, pre = oracle.sig(key[:b]), oracle.sig(key[:a])
+        want = oracle.sig(key[a:b])
+        got = 0
+        for k in range(1, 5):
+            d = comp(full, k) ^ comp(pre, k)
+            got |= gmul(d, gpow(gpow(2, k * (a // 2)), 65534)) << (16 * (k - 1))
+        assert got == want
