@@ -448,6 +448,39 @@ __device__ __forceinline__ void fill_emask(uint4* emask) {
 // bR + off + 16, realigned by a funnel shift of d bytes (the word part of d is
 // warp-uniform).  Only aligned chunks that hold a key byte are read.  Only the
 // steps that hold the key's first or last byte apply byte masks.
+// realigned R words of one lane for the misalignment d (word part warp-uniform)
+__device__ __forceinline__ void realign_r(const uint4& ra, const uint4& rb, uint32_t d, uint32_t sh, uint32_t& r0,
+                                          uint32_t& r1, uint32_t& r2, uint32_t& r3) {
+  switch (d >> 2) {                                // warp-uniform
+    case 0:
+      r0 = __funnelshift_r(ra.x, ra.y, sh); r1 = __funnelshift_r(ra.y, ra.z, sh);
+      r2 = __funnelshift_r(ra.z, ra.w, sh); r3 = __funnelshift_r(ra.w, rb.x, sh);
+      break;
+    case 1:
+      r0 = __funnelshift_r(ra.y, ra.z, sh); r1 = __funnelshift_r(ra.z, ra.w, sh);
+      r2 = __funnelshift_r(ra.w, rb.x, sh); r3 = __funnelshift_r(rb.x, rb.y, sh);
+      break;
+    case 2:
+      r0 = __funnelshift_r(ra.z, ra.w, sh); r1 = __funnelshift_r(ra.w, rb.x, sh);
+      r2 = __funnelshift_r(rb.x, rb.y, sh); r3 = __funnelshift_r(rb.y, rb.z, sh);
+      break;
+    default:
+      r0 = __funnelshift_r(ra.w, rb.x, sh); r1 = __funnelshift_r(rb.x, rb.y, sh);
+      r2 = __funnelshift_r(rb.y, rb.z, sh); r3 = __funnelshift_r(rb.z, rb.w, sh);
+      break;
+  }
+}
+
+// Byte equality of the len-byte keys at pR and pS (len < kNarrowLen) by the
+// whole warp, 1024 bytes per round trip: lane l compares, for each of the two
+// 512-byte halves of a step, the S chunk [off, off + 16) with the R bytes
+// [off + d, off + d + 16) from the two aligned R chunks at bR + off and
+// bR + off + 16 (offsets from the aligned chunk bS that holds the S key's first
+// byte; bR is the aligned R chunk that holds the matching R byte, minus the
+// misalignment d).  Both halves' loads are issued before either is compared,
+// so a key of up to 1 KB costs one memory round trip.  Only aligned chunks
+// that hold a key byte are read; only the steps that hold the key's first or
+// last byte apply byte masks.
 __device__ __forceinline__ bool warp_equal(const uint8_t* __restrict__ pR, const uint8_t* __restrict__ pS,
                                            uint32_t len, const uint4* __restrict__ emask) {
   const uint32_t lane = threadIdx.x & 31u;
@@ -458,39 +491,32 @@ __device__ __forceinline__ bool warp_equal(const uint8_t* __restrict__ pR, const
   const uint32_t sh = 8u * (d & 3u);
   const uint32_t kend = sa + len;                  // S key bytes: [sa, kend) from bS
   const uint32_t rlo = sa + d, rend = kend + d;    // R key bytes: [rlo, rend) from bR
-  for (uint32_t base = 0; base < kend; base += 512u) {
-    const uint32_t off = base + 16u * lane;
-    uint4 sv = make_uint4(0, 0, 0, 0), ra = sv, rb = sv;
-    if (off < kend) sv = ld16(bS + off);
-    if (off + 16u > rlo && off < rend) ra = ld16(bR + off);
-    if (off + 16u < rend) rb = ld16(bR + off + 16u);
-    uint32_t r0, r1, r2, r3;
-    switch (d >> 2) {                              // warp-uniform
-      case 0:
-        r0 = __funnelshift_r(ra.x, ra.y, sh); r1 = __funnelshift_r(ra.y, ra.z, sh);
-        r2 = __funnelshift_r(ra.z, ra.w, sh); r3 = __funnelshift_r(ra.w, rb.x, sh);
-        break;
-      case 1:
-        r0 = __funnelshift_r(ra.y, ra.z, sh); r1 = __funnelshift_r(ra.z, ra.w, sh);
-        r2 = __funnelshift_r(ra.w, rb.x, sh); r3 = __funnelshift_r(rb.x, rb.y, sh);
-        break;
-      case 2:
-        r0 = __funnelshift_r(ra.z, ra.w, sh); r1 = __funnelshift_r(ra.w, rb.x, sh);
-        r2 = __funnelshift_r(rb.x, rb.y, sh); r3 = __funnelshift_r(rb.y, rb.z, sh);
-        break;
-      default:
-        r0 = __funnelshift_r(ra.w, rb.x, sh); r1 = __funnelshift_r(rb.x, rb.y, sh);
-        r2 = __funnelshift_r(rb.y, rb.z, sh); r3 = __funnelshift_r(rb.z, rb.w, sh);
-        break;
+  for (uint32_t base = 0; base < kend; base += 1024u) {
+    uint4 sv[2], ra[2], rb[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const uint32_t off = base + 512u * h + 16u * lane;
+      sv[h] = make_uint4(0, 0, 0, 0); ra[h] = sv[h]; rb[h] = sv[h];
+      if (off < kend) sv[h] = ld16(bS + off);
+      if (off + 16u > rlo && off < rend) ra[h] = ld16(bR + off);
+      if (off + 16u < rend) rb[h] = ld16(bR + off + 16u);
     }
-    uint32_t x0 = r0 ^ sv.x, x1 = r1 ^ sv.y, x2 = r2 ^ sv.z, x3 = r3 ^ sv.w;
-    if ((base == 0u && sa != 0u) || base + 512u > kend) {   // warp-uniform: the key's first or last byte
-      const uint32_t lo = off < sa ? sa - off : 0u;
-      const uint32_t hi = off < kend ? (kend - off < 16u ? kend - off : 16u) : 0u;
-      const uint4 mh = emask[hi], ml = emask[lo];
-      x0 &= mh.x & ~ml.x; x1 &= mh.y & ~ml.y; x2 &= mh.z & ~ml.z; x3 &= mh.w & ~ml.w;
+    uint32_t diff = 0;
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const uint32_t hb = base + 512u * h, off = hb + 16u * lane;
+      uint32_t r0, r1, r2, r3;
+      realign_r(ra[h], rb[h], d, sh, r0, r1, r2, r3);
+      uint32_t x0 = r0 ^ sv[h].x, x1 = r1 ^ sv[h].y, x2 = r2 ^ sv[h].z, x3 = r3 ^ sv[h].w;
+      if ((hb == 0u && sa != 0u) || hb + 512u > kend) {   // warp-uniform: the key's first or last byte
+        const uint32_t lo = off < sa ? sa - off : 0u;
+        const uint32_t hi = off < kend ? (kend - off < 16u ? kend - off : 16u) : 0u;
+        const uint4 mh = emask[hi], ml = emask[lo];
+        x0 &= mh.x & ~ml.x; x1 &= mh.y & ~ml.y; x2 &= mh.z & ~ml.z; x3 &= mh.w & ~ml.w;
+      }
+      diff |= x0 | x1 | x2 | x3;
     }
-    if (__any_sync(kFull, (x0 | x1 | x2 | x3) != 0u)) return false;
+    if (__any_sync(kFull, diff != 0u)) return false;
   }
   return true;
 }
