@@ -103,9 +103,8 @@ __global__ void __launch_bounds__(kPThreads) prefix_offset_kernel(uint64_t* __re
     if (k0 + j < n) pref_off[k0 + j] += add;
 }
 
-// x^(8 k c) T, component-wise, through the log / antilog tables
-__device__ __forceinline__ uint64_t shift_chunk_value(uint32_t t1, uint32_t t2, uint32_t t3, uint32_t t4, uint64_t c) {
-  const uint32_t e1 = (uint32_t)((8u * (c % kOrder)) % kOrder);
+// x^(8 k c) T, component-wise, through the log / antilog tables; e1 = 8 c mod 65535
+__device__ __forceinline__ uint64_t shift_chunk_value(uint32_t t1, uint32_t t2, uint32_t t3, uint32_t t4, uint32_t e1) {
   uint32_t e = e1;
   uint64_t out = 0;
   const uint32_t t[4] = {t1, t2, t3, t4};
@@ -122,9 +121,26 @@ __device__ __forceinline__ uint64_t shift_chunk_value(uint32_t t1, uint32_t t2, 
   return out;
 }
 
+// Where lane l's chunk c = 32 s + l stands among the blocks of chunks_per_block
+// chunks: block q and place r in it, kept per lane and advanced by 32 chunks per
+// step without a division (the lane's start and the per-step advance are
+// divided once per kernel).
+struct BlockPos {
+  uint32_t q, r;              // block index, chunk index inside the block
+  uint32_t dq, dr;            // 32 / chunks_per_block, 32 % chunks_per_block
+  uint32_t q0, r0;            // lane / chunks_per_block, lane % chunks_per_block
+  uint32_t cpb;
+  __device__ __forceinline__ void start() { q = q0; r = r0; }
+  __device__ __forceinline__ void advance() {
+    q += dq;
+    r += dr;
+    if (r >= cpb) { r -= cpb; q += 1; }
+  }
+};
+
 template <class Cursor>
 __device__ __forceinline__ void prefix_key(const uint8_t* __restrict__ arena, uint64_t s0, uint64_t len,
-                                           uint32_t chunks_per_block, uint64_t* __restrict__ o,
+                                           BlockPos& bp, uint64_t* __restrict__ o,
                                            const uint4* __restrict__ emask, const Cursor& rc) {
   const uint32_t lane = threadIdx.x & 31u;
   if (len == 0) {
@@ -137,6 +153,8 @@ __device__ __forceinline__ void prefix_key(const uint8_t* __restrict__ arena, ui
   const uint32_t sh = 8u * (a & 3u);
   const uint64_t nchunks = (len + 15) / 16;
   uint64_t carry = 0;
+  bp.start();
+  uint32_t e1 = 8u * lane;                           // 8 c mod 65535 for c = c0 + lane
   for (uint64_t c0 = 0; c0 < nchunks; c0 += 32) {
     const uint64_t c = c0 + lane;
     uint64_t W = 0;
@@ -168,7 +186,7 @@ __device__ __forceinline__ void prefix_key(const uint8_t* __restrict__ arena, ui
       v0 &= m.x; v1 &= m.y; v2 &= m.z; v3 &= m.w;
       uint32_t t1 = 0, t2 = 0, t3 = 0, t4 = 0;
       horner_chunk(v0, v1, v2, v3, t1, t2, t3, t4, rc);
-      W = shift_chunk_value(t1, t2, t3, t4, c);
+      W = shift_chunk_value(t1, t2, t3, t4, e1);
     }
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
@@ -176,8 +194,11 @@ __device__ __forceinline__ void prefix_key(const uint8_t* __restrict__ arena, ui
       if (lane >= (uint32_t)d) W ^= t;
     }
     const uint64_t P = carry ^ W;
-    if (c < nchunks && ((c + 1) % chunks_per_block == 0 || c + 1 == nchunks)) o[c / chunks_per_block] = P;
+    if (c < nchunks && (bp.r + 1 == bp.cpb || c + 1 == nchunks)) o[bp.q] = P;
     carry = __shfl_sync(0xFFFFFFFFu, P, 31);
+    bp.advance();
+    e1 += 256u;
+    if (e1 >= kOrder) e1 -= kOrder;
   }
 }
 
@@ -192,11 +213,16 @@ __global__ void __launch_bounds__(kPThreads) prefix_kernel(const uint8_t* __rest
   fill_emask(emask);
   init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
   const RedCursor rc = red_cursor(red);
-  const uint32_t cpb = block_bytes / 16u;
+  BlockPos bp;
+  bp.cpb = block_bytes / 16u;
+  bp.dq = 32u / bp.cpb;
+  bp.dr = 32u % bp.cpb;
+  bp.q0 = (threadIdx.x & 31u) / bp.cpb;
+  bp.r0 = (threadIdx.x & 31u) % bp.cpb;
   const uint64_t nwarps = (uint64_t)gridDim.x * (kPThreads / 32);
   for (uint64_t i = (uint64_t)blockIdx.x * (kPThreads / 32) + (threadIdx.x >> 5); i < n; i += nwarps) {
     const uint64_t s0 = off[i];
-    prefix_key(arena, s0, off[i + 1] - s0, cpb, out + pref_off[i], emask, rc);
+    prefix_key(arena, s0, off[i + 1] - s0, bp, out + pref_off[i], emask, rc);
   }
 }
 
