@@ -450,11 +450,17 @@ def run_gpu(args):
     # signatures only (no byte verification; its extra pairs are signature collisions),
     # with four components and with the paper's two (sig_{alpha,2}), and the exact
     # join on two-component signatures
-    def variant(ncomp, mode):
+    def variant(ncomp, mode, field=16):
+        def sig(rel, out):
+            if field == 8:
+                ag.sig_compute_gf8(rel, out, stream=stream)
+            else:
+                ag.sig_compute(rel, out, stream=stream, n_components=ncomp)
+
         def run():
-            ag.sig_compute(dR, sigR, stream=stream, n_components=ncomp)
+            sig(dR, sigR)
             t = ag.join_build(dR, ws[:tb], lf, sigR=sigR, stream=stream)
-            ag.sig_compute(dS, sigS, stream=stream, n_components=ncomp)
+            sig(dS, sigS)
             ag.join_probe_mode(t, dS, sigS, pairs, count, mode=mode, sync=False, stream=stream)
         run()
         torch.cuda.synchronize()
@@ -478,11 +484,24 @@ def run_gpu(args):
     paper_variants = {
         "note": "Figure 2's probe outputs on a signature match; these runs time it on the same inputs "
                 "(signatures of R, build, signatures of S, probe) and count the pairs it adds to the "
-                "exact join (signature collisions)",
+                "exact join (signature collisions); gf8 = byte symbols over GF(2^8), 4 components",
         "sig_only_n4": variant(4, "sig_only"),
         "sig_only_n2": variant(2, "sig_only"),
         "exact_n2": variant(2, "inner"),
+        "sig_only_gf8": variant(4, "sig_only", field=8),
+        "exact_gf8": variant(4, "inner", field=8),
     }
+    # the byte-symbol signature kernel alone on S (keys / CUDA-event time)
+    for _ in range(2):
+        ag.sig_compute_gf8(dS, sigS, stream=stream)
+    g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    g0.record(stream)
+    for _ in range(5):
+        ag.sig_compute_gf8(dS, sigS, stream=stream)
+    g1.record(stream)
+    torch.cuda.synchronize()
+    gms = g0.elapsed_time(g1) / 5
+    paper_variants["gf8_signature_kernel_S"] = {"ms": gms, "key_gbps": wl.S.nbytes / (gms * 1e-3) / 1e9}
 
     # cumulative (prefix) signatures of S at 256-byte blocks: the layout pass and the
     # signatures pass, timed apart (keys / CUDA-event time)

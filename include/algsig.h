@@ -104,6 +104,20 @@ as_status as_sig_compute_n(const uint8_t* d_arena, const uint64_t* d_off, uint64
                            uint64_t* d_sig_out, as_stream stream);
 
 /*
+ * as_sig_compute_gf8 -- signatures with byte symbols (Section 3.1: a symbol
+ * is a byte or a double byte): GF(2^8) with field polynomial
+ * x^8 + x^4 + x^3 + x^2 + 1, alpha_k = x^k, p_i = byte i,
+ *     sig8^k = sum_{i=0}^{l-1} b_i x^(k i),   k = 1..4,
+ * packed with component k in bits [8(k-1), 8k) (bits 32..63 zero).  Keys of
+ * equal length under 255 bytes that differ in at most 4 bytes have different
+ * signatures; past 255 bytes the exponent wraps (x^255 = 1).  A join on them is
+ * as_join_build with d_sigR and as_join_probe_mode with d_sigS, both from this
+ * call.  Arguments and errors as for as_sig_compute.
+ */
+as_status as_sig_compute_gf8(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, uint64_t* d_sig_out,
+                             as_stream stream);
+
+/*
  * Cumulative (prefix) signatures (Section 5 lists them, after the paper's
  * reference [7], as the way to signatures of prefixes and substrings).  For a
  * block size B (a positive multiple of 16 bytes) key i of length len gets

@@ -11,6 +11,9 @@ It wraps oracle.c, a plain C statement of:
     the table definition and once by Horner's rule (Section 3.1);
   * cumulative signatures (the signatures of a key's block prefixes), by
     definition from the signature routine, in Python;
+  * the GF(2^8) byte-symbol signature (field polynomial x^8+x^4+x^3+x^2+1),
+    by the table definition and by Horner's rule (Section 3.1's other symbol
+    size);
   * the n-component signature (the first n of the four components) and the
     signature-only join of Figure 2 (pairs of equal signature and length, no
     byte comparison; not exact, kept to count collisions), in Python;
@@ -74,6 +77,13 @@ def _load():
         lib.or_sig_horner.argtypes = [P, U64]
         lib.or_sig_horner.restype = U64
         lib.or_sig_batch.argtypes = [P, P, U64, P, ctypes.c_int, ctypes.c_int]
+        lib.or_gf8_init.restype = ctypes.c_int
+        lib.or_gf8_tables.argtypes = [P, P]
+        lib.or_sig8_tables.argtypes = [P, U64]
+        lib.or_sig8_tables.restype = U64
+        lib.or_sig8_horner.argtypes = [P, U64]
+        lib.or_sig8_horner.restype = U64
+        lib.or_sig8_batch.argtypes = [P, P, U64, P, ctypes.c_int, ctypes.c_int]
         for f in (lib.or_join_nested, lib.or_join_simple):
             f.argtypes = [P, P, P, U64, P, P, P, U64, P, U64]
             f.restype = U64
@@ -81,6 +91,8 @@ def _load():
         lib.or_join_grace.restype = U64
         if not lib.or_gf_init():
             raise RuntimeError("oracle: x is not primitive under the field polynomial")
+        if not lib.or_gf8_init():
+            raise RuntimeError("oracle: x is not primitive under the GF(2^8) polynomial")
         _lib = lib
         return lib
 
@@ -125,6 +137,38 @@ def sig(key: bytes, method: str = "tables") -> int:
 
 def components(s: int):
     return tuple((s >> (16 * k)) & 0xFFFF for k in range(4))
+
+
+POLY8 = 0x11D           # x^8 + x^4 + x^3 + x^2 + 1 (byte symbols)
+ORDER8 = 255
+
+
+def gf8_tables():
+    """(log[256], antilog[255]) of GF(2^8) as uint8 arrays."""
+    lib = _load()
+    log = np.zeros(256, dtype=np.uint8)
+    alog = np.zeros(255, dtype=np.uint8)
+    lib.or_gf8_tables(log.ctypes.data, alog.ctypes.data)
+    return log, alog
+
+
+def sig8(key: bytes, method: str = "tables") -> int:
+    """Signature over GF(2^8) with byte symbols (the paper's other symbol size):
+    sig^k = sum_i b_i x^(k i), k = 1..4, component k in bits [8(k-1), 8k)."""
+    lib = _load()
+    arr, p = _buf(key)
+    f = lib.or_sig8_tables if method == "tables" else lib.or_sig8_horner
+    return int(f(p, len(key)))
+
+
+def sig8_batch(arena: np.ndarray, off: np.ndarray, method: str = "tables", nthreads: int = 1) -> np.ndarray:
+    lib = _load()
+    n = off.shape[0] - 1
+    out = np.zeros(max(n, 1), dtype=np.uint64)
+    arena = np.ascontiguousarray(arena)
+    off = np.ascontiguousarray(off, dtype=np.uint64)
+    lib.or_sig8_batch(arena.ctypes.data, off.ctypes.data, n, out.ctypes.data, 0 if method == "tables" else 1, nthreads)
+    return out[:n]
 
 
 def component_mask(n_components: int) -> int:
@@ -216,14 +260,19 @@ def join_mode(R, S, mode: str) -> np.ndarray:
     return sort_pairs(out)
 
 
-def join_sig_only(R, S, n_components: int = 4) -> np.ndarray:
+def join_sig_only(R, S, n_components: int = 4, field: int = 16) -> np.ndarray:
     """The probe of Figure 2 as the paper states it (output on a signature
     match, Section 3.2): every (r.id, s.id) whose n-component signatures and
     key lengths are equal, with no byte comparison.  Plain definition: group R
-    by (signature, length) and look every S key up.  Sorted like sort_pairs."""
-    mask = np.uint64(component_mask(n_components))
-    sR = sig_batch(R.arena, R.off) & mask
-    sS = sig_batch(S.arena, S.off) & mask
+    by (signature, length) and look every S key up.  field = 8 uses the byte
+    symbol signatures (all four components).  Sorted like sort_pairs."""
+    if field == 8:
+        sR = sig8_batch(R.arena, R.off)
+        sS = sig8_batch(S.arena, S.off)
+    else:
+        mask = np.uint64(component_mask(n_components))
+        sR = sig_batch(R.arena, R.off) & mask
+        sS = sig_batch(S.arena, S.off) & mask
     lR = np.diff(np.asarray(R.off, dtype=np.uint64))
     lS = np.diff(np.asarray(S.off, dtype=np.uint64))
     groups = {}

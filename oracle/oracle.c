@@ -341,3 +341,100 @@ uint64_t or_join_grace(const uint8_t* aR, const uint64_t* oR, const uint32_t* id
     free(rpart); free(spart); free(rcnt); free(scnt); free(th); free(jobs);
     return total;
 }
+
+/* ------------------------------------------------------------------ */
+/* Byte symbols: GF(2^8) (Section 3.1: "a symbol is either a byte or a */
+/* double byte")                                                       */
+/* ------------------------------------------------------------------ */
+
+/* Reading: field polynomial x^8 + x^4 + x^3 + x^2 + 1 (0x11D), alpha_k = x^k,
+   symbol p_i = byte i, 4 components packed with component k in bits
+   [8(k-1), 8k) of the low 32 bits. */
+#define OR8_POLY 0x11Du
+#define OR8_ORDER 255u
+
+static uint8_t g8_log[256];
+static uint8_t g8_antilog[255];
+static int g8_ready = 0;
+
+static uint32_t times_x8(uint32_t a) {
+    a <<= 1;
+    if (a & 0x100u) a ^= OR8_POLY;
+    return a;
+}
+
+/* log / antilog of x by repeated multiplication; 1 if x is primitive */
+int or_gf8_init(void) {
+    if (g8_ready) return 1;
+    uint32_t a = 1;
+    for (uint32_t e = 0; e < OR8_ORDER; e++) {
+        if (e > 0 && a == 1) return 0;
+        g8_antilog[e] = (uint8_t)a;
+        g8_log[a] = (uint8_t)e;
+        a = times_x8(a);
+    }
+    if (a != 1) return 0;
+    g8_ready = 1;
+    return 1;
+}
+
+void or_gf8_tables(uint8_t* log_out, uint8_t* antilog_out) {
+    or_gf8_init();
+    if (log_out) memcpy(log_out, g8_log, sizeof(g8_log));
+    if (antilog_out) memcpy(antilog_out, g8_antilog, sizeof(g8_antilog));
+}
+
+/* The definition: sig^k = XOR over i with b_i != 0 of antilog[(log b_i + k*i) mod 255]. */
+uint64_t or_sig8_tables(const uint8_t* key, uint64_t len) {
+    or_gf8_init();
+    uint8_t s[4] = {0, 0, 0, 0};
+    for (uint64_t i = 0; i < len; i++) {
+        if (key[i] == 0) continue;
+        const uint64_t lb = g8_log[key[i]];
+        for (int k = 1; k <= 4; k++) s[k - 1] ^= g8_antilog[(lb + (uint64_t)k * (i % OR8_ORDER)) % OR8_ORDER];
+    }
+    return (uint64_t)s[0] | ((uint64_t)s[1] << 8) | ((uint64_t)s[2] << 16) | ((uint64_t)s[3] << 24);
+}
+
+/* Independent route: Horner's rule from the last byte down, s_k <- s_k * x^k + b_i,
+   multiplying by x with the shift-and-reduce step only. */
+uint64_t or_sig8_horner(const uint8_t* key, uint64_t len) {
+    uint32_t s[4] = {0, 0, 0, 0};
+    for (uint64_t t = len; t > 0; t--) {
+        for (int k = 0; k < 4; k++) {
+            uint32_t a = s[k];
+            for (int r = 0; r <= k; r++) a = times_x8(a);
+            s[k] = a ^ key[t - 1];
+        }
+    }
+    return (uint64_t)s[0] | ((uint64_t)s[1] << 8) | ((uint64_t)s[2] << 16) | ((uint64_t)s[3] << 24);
+}
+
+typedef struct {
+    const uint8_t* arena; const uint64_t* off; uint64_t lo, hi; uint64_t* out; int method;
+} sig8_job;
+
+static void* sig8_worker(void* arg) {
+    sig8_job* j = (sig8_job*)arg;
+    for (uint64_t i = j->lo; i < j->hi; i++) {
+        const uint8_t* k = j->arena + j->off[i];
+        uint64_t len = j->off[i + 1] - j->off[i];
+        j->out[i] = j->method ? or_sig8_horner(k, len) : or_sig8_tables(k, len);
+    }
+    return NULL;
+}
+
+void or_sig8_batch(const uint8_t* arena, const uint64_t* off, uint64_t n, uint64_t* out, int method, int nthreads) {
+    or_gf8_init();
+    if (nthreads < 1) nthreads = 1;
+    if ((uint64_t)nthreads > n) nthreads = n ? (int)n : 1;
+    pthread_t* th = (pthread_t*)malloc(sizeof(pthread_t) * nthreads);
+    sig8_job* jobs = (sig8_job*)malloc(sizeof(sig8_job) * nthreads);
+    for (int t = 0; t < nthreads; t++) {
+        jobs[t].arena = arena; jobs[t].off = off; jobs[t].out = out; jobs[t].method = method;
+        jobs[t].lo = n * t / nthreads; jobs[t].hi = n * (t + 1) / nthreads;
+        pthread_create(&th[t], NULL, sig8_worker, &jobs[t]);
+    }
+    for (int t = 0; t < nthreads; t++) pthread_join(th[t], NULL);
+    free(th); free(jobs);
+}

@@ -30,7 +30,7 @@ AS_ERR_TABLE_FULL = 4
 AS_ERR_CUDA = 5
 AS_ERR_UNSUPPORTED = 6
 
-EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_sig_compute_n",
+EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_sig_compute_n", "as_sig_compute_gf8",
            "as_sig_prefix_ws_bytes", "as_sig_prefix_offsets", "as_sig_prefixes", "as_join_table_bytes",
            "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_probe_sigs", "as_join_probe_mode", "as_join_ws_bytes", "as_join",
            "as_baseline_ws_bytes", "as_baseline_join")
@@ -73,6 +73,8 @@ def load(path: str | None = None):
         lib.as_sig_compute.restype = S
         lib.as_sig_compute_n.argtypes = [P, P, U64, S, P, P]
         lib.as_sig_compute_n.restype = S
+        lib.as_sig_compute_gf8.argtypes = [P, P, U64, P, P]
+        lib.as_sig_compute_gf8.restype = S
         lib.as_sig_prefix_ws_bytes.argtypes = [U64]
         lib.as_sig_prefix_ws_bytes.restype = SZ
         lib.as_sig_prefix_offsets.argtypes = [P, U64, ctypes.c_uint32, P, P, SZ, P]
@@ -170,6 +172,17 @@ def sig_compute(rel: DeviceRelation, out: torch.Tensor | None = None, stream=Non
         _check(lib.as_sig_compute(_ptr(rel.arena), _ptr(rel.off), n, _ptr(out), _stream(stream)))
     else:
         _check(lib.as_sig_compute_n(_ptr(rel.arena), _ptr(rel.off), n, n_components, _ptr(out), _stream(stream)))
+    return out
+
+
+def sig_compute_gf8(rel: DeviceRelation, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """as_sig_compute_gf8: byte-symbol signature over GF(2^8) of every key (int64 bits,
+    component k in bits [8(k-1), 8k))."""
+    lib = load()
+    n = rel.n
+    if out is None:
+        out = torch.empty(max(n, 0), dtype=torch.int64, device=rel.arena.device)
+    _check(lib.as_sig_compute_gf8(_ptr(rel.arena), _ptr(rel.off), n, _ptr(out), _stream(stream)))
     return out
 
 

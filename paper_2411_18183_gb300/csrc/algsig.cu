@@ -681,6 +681,7 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
 }  // namespace algsig
 
 #include "prefix.cuh"
+#include "gf8.cuh"
 
 namespace algsig {
 
@@ -950,6 +951,9 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaFuncSetAttribute(prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPrefix)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
+    if ((e = cudaFuncSetAttribute(sig8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig8)) !=
+        cudaSuccess)
+      return cuda_fail(e, "kernel attribute");
     if ((e = cudaFuncSetAttribute(bl_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBHash)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
@@ -1034,6 +1038,22 @@ as_status as_sig_compute(const uint8_t* d_arena, const uint64_t* d_off, uint64_t
   if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute: null pointer");
   if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute: arena not 16-byte aligned");
   return launch_sig(d_arena, d_off, n, d_sig_out, (cudaStream_t)stream);
+}
+
+as_status as_sig_compute_gf8(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, uint64_t* d_sig_out,
+                             as_stream stream) {
+  if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute_gf8: null pointer");
+  if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute_gf8: arena not 16-byte aligned");
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  if (n == 0) return AS_OK;
+  const uint64_t want = (n + kG8Threads - 1) / kG8Threads;
+  const unsigned blocks = (unsigned)(want < (uint64_t)d->sms * 8 ? want : (uint64_t)d->sms * 8);
+  sig8_kernel<<<blocks, kG8Threads, kSmemSig8, (cudaStream_t)stream>>>(d_arena, d_off, n, d_sig_out);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "byte-symbol signature kernel launch");
+  return AS_OK;
 }
 
 size_t as_sig_prefix_ws_bytes(uint64_t n) {

@@ -74,3 +74,49 @@ def solve(M, rhs):
                 f = A[r][c]
                 A[r] = [v ^ gmul(f, w) for v, w in zip(A[r], A[c])]
     return [A[r][n] for r in range(n)]
+
+
+# ---- byte symbols: GF(2^8) with x^8 + x^4 + x^3 + x^2 + 1 -------------------
+
+POLY8 = (1 << 8) | (1 << 4) | (1 << 3) | (1 << 2) | 1
+
+
+def gmul8(a: int, b: int) -> int:
+    return polymod(clmul(a, b), POLY8)
+
+
+def gpow8(a: int, e: int) -> int:
+    r = 1
+    while e:
+        if e & 1:
+            r = gmul8(r, a)
+        a = gmul8(a, a)
+        e >>= 1
+    return r
+
+
+def sig8_by_polynomial(key: bytes) -> int:
+    """Each component as one GF(2)[x] polynomial sum_i b_i(x) x^(k i), reduced once."""
+    out = 0
+    for k in range(1, 5):
+        big = 0
+        for i, b in enumerate(bytes(key)):
+            big ^= b << (k * i)
+        out |= polymod(big, POLY8) << (8 * (k - 1))
+    return out
+
+
+def solve8(M, rhs):
+    """Gaussian elimination over GF(2^8): M x = rhs (M square, non-singular)."""
+    n = len(M)
+    A = [list(M[r]) + [rhs[r]] for r in range(n)]
+    for c in range(n):
+        p = next(r for r in range(c, n) if A[r][c])
+        A[c], A[p] = A[p], A[c]
+        inv = gpow8(A[c][c], 254)
+        A[c] = [gmul8(v, inv) for v in A[c]]
+        for r in range(n):
+            if r != c and A[r][c]:
+                f = A[r][c]
+                A[r] = [v ^ gmul8(f, w) for v, w in zip(A[r], A[c])]
+    return [A[r][n] for r in range(n)]

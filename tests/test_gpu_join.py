@@ -249,3 +249,37 @@ def test_signature_only_probe_matches_oracle(cuda, n_components):
         assert np.array_equal(got, want), (mode, n_components)
     extra = len(oracle.join_sig_only(Rh, Sh, n_components)) - len(oracle.join_simple(Rh, Sh))
     assert extra == (1 if n_components == 4 else 2)
+
+
+def test_byte_symbol_join_exact_and_signature_only(cuda):
+    """The join on GF(2^8) signatures (as_sig_compute_gf8 on both sides): exact
+    with verification, and the signature-only probe adds exactly the
+    constructed five-byte collision (and the pair past the 255-byte wrap)."""
+    from gfpoly import gpow8, solve8
+    ag = cuda
+    rng = random.Random(808)
+    pos = [2, 9, 40, 100, 200]
+    M = [[gpow8(2, k * pos[j]) for j in range(4)] for k in range(1, 5)]
+    d = solve8(M, [gpow8(2, k * pos[4]) for k in range(1, 5)]) + [1]
+    a = bytes(rng.randrange(32, 127) for _ in range(230))
+    b = bytearray(a)
+    for p_, dj in zip(pos, d):
+        b[p_] ^= dj
+    w = bytes(rng.randrange(32, 127) for _ in range(300))
+    w2 = bytearray(w)
+    w2[0] ^= 0x5A
+    w2[255] ^= 0x5A
+    wl = workloads.generate(workloads.CONFIGS["large"].scaled(2000, 10_000))
+    Rh = relation_garbage_tail([wl.R.key(i) for i in range(wl.R.n)] + [a, w], seed=5)
+    Sh = relation_garbage_tail([wl.S.key(i) for i in range(wl.S.n)] + [bytes(b), bytes(w2), a], seed=6)
+    R, S = dev(ag, Rh), dev(ag, Sh)
+    sigR, sigS = ag.sig_compute_gf8(R), ag.sig_compute_gf8(S)
+    ws = ag.alloc_ws(ag.join_table_bytes(R.n, 0.5))
+    t = ag.join_build(R, ws, 0.5, sigR=sigR)
+    for mode, want in (("sig_only", oracle.join_sig_only(Rh, Sh, field=8)), ("inner", oracle.join_simple(Rh, Sh))):
+        pairs = torch.zeros(2 * (len(want) + 64), dtype=torch.int32, device="cuda")
+        count = torch.zeros(1, dtype=torch.int64, device="cuda")
+        cnt = ag.join_probe_mode(t, S, sigS, pairs, count, mode=mode)
+        got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
+        assert np.array_equal(got, want), mode
+    assert len(oracle.join_sig_only(Rh, Sh, field=8)) - len(oracle.join_simple(Rh, Sh)) >= 2

@@ -120,3 +120,21 @@ def test_cumulative_signatures(cuda, block_bytes):
             assert out[pref[i]:pref[i + 1]].tolist() == want, (i, int(lens[i]))
     with pytest.raises(ag.AlgsigError):
         ag.sig_prefixes(ag.DeviceRelation.from_host(rels[0].arena, rels[0].off, rels[0].ids), 24)
+
+
+def test_byte_symbol_signatures_gf8(cuda):
+    """as_sig_compute_gf8 against the oracle's GF(2^8) definition: every
+    alignment, every short length, keys past the 255-byte exponent wrap, and a
+    scaled large-workload relation."""
+    ag = cuda
+    rng = random.Random(8)
+    keys = edge_keys() + [bytes(rng.randrange(256) for _ in range(n)) for n in
+                          list(range(0, 70)) + [254, 255, 256, 257, 511, 4097, 9000]]
+    rels = [relation_garbage_tail(interleave_gaps(keys, seed=s), seed=s) for s in range(3)]
+    rels.append(workloads.generate(workloads.CONFIGS["large"].scaled(1000, 5000)).S)
+    for rel in rels:
+        D = ag.DeviceRelation.from_host(rel.arena, rel.off, rel.ids)
+        got = ag.sig_compute_gf8(D).cpu().numpy().view(np.uint64)
+        want = oracle.sig8_batch(rel.arena, rel.off, nthreads=8)
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, f"{bad.size} mismatches, first at key {bad[:5].tolist()}"

@@ -6,6 +6,7 @@ import numpy as np
 import pytest
 
 import oracle
+import workloads
 from cases import edge_keys, five_symbol_collision, symbol_collision
 from gfpoly import gmul, gpow, sig_by_polynomial, symbols
 
@@ -181,3 +182,46 @@ def test_cumulative_signatures_and_substring_rule():
             d = comp(full, k) ^ comp(pre, k)
             got |= gmul(d, gpow(gpow(2, k * (a // 2)), 65534)) << (16 * (k - 1))
         assert got == want
+
+
+def test_byte_symbol_signature_gf8():
+    """The GF(2^8) signature (byte symbols): x is primitive under
+    x^8+x^4+x^3+x^2+1 (order 255); tables = Horner = the polynomial definition;
+    a single byte gives that byte in every component; keys of equal length
+    under 255 bytes that differ in at most 4 bytes never collide, a constructed
+    5-byte difference does, and past 255 bytes the exponent wraps (x^255 = 1),
+    so equal changes at bytes 0 and 255 cancel."""
+    from gfpoly import gmul8, gpow8, sig8_by_polynomial, solve8
+    for p in (3, 5, 17):
+        assert gpow8(2, 255 // p) != 1
+    assert gpow8(2, 255) == 1
+    rng = random.Random(88)
+    assert oracle.sig8(b"") == 0
+    for b in range(256):
+        assert oracle.sig8(bytes([b])) == b * 0x01010101
+    for _ in range(150):
+        key = rand_key(rng, rng.randrange(0, 300))
+        s = oracle.sig8(key)
+        assert s == oracle.sig8(key, "horner") == sig8_by_polynomial(key)
+    for _ in range(300):
+        key = rand_key(rng, rng.randrange(4, 255))
+        other = bytearray(key)
+        for pos in rng.sample(range(len(key)), rng.randrange(1, 5)):
+            other[pos] ^= rng.randrange(1, 256)
+        assert oracle.sig8(bytes(other)) != oracle.sig8(key)
+    pos = [2, 9, 40, 100, 200]
+    M = [[gpow8(2, k * pos[j]) for j in range(4)] for k in range(1, 5)]
+    d = solve8(M, [gpow8(2, k * pos[4]) for k in range(1, 5)]) + [1]
+    key = rand_key(rng, 230)
+    other = bytearray(key)
+    for p_, dj in zip(pos, d):
+        other[p_] ^= dj
+    assert bytes(other) != key and oracle.sig8(bytes(other)) == oracle.sig8(key)
+    key = rand_key(rng, 300)
+    other = bytearray(key)
+    other[0] ^= 0x5A
+    other[255] ^= 0x5A
+    assert oracle.sig8(bytes(other)) == oracle.sig8(key)
+    batch_keys = [rand_key(rng, rng.randrange(0, 90)) for _ in range(200)]
+    rel = workloads.relation_from_keys(batch_keys)
+    assert oracle.sig8_batch(rel.arena, rel.off, nthreads=3).tolist() == [oracle.sig8(k) for k in batch_keys]
