@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/algsig.h"
+#include <nvtx3/nvToolsExt.h>
 #include "gf16.cuh"
 
 namespace algsig {
@@ -1014,6 +1015,15 @@ static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t 
 
 using namespace algsig;
 
+// NVTX range around each entry point (a profiler shows the library's calls on
+// the host timeline; without one attached the calls cost nothing)
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 extern "C" {
 
 const char* as_last_error(void) { return t_err.c_str(); }
@@ -1035,6 +1045,7 @@ int as_version(void) { return 100; }
 
 as_status as_sig_compute(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, uint64_t* d_sig_out,
                          as_stream stream) {
+  NvtxRange nvtx_range("as_sig_compute");
   if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute: null pointer");
   if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute: arena not 16-byte aligned");
   return launch_sig(d_arena, d_off, n, d_sig_out, (cudaStream_t)stream);
@@ -1042,6 +1053,7 @@ as_status as_sig_compute(const uint8_t* d_arena, const uint64_t* d_off, uint64_t
 
 as_status as_sig_compute_gf8(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, uint64_t* d_sig_out,
                              as_stream stream) {
+  NvtxRange nvtx_range("as_sig_compute_gf8");
   if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute_gf8: null pointer");
   if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute_gf8: arena not 16-byte aligned");
   DeviceState* d = nullptr;
@@ -1062,6 +1074,7 @@ size_t as_sig_prefix_ws_bytes(uint64_t n) {
 
 as_status as_sig_prefix_offsets(const uint64_t* d_off, uint64_t n, uint32_t block_bytes, uint64_t* d_pref_off,
                                 void* d_ws, size_t ws_bytes, as_stream stream) {
+  NvtxRange nvtx_range("as_sig_prefix_offsets");
   if (block_bytes == 0 || block_bytes % 16 != 0)
     return fail(AS_ERR_INVALID, "as_sig_prefix_offsets: block_bytes %u is not a positive multiple of 16", block_bytes);
   if (!d_pref_off || (n > 0 && (!d_off || !d_ws))) return fail(AS_ERR_INVALID, "as_sig_prefix_offsets: null pointer");
@@ -1088,6 +1101,7 @@ as_status as_sig_prefix_offsets(const uint64_t* d_off, uint64_t n, uint32_t bloc
 
 as_status as_sig_prefixes(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, uint32_t block_bytes,
                           const uint64_t* d_pref_off, uint64_t* d_out, as_stream stream) {
+  NvtxRange nvtx_range("as_sig_prefixes");
   if (block_bytes == 0 || block_bytes % 16 != 0)
     return fail(AS_ERR_INVALID, "as_sig_prefixes: block_bytes %u is not a positive multiple of 16", block_bytes);
   if (n > 0 && (!d_arena || !d_off || !d_pref_off || !d_out)) return fail(AS_ERR_INVALID, "as_sig_prefixes: null pointer");
@@ -1107,6 +1121,7 @@ as_status as_sig_prefixes(const uint8_t* d_arena, const uint64_t* d_off, uint64_
 
 as_status as_sig_compute_n(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, int n_components,
                            uint64_t* d_sig_out, as_stream stream) {
+  NvtxRange nvtx_range("as_sig_compute_n");
   if (n_components != 2 && n_components != 4)
     return fail(AS_ERR_INVALID, "as_sig_compute_n: n_components must be 2 or 4 (got %d)", n_components);
   if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute_n: null pointer");
@@ -1129,6 +1144,7 @@ size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor) {
 as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, const uint64_t* d_offR,
                         const uint32_t* d_idR, uint64_t m, const uint64_t* d_sigR, float load_factor, as_table* out,
                         as_stream stream) {
+  NvtxRange nvtx_range("as_join_build");
   if (!out) return fail(AS_ERR_INVALID, "as_join_build: null table");
   uint64_t cap;
   uint32_t l2;
@@ -1245,6 +1261,7 @@ static as_status finish_probe(const char* fn, const as_table* t, uint64_t cap_pa
 as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS,
                         uint64_t n, uint64_t* d_sigS_out, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
                         uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  NvtxRange nvtx_range("as_join_probe");
   as_status st = probe_args("as_join_probe", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
   if (st != AS_OK) return st;
   uint64_t* sigS = d_sigS_out;
@@ -1274,6 +1291,7 @@ as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64
 as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
                              const uint32_t* d_idS, uint64_t n, const uint64_t* d_sigS, uint32_t* d_pairs,
                              uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  NvtxRange nvtx_range("as_join_probe_sigs");
   as_status st = probe_args("as_join_probe_sigs", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
   if (st != AS_OK) return st;
   if (n > 0 && !d_sigS) return fail(AS_ERR_INVALID, "as_join_probe_sigs: null signatures");
@@ -1293,6 +1311,7 @@ as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const u
 as_status as_join_probe_mode(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
                              const uint32_t* d_idS, uint64_t n, const uint64_t* d_sigS, int mode, uint32_t* d_pairs,
                              uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  NvtxRange nvtx_range("as_join_probe_mode");
   as_status st = probe_args("as_join_probe_mode", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
   if (st != AS_OK) return st;
   if (mode < AS_JOIN_INNER || mode > AS_JOIN_SIG_ONLY) return fail(AS_ERR_INVALID, "as_join_probe_mode: mode %d", mode);
@@ -1314,6 +1333,7 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
                   const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
                   float load_factor, void* d_ws, size_t ws_bytes, uint32_t* d_pairs, uint64_t cap_pairs,
                   uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  NvtxRange nvtx_range("as_join");
   const size_t tb = as_join_table_bytes(m, load_factor);
   if (!tb) return fail(AS_ERR_INVALID, "as_join: need 0 < load_factor <= 1 and m < 2^32-1");
   const size_t need = as_join_ws_bytes(m, n, load_factor);
@@ -1370,6 +1390,7 @@ as_status as_baseline_join(const uint8_t* d_arenaR, const uint64_t* d_offR, cons
                            const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
                            float load_factor, int tagged, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
                            uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  NvtxRange nvtx_range("as_baseline_join");
   uint64_t cap;
   uint32_t l2;
   if (!table_geometry(m, load_factor, &cap, &l2))
@@ -1455,6 +1476,7 @@ size_t as_join_batch_ws_bytes(const as_join_desc* descs, int n_joins, uint64_t m
 
 as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t mR, uint64_t nS, float load_factor,
                                 void* d_ws, size_t ws_bytes, as_batch* out, as_stream stream) {
+  NvtxRange nvtx_range("as_join_batch_prepare");
   if (!out) return fail(AS_ERR_INVALID, "as_join_batch_prepare: null batch");
   uint64_t tot, vr, vs, bytes;
   if (!batch_layout(descs, n_joins, mR, nS, load_factor, &tot, &vr, &vs, &bytes))
@@ -1519,6 +1541,7 @@ as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t
 as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR,
                             const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint32_t* d_pairs,
                             uint64_t* d_counts, as_stream stream) {
+  NvtxRange nvtx_range("as_join_batch_run");
   if (!b || !b->descs || !d_counts) return fail(AS_ERR_INVALID, "as_join_batch_run: null batch or counters");
   if (!d_arenaR || !d_offR || !d_arenaS || !d_offS) return fail(AS_ERR_INVALID, "as_join_batch_run: null relation");
   if (misaligned16(d_arenaR) || misaligned16(d_arenaS))
@@ -1577,6 +1600,7 @@ as_status as_join_batch(const uint8_t* d_arenaR, const uint64_t* d_offR, const u
                         const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t nS,
                         const as_join_desc* descs, int n_joins, float load_factor, void* d_ws, size_t ws_bytes,
                         uint32_t* d_pairs, uint64_t* d_counts, as_stream stream) {
+  NvtxRange nvtx_range("as_join_batch");
   as_batch b;
   as_status st = as_join_batch_prepare(descs, n_joins, mR, nS, load_factor, d_ws, ws_bytes, &b, stream);
   if (st != AS_OK) return st;
@@ -1601,6 +1625,7 @@ extern "C" as_status as_join_probe_noalloc(const as_table* t, const uint8_t* d_a
                                            const uint32_t* d_idS, uint64_t n, uint32_t* d_pairs,
                                            uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count,
                                            as_stream stream) {
+  NvtxRange nvtx_range("as_join_probe_noalloc");
   using namespace algsig;
   if (n > (uint64_t)AS_PROBE_NOALLOC_MAX_KEYS)
     return fail(AS_ERR_INVALID, "as_join_probe_noalloc: %llu keys, the fixed scratch holds at most %u",

@@ -41,6 +41,7 @@ class Request:
     done: float | None = None
     count: int | None = None        # pairs found
     pairs: object = None            # (cnt, 2) uint32 pairs when results are kept
+    status: str = "pending"         # done, cancelled (before launch) or timeout (never admitted in time)
 
     @property
     def latency(self) -> float | None:
@@ -48,16 +49,28 @@ class Request:
 
 
 class Ledger:
-    """Admission accounting: admitted bytes never exceed the budget."""
+    """Admission accounting: admitted bytes never exceed the budget.
+    refuse_next(k) makes the next k admissions fail as if the device memory
+    were taken (a host-side injection of an allocation failure): the requests
+    wait and are admitted later."""
 
     def __init__(self, budget: int):
         self.budget = int(budget)
         self.used = 0
         self.peak = 0
+        self.refusals = 0
+        self.refused = 0
+
+    def refuse_next(self, k: int = 1) -> None:
+        self.refusals += int(k)
 
     def try_admit(self, nbytes: int) -> bool:
         if nbytes > self.budget:
             raise ValueError(f"request of {nbytes} bytes can never fit a budget of {self.budget}")
+        if self.refusals > 0:
+            self.refusals -= 1
+            self.refused += 1
+            return False
         if self.used + nbytes > self.budget:
             return False
         self.used += nbytes
@@ -104,15 +117,19 @@ class Server:
     request_bytes(pool_index)."""
 
     def __init__(self, executor, budget_bytes: int, max_batch: int = 64, clock=time.perf_counter,
-                 idle_sleep: float = 20e-6):
+                 idle_sleep: float = 20e-6, admit_timeout: float | None = None):
         self.ex = executor
         self.ledger = Ledger(budget_bytes)
         self.max_batch = max_batch
         self.clock = clock
         self.idle_sleep = idle_sleep
+        self.admit_timeout = admit_timeout      # seconds a request may wait for admission
         self.batches = 0
 
-    def run(self, arrivals, timeout: float = 600.0):
+    def run(self, arrivals, timeout: float = 600.0, cancels=()):
+        """Serve the (time, pool_index) arrivals.  cancels: (time, request id)
+        pairs; a request cancelled before its batch is launched is dropped (its
+        admitted bytes are released), one already launched completes."""
         # A collection of the cyclic garbage collector can pause the loop for tens
         # of milliseconds while requests keep arriving; collect once up front and
         # keep it off while requests are in flight.
@@ -120,15 +137,16 @@ class Server:
         was_enabled = gc.isenabled()
         gc.disable()
         try:
-            return self._run(arrivals, timeout)
+            return self._run(arrivals, timeout, cancels)
         finally:
             if was_enabled:
                 gc.enable()
 
-    def _run(self, arrivals, timeout: float):
+    def _run(self, arrivals, timeout: float, cancels):
         reqs = [Request(i, p, t, self.ex.request_bytes(p)) for i, (t, p) in enumerate(sorted(arrivals))]
         pending = collections.deque(reqs)
         waiting, admitted = collections.deque(), collections.deque()
+        cancel_q = collections.deque(sorted(cancels))
         busy = {}                                        # slot -> batch
         free = collections.deque(self.ex.slots())
         t0 = self.clock()
@@ -140,6 +158,27 @@ class Server:
             progressed = False
             while pending and pending[0].arrival <= now:
                 waiting.append(pending.popleft())
+            while cancel_q and cancel_q[0][0] <= now:     # cancellations due: drop requests not yet launched
+                _, rid = cancel_q.popleft()
+                r = reqs[rid]
+                if r.status != "pending" or r.launched is not None:
+                    continue
+                if r in waiting:
+                    waiting.remove(r)
+                elif r in admitted:
+                    admitted.remove(r)
+                    self.ledger.release(r.nbytes)
+                elif r in pending:
+                    pending.remove(r)
+                r.status, r.done = "cancelled", now
+                finished += 1
+                progressed = True
+            if self.admit_timeout is not None:           # requests that waited too long for admission
+                while waiting and now - waiting[0].arrival > self.admit_timeout:
+                    r = waiting.popleft()
+                    r.status, r.done = "timeout", now
+                    finished += 1
+                    progressed = True
             while waiting and self.ledger.try_admit(waiting[0].nbytes):
                 r = waiting.popleft()
                 r.admitted = now
@@ -151,7 +190,7 @@ class Server:
                     continue
                 t = self.clock() - t0
                 for r, cnt, pairs in res:
-                    r.done, r.count, r.pairs = t, cnt, pairs
+                    r.done, r.count, r.pairs, r.status = t, cnt, pairs, "done"
                     self.ledger.release(r.nbytes)
                     finished += 1
                 del busy[slot]
@@ -179,12 +218,15 @@ class Server:
 
 
 def summarize(reqs, wall: float | None = None) -> dict:
-    lat = np.array([r.latency for r in reqs if r.latency is not None])
-    done = [r for r in reqs if r.done is not None]
+    served = [r for r in reqs if r.status == "done"]
+    lat = np.array([r.latency for r in served if r.latency is not None])
+    done = served
     span = wall if wall is not None else (max(r.done for r in done) - min(r.arrival for r in reqs)) if done else 0.0
     return {
         "requests": len(reqs),
         "completed": len(done),
+        "cancelled": sum(1 for r in reqs if r.status == "cancelled"),
+        "timed_out": sum(1 for r in reqs if r.status == "timeout"),
         "p50_ms": float(np.percentile(lat, 50) * 1e3) if len(lat) else None,
         "p99_ms": float(np.percentile(lat, 99) * 1e3) if len(lat) else None,
         "max_ms": float(lat.max() * 1e3) if len(lat) else None,

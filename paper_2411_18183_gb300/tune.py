@@ -67,9 +67,63 @@ class GraphBatch:
         return self.pairs[2 * d.pair_offset: 2 * (d.pair_offset + min(c, d.pair_cap))].view(-1, 2)
 
 
-def autotune(R: DeviceRelation, S: DeviceRelation, ranges, pair_caps, candidates=LOAD_FACTORS, reps: int = 3):
+class TuneCache:
+    """Best load factors found by autotune, keyed by (GPU name, key-length
+    class, size class) so that batches of the same shape skip the timing.
+    Optionally persisted as JSON."""
+
+    LENGTH_CLASSES = (128, 1024, 8192)          # upper bounds of the key-length bands, then longer
+
+    def __init__(self, path: str | None = None):
+        self.path = path
+        self.table: dict[str, float] = {}
+        if path:
+            import json
+            import os
+            if os.path.exists(path):
+                with open(path) as f:
+                    self.table = {k: float(v) for k, v in json.load(f).items()}
+
+    @classmethod
+    def key(cls, device_name: str, mean_key_bytes: float, rows: int) -> str:
+        lc = next((i for i, b in enumerate(cls.LENGTH_CLASSES) if mean_key_bytes <= b), len(cls.LENGTH_CLASSES))
+        sc = max(0, int(rows).bit_length() - 1)     # floor(log2(rows))
+        return f"{device_name}|len{lc}|rows2^{sc}"
+
+    def get(self, key: str):
+        return self.table.get(key)
+
+    def put(self, key: str, load_factor: float) -> None:
+        self.table[key] = float(load_factor)
+        if self.path:
+            import json
+            with open(self.path, "w") as f:
+                json.dump(self.table, f, indent=1, sort_keys=True)
+
+
+def batch_shape_key(R: DeviceRelation, S: DeviceRelation, ranges) -> str:
+    """TuneCache key of a batch: the device, the mean key length of its S rows
+    and its total S rows."""
+    ranges = list(ranges)
+    rows = sum(int(se) - int(sb) for (_, _, sb, se) in ranges)
+    nbytes = 0
+    if rows:
+        idx = torch.tensor([int(x) for (_, _, sb, se) in ranges for x in (sb, se)], dtype=torch.int64,
+                           device=S.off.device)
+        ends = S.off[idx].cpu().view(-1, 2)
+        nbytes = int((ends[:, 1] - ends[:, 0]).sum())
+    return TuneCache.key(torch.cuda.get_device_name(S.off.device), nbytes / max(1, rows), rows)
+
+
+def autotune(R: DeviceRelation, S: DeviceRelation, ranges, pair_caps, candidates=LOAD_FACTORS, reps: int = 3,
+             cache: TuneCache | None = None):
     """Time every candidate load factor on this batch; return (best GraphBatch
-    with its graph captured, {load_factor: ms})."""
+    with its graph captured, {load_factor: ms}).  With a cache, a batch of a
+    shape seen before takes the cached load factor without timing (the dict
+    is then empty)."""
+    key = batch_shape_key(R, S, ranges) if cache is not None else None
+    if cache is not None and cache.get(key) is not None:
+        return GraphBatch(R, S, ranges, pair_caps, cache.get(key)).capture(), {}
     times, best = {}, None
     for lf in candidates:
         gb = GraphBatch(R, S, ranges, pair_caps, lf)
@@ -78,4 +132,6 @@ def autotune(R: DeviceRelation, S: DeviceRelation, ranges, pair_caps, candidates
             best = gb
         else:
             del gb
+    if cache is not None:
+        cache.put(key, best.lf)
     return best.capture(), times

@@ -123,3 +123,24 @@ def test_autotuned_graph_batch(cuda, batch):
         Rj, Sj = batch.join_relations(j)
         got = oracle.sort_pairs(gb.result(j).cpu().numpy().view(np.uint32))
         assert np.array_equal(got, oracle.join_simple(Rj, Sj))
+
+
+def test_autotune_cache_skips_timing_for_a_known_shape(cuda, batch, tmp_path):
+    """With a TuneCache the first autotune times the candidates and records the
+    winner under the batch's shape; the second takes it without timing, and
+    its graph gives the same counts."""
+    from paper_2411_18183_gb300 import tune
+    ag = cuda
+    Rd, Sd = dev(ag, batch.R), dev(ag, batch.S)
+    R = ag.DeviceRelation(Rd.arena, Rd.off, None)
+    S = ag.DeviceRelation(Sd.arena, Sd.off, None)
+    caps = [max(64, 2 * e + 64) for e in batch.expected]
+    cache = tune.TuneCache(str(tmp_path / "tune.json"))
+    gb1, t1 = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1, cache=cache)
+    gb2, t2 = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1, cache=cache)
+    assert set(t1) == {0.4, 0.8} and t2 == {} and gb2.lf == gb1.lf
+    assert tune.TuneCache(str(tmp_path / "tune.json")).get(tune.batch_shape_key(R, S, batch.ranges)) == gb1.lf
+    gb2.counts.zero_()
+    gb2.replay()
+    torch.cuda.synchronize()
+    assert gb2.counts.cpu().tolist() == list(batch.expected)

@@ -283,3 +283,50 @@ def test_byte_symbol_join_exact_and_signature_only(cuda):
         got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
         assert np.array_equal(got, want), mode
     assert len(oracle.join_sig_only(Rh, Sh, field=8)) - len(oracle.join_simple(Rh, Sh)) >= 2
+
+
+def test_output_buffers_never_written_past_their_capacity(cuda):
+    """Canary words after every output buffer: the pairs buffer of a join that
+    overflows its capacity, the batch's per-join regions (each join's region
+    is followed by the next join's canaried gap) and the signature output stay
+    untouched past their ends."""
+    ag = cuda
+    CANARY = 0x5A5A5A5A
+    wl = workloads.generate(workloads.CONFIGS["plain"].scaled(1000, 10_000))
+    R, S = dev(ag, wl.R), dev(ag, wl.S)
+    ws = ag.alloc_ws(ag.join_ws_bytes(R.n, S.n, 0.5))
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    for cap in (0, 1, 100, 2999, 3000):
+        buf = torch.full((2 * cap + 64,), CANARY, dtype=torch.int32, device="cuda")
+        st, cnt = ag.join_into(R, S, ws, buf[: 2 * cap], count, 0.5, sync=True, allow_capacity=True)
+        assert cnt == 3000 and st == (ag.AS_OK if cap >= 3000 else ag.AS_ERR_CAPACITY)
+        assert bool((buf[2 * cap:] == CANARY).all()), cap
+    sig = torch.full((S.n + 16,), CANARY, dtype=torch.int64, device="cuda")
+    ag.sig_compute(S, sig[: S.n])
+    torch.cuda.synchronize()
+    assert bool((sig[S.n:] == CANARY).all())
+    # batch: join j's region of pair_cap pairs is followed by a gap of canaries
+    keys_r = [wl.R.key(i) for i in range(200)]
+    keys_s = [wl.S.key(i) for i in range(2000)]
+    Rb = ag.DeviceRelation.from_host(*_pack(keys_r + keys_r))
+    Sb = ag.DeviceRelation.from_host(*_pack(keys_s + keys_s))
+    caps = [5, 3]
+    descs = ag.make_descs([(0, 200, 0, 2000), (200, 400, 2000, 4000)], caps)
+    gap = 32
+    descs[1].pair_offset = caps[0] + gap
+    total = caps[0] + gap + caps[1] + gap
+    pairs = torch.full((2 * total,), CANARY, dtype=torch.int32, device="cuda")
+    counts = torch.zeros(2, dtype=torch.int64, device="cuda")
+    bws = ag.alloc_ws(ag.join_batch_ws_bytes(descs, Rb.n, Sb.n, 0.5))
+    b = ag.join_batch_prepare(descs, Rb, Sb, bws, 0.5)
+    ag.join_batch_run(b, Rb, Sb, pairs, counts)
+    torch.cuda.synchronize()
+    assert counts.tolist()[0] > caps[0] and counts.tolist()[1] > caps[1]
+    p = pairs.view(-1, 2)
+    assert bool((p[caps[0]: caps[0] + gap] == CANARY).all())
+    assert bool((p[caps[0] + gap + caps[1]:] == CANARY).all())
+
+
+def _pack(keys):
+    rel = workloads.relation_from_keys(keys)
+    return rel.arena, rel.off, rel.ids

@@ -130,3 +130,72 @@ def test_server_overlaps_batches_on_slots():
     # with two slots, some request launched while another batch was still running
     spans = sorted((r.launched, r.done) for r in reqs)
     assert any(a2 < d1 and a2 > a1 for (a1, d1), (a2, _) in itertools.combinations(spans, 2))
+
+
+def test_cancel_before_launch_releases_memory_and_launched_requests_complete():
+    """Host-side cancellation: requests cancelled while waiting or admitted
+    are dropped and their admitted bytes released; a cancel that arrives after
+    the request's batch was launched does not stop it."""
+    sizes = [40] * 6
+    arrivals = [(0.0, j) for j in range(6)]
+    ex = FakeExecutor(1, sizes, polls_to_finish=200)
+    srv = serve.Server(ex, budget_bytes=100, max_batch=2, clock=FakeClock(), idle_sleep=0)
+    ex.server = srv
+    # request 0/1 launch at once (2 x 40 <= 100); 2..5 wait on the budget or the one slot
+    reqs = srv.run(arrivals, timeout=1e6, cancels=[(0.001, 3), (0.001, 4), (0.001, 0)])
+    st = {r.rid: r.status for r in reqs}
+    assert st[3] == st[4] == "cancelled"
+    assert st[0] == "done" and st[1] == "done" and st[2] == "done" and st[5] == "done"
+    assert all(r.count == 10 * r.pool_index for r in reqs if r.status == "done")
+    launched = [p for b in ex.launched for p in b]
+    assert 3 not in launched and 4 not in launched
+    assert srv.ledger.used == 0
+    s = serve.summarize(reqs)
+    assert s["cancelled"] == 2 and s["completed"] == 4
+
+
+def test_admission_timeout_drops_requests_that_wait_too_long():
+    """A request that cannot be admitted within admit_timeout (the budget is
+    held by a long batch) is dropped with status timeout; the one behind it in
+    arrival order (admission is first come, first served) is admitted once
+    the queue head is gone, and completes."""
+    sizes = [90, 90, 5]
+    arrivals = [(0.0, 0), (0.0, 1), (0.005, 2)]
+    ex = FakeExecutor(2, sizes, polls_to_finish=400)
+    srv = serve.Server(ex, budget_bytes=100, max_batch=1, clock=FakeClock(), idle_sleep=0, admit_timeout=0.01)
+    reqs = srv.run(arrivals, timeout=1e6)
+    st = {r.rid: r.status for r in reqs}
+    assert st[0] == "done" and st[1] == "timeout" and st[2] == "done"
+    assert srv.ledger.used == 0
+    assert serve.summarize(reqs)["timed_out"] == 1
+
+
+def test_injected_admission_failures_delay_but_do_not_lose_requests():
+    """Allocation failures injected into the ledger (the next k admissions
+    refused) leave the requests waiting; every one is admitted later, within
+    the budget, and completes with its result."""
+    sizes = [10 + j for j in range(10)]
+    arrivals = [(1e-5 * j, j) for j in range(10)]
+    ex = FakeExecutor(2, sizes)
+    srv = serve.Server(ex, budget_bytes=60, max_batch=4, clock=FakeClock(), idle_sleep=0)
+    srv.ledger.refuse_next(25)
+    reqs = srv.run(arrivals, timeout=1e6)
+    assert srv.ledger.refused == 25
+    assert all(r.status == "done" and r.count == 10 * r.pool_index for r in reqs)
+    assert srv.ledger.peak <= 60 and srv.ledger.used == 0
+
+
+def test_tune_cache_keys_and_persistence(tmp_path):
+    """The autotuner's cache: batches are keyed by device, key-length class
+    and size class (floor log2 of the rows), and the table survives a reload
+    from its JSON file."""
+    from paper_2411_18183_gb300.tune import TuneCache
+    k = TuneCache.key
+    assert k("GPU", 100, 1000) == k("GPU", 128, 1023) != k("GPU", 129, 1000)
+    assert k("GPU", 100, 1000) != k("GPU", 100, 1024) and k("GPU", 100, 1024) == k("GPU", 100, 2047)
+    assert k("GPU", 9000, 5) != k("GPU", 8192, 5) and k("A", 1, 1) != k("B", 1, 1)
+    path = str(tmp_path / "tune.json")
+    c = TuneCache(path)
+    assert c.get(k("GPU", 700, 10_000)) is None
+    c.put(k("GPU", 700, 10_000), 0.35)
+    assert TuneCache(path).get(k("GPU", 700, 10_000)) == 0.35
