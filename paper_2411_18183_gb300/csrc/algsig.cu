@@ -28,7 +28,7 @@ namespace algsig {
 __device__ uint16_t g_log[65536];
 __device__ uint16_t g_alog[65536];
 // constant-multiply tables of the tile combination (rounds.cuh), set up once per device
-__device__ uint16_t g_const[21 * 512];
+__device__ uint16_t g_const[17 * 512];
 }  // namespace algsig
 
 #include "rounds.cuh"
@@ -49,7 +49,7 @@ constexpr int kMaxDevices = 64;
 constexpr size_t kSmemTables = (size_t)kRedBytes + 512 * 4;
 constexpr size_t kSmemBufs = (size_t)kWarpsPerBlock * 2 * kBufBytes;
 constexpr size_t kSmemSig = kSmemTables + kConstBytes + kSmemBufs;
-static_assert(kConstEntries == 21 * 512, "constant table size");
+static_assert(kConstEntries == 17 * 512, "constant table size");
 
 // ----------------------------------------------------------------------------
 // Batches of joins
@@ -228,7 +228,7 @@ __device__ __forceinline__ void sig_walk(const uint8_t* __restrict__ arena, cons
 // g_walk_timeouts and the warp leaves.
 // ----------------------------------------------------------------------------
 
-constexpr int kWSPairs = 7;
+constexpr int kWSPairs = 8;
 constexpr int kWSThreads = 64 * kWSPairs;
 constexpr uint32_t kWaitTries = 1u << 22;
 __device__ unsigned long long g_walk_timeouts;
@@ -245,8 +245,12 @@ struct PairShared {
   uint64_t val[2][32];
   uint64_t bar[4];   // ready[0..1] (control -> math), done[0..1] (math -> control)
 };
-constexpr size_t kSmemWS = kSmemTables + kConstBytes + (size_t)kWSPairs * 2 * kBufBytes +
+// tables | constants | staging buffers | pair hand-over state (the tables' init
+// scratch lives in the first staging buffer, unused until the walk starts)
+constexpr size_t kSmemWSTables = (size_t)kRedBytes;
+constexpr size_t kSmemWS = kSmemWSTables + kConstBytes + (size_t)kWSPairs * 2 * kBufBytes +
                            (size_t)kWSPairs * sizeof(PairShared);
+static_assert(kSmemWS <= 232448, "warp-specialised signature walk: shared memory");
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 __device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
@@ -407,19 +411,19 @@ __global__ void __launch_bounds__(kWSThreads, 1) sig_kernel_ws(const uint8_t* __
                                                                uint64_t* __restrict__ sig_out) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* red = reinterpret_cast<uint32_t*>(smem);
-  uint16_t* ctab = reinterpret_cast<uint16_t*>(smem + kSmemTables);
+  uint16_t* ctab = reinterpret_cast<uint16_t*>(smem + kSmemWSTables);
+  uint8_t* buf0 = smem + kSmemWSTables + kConstBytes;
   for (int i = threadIdx.x; i < kConstEntries / 2; i += blockDim.x)
     reinterpret_cast<uint32_t*>(ctab)[i] = reinterpret_cast<const uint32_t*>(g_const)[i];
-  PairShared* pshared = reinterpret_cast<PairShared*>(smem + kSmemTables + kConstBytes +
-                                                      (size_t)kWSPairs * 2 * kBufBytes);
+  PairShared* pshared = reinterpret_cast<PairShared*>(buf0 + (size_t)kWSPairs * 2 * kBufBytes);
   if (threadIdx.x < kWSPairs * 4) mbar_init(&pshared[threadIdx.x / 4].bar[threadIdx.x % 4], 1);
-  init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
+  init_red_tables(red, reinterpret_cast<uint32_t*>(buf0));   // scratch in a staging buffer; ends with __syncthreads()
   using Cursor = typename std::conditional<AT400, RedCursorAt400, RedCursor>::type;
   Cursor rc;
   if constexpr (AT400) rc = red_cursor_at400(); else rc = red_cursor(red);
   const int w = threadIdx.x >> 5;
   const int pair = w % kWSPairs;
-  uint8_t* bufs = smem + kSmemTables + kConstBytes + (size_t)pair * 2 * kBufBytes;
+  uint8_t* bufs = buf0 + (size_t)pair * 2 * kBufBytes;
   PairShared& ps = pshared[pair];
   if (w < kWSPairs) {
     ws_math<NCOMP>(ps, bufs, rc);
@@ -1128,8 +1132,8 @@ static as_status ensure_device(DeviceState** out) {
     };
     for (int t = 0; t < kConstCount; t++) {
       uint64_t ex;
-      if (t < 20) {
-        const int k = t / 5 + 1, sh = t % 5;
+      if (t < 4 * kScanLevels) {
+        const int k = t / kScanLevels + 1, sh = t % kScanLevels;
         ex = ((uint64_t)k * (kTile / 2) << sh) % kOrder;
       } else {
         ex = kOrder - 32;

@@ -342,7 +342,8 @@ __device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t spa
 // log/antilog tables in global memory and is finished one round later, so the
 // lookups overlap the next round's arithmetic.
 
-constexpr int kConstCount = 21;                       // 20 scan constants + x^-32
+constexpr int kConstCount = 17;                       // 16 scan constants (s = 0..3) + x^-32
+constexpr int kScanLevels = 4;                         // c_k^(2^s) tables kept for s < kScanLevels
 constexpr int kConstEntries = kConstCount * 512;
 constexpr int kConstBytes = kConstEntries * 2;
 
@@ -356,8 +357,14 @@ __device__ __forceinline__ uint64_t mul_scan(const uint16_t* ctab, uint64_t v, i
   uint64_t r = 0;
 #pragma unroll
   for (int k = 0; k < 4; k++) {
-    const uint16_t* t = ctab + (size_t)(k * 5 + s) * 512;
-    r |= (uint64_t)mulc(t, (uint32_t)(v >> (16 * k)) & 0xFFFFu) << (16 * k);
+    uint32_t c = (uint32_t)(v >> (16 * k)) & 0xFFFFu;
+    if (s < kScanLevels) {
+      c = mulc(ctab + (size_t)(k * kScanLevels + s) * 512, c);
+    } else {                                           // c_k^16 = (c_k^8)^2
+      const uint16_t* t = ctab + (size_t)(k * kScanLevels + kScanLevels - 1) * 512;
+      c = mulc(t, mulc(t, c));
+    }
+    r |= (uint64_t)c << (16 * k);
   }
   return r;
 }
@@ -365,7 +372,7 @@ __device__ __forceinline__ uint64_t mul_scan(const uint16_t* ctab, uint64_t v, i
 // x^-(k lo/2) * P, component-wise
 template <class Cursor>
 __device__ __forceinline__ uint64_t lo_correct(const uint16_t* ctab, uint64_t P, uint32_t lo, const Cursor& rc) {
-  const uint16_t* inv32 = ctab + 20 * 512;
+  const uint16_t* inv32 = ctab + (size_t)(4 * kScanLevels) * 512;
   uint64_t out = 0;
 #pragma unroll
   for (int k = 1; k <= 4; k++) {
