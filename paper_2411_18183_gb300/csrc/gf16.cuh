@@ -80,11 +80,14 @@ struct RedCursor {
   uint32_t tab;       // shared byte address of the tables
   uint32_t off16;     // 4*lane
   uint32_t off24;     // 4*lane + 128
+  uint32_t k16, nk16, k256;
   __device__ __forceinline__ uint32_t load(uint32_t idx) const { return lds32(tab + idx); }
 };
+__device__ uint32_t g_k16 = 0x10000u;   // 2^16, read at run time so the compiler keeps multiplies by it
 struct RedCursorAt400 {
   uint32_t off16;
   uint32_t off24;
+  uint32_t k16, nk16, k256;
   __device__ __forceinline__ uint32_t load(uint32_t idx) const {
     uint32_t v;
     asm volatile("ld.shared.u32 %0, [%1+1024];" : "=r"(v) : "r"(idx));
@@ -98,12 +101,14 @@ __device__ __forceinline__ RedCursor red_cursor(const uint32_t* red) {
   c.tab = (uint32_t)__cvta_generic_to_shared(red);
   c.off16 = 4u * (threadIdx.x & 31u);
   c.off24 = c.off16 + 128u;
+  c.k16 = *(volatile uint32_t*)&g_k16; c.nk16 = 0u - c.k16; c.k256 = c.k16 >> 8;
   return c;
 }
 __device__ __forceinline__ RedCursorAt400 red_cursor_at400() {
   RedCursorAt400 c;
   c.off16 = 4u * (threadIdx.x & 31u);
   c.off24 = c.off16 + 128u;
+  c.k16 = *(volatile uint32_t*)&g_k16; c.nk16 = 0u - c.k16; c.k256 = c.k16 >> 8;
   return c;
 }
 
@@ -134,10 +139,11 @@ template <int NCOMP = 4, class Cursor>
 __device__ __forceinline__ void horner_chunk(uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
                                              uint32_t& a1, uint32_t& a2, uint32_t& a3, uint32_t& a4,
                                              const Cursor& rc) {
-  const uint32_t l0 = v0 & 0xFFFFu, h0 = v0 >> 16;
-  const uint32_t l1 = v1 & 0xFFFFu, h1 = v1 >> 16;
-  const uint32_t l2 = v2 & 0xFFFFu, h2 = v2 >> 16;
-  const uint32_t l3 = v3 & 0xFFFFu, h3 = v3 >> 16;
+  // halves on the FMA pipe: h = hi32(v * 2^16), l = v - h * 2^16
+  const uint32_t h0 = __umulhi(v0, rc.k16), l0 = h0 * rc.nk16 + v0;
+  const uint32_t h1 = __umulhi(v1, rc.k16), l1 = h1 * rc.nk16 + v1;
+  const uint32_t h2 = __umulhi(v2, rc.k16), l2 = h2 * rc.nk16 + v2;
+  const uint32_t h3 = __umulhi(v3, rc.k16), l3 = h3 * rc.nk16 + v3;
   uint32_t u;
   // k = 1: 8 symbols, growth 8 bits
   u = (a1 << 8) ^ l0 ^ (h0 << 1) ^ (l1 << 2) ^ (h1 << 3) ^ (l2 << 4) ^ (h2 << 5) ^ (l3 << 6) ^ (h3 << 7);

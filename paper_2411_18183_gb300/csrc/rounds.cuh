@@ -247,14 +247,28 @@ __device__ __forceinline__ Plan plan_round(const PlanLoad& L, uint64_t kc, uint6
   return p;
 }
 
-// copy the round's span into `buf` (padded layout), one commit group per call
+// copy the round's span into `buf` (padded layout), one commit group per call.
+// Lane l copies the span's chunks l + 32 j; with kTileChunks dividing 32 their
+// padded places are kCopyStride bytes apart, so the copies of a lane take
+// fixed offsets from two base addresses (a fall-through switch on the count).
+static_assert(32 % kTileChunks == 0, "tiles must divide a warp's 32 chunks");
+constexpr uint32_t kCopyStride = 16u * (32u + 32u / kTileChunks);
+static_assert(kSpanChunks <= 17 * 32, "span copies: at most 17 per lane");
 __device__ __forceinline__ void issue_span(uint8_t* buf, const uint8_t* __restrict__ arena, const Plan& p) {
   if (p.valid) {
-    const int lane = threadIdx.x & 31;
+    const uint32_t lane = threadIdx.x & 31u;
     const uint32_t nchunks = (uint32_t)((p.span_hi - p.span_lo) >> 4);
-    const uint8_t* src = arena + p.span_lo;
-    for (uint32_t i = (uint32_t)lane; i < nchunks; i += 32)
-      cp_async16(buf + 16 * (i + i / (uint32_t)kTileChunks), src + 16 * i);
+    const uint32_t cnt = nchunks > lane ? (nchunks - lane + 31u) >> 5 : 0u;
+    uint8_t* d = buf + 16u * (lane + lane / (uint32_t)kTileChunks);
+    const uint8_t* g = arena + p.span_lo + 16u * lane;
+#define ALGSIG_COPY(j) case (j) + 1: cp_async16(d + kCopyStride * (j), g + 512u * (j));
+    switch (cnt) {
+      ALGSIG_COPY(16) ALGSIG_COPY(15) ALGSIG_COPY(14) ALGSIG_COPY(13) ALGSIG_COPY(12) ALGSIG_COPY(11)
+      ALGSIG_COPY(10) ALGSIG_COPY(9) ALGSIG_COPY(8) ALGSIG_COPY(7) ALGSIG_COPY(6) ALGSIG_COPY(5)
+      ALGSIG_COPY(4) ALGSIG_COPY(3) ALGSIG_COPY(2) ALGSIG_COPY(1) ALGSIG_COPY(0)
+      default: break;
+    }
+#undef ALGSIG_COPY
   }
   cp_async_commit();
 }
