@@ -222,7 +222,7 @@ def summarize(reqs, wall: float | None = None) -> dict:
     lat = np.array([r.latency for r in served if r.latency is not None])
     done = served
     span = wall if wall is not None else (max(r.done for r in done) - min(r.arrival for r in reqs)) if done else 0.0
-    return {
+    out = {
         "requests": len(reqs),
         "completed": len(done),
         "cancelled": sum(1 for r in reqs if r.status == "cancelled"),
@@ -234,6 +234,20 @@ def summarize(reqs, wall: float | None = None) -> dict:
         "span_s": span,
         "requests_per_s": len(done) / span if span > 0 else None,
     }
+    if served:
+        # where the slowest request spent its time, and the longest pause between launches
+        w = max(served, key=lambda r: r.latency)
+        out["slowest"] = {"at_s": w.arrival, "latency_ms": w.latency * 1e3,
+                          "admission_wait_ms": (w.admitted - w.arrival) * 1e3,
+                          "launch_wait_ms": (w.launched - w.admitted) * 1e3,
+                          "run_ms": (w.done - w.launched) * 1e3}
+        ls = sorted(r.launched for r in served)
+        if len(ls) > 1:
+            g = np.diff(ls)
+            i = int(np.argmax(g))
+            out["longest_launch_gap_ms"] = float(g[i] * 1e3)
+            out["longest_launch_gap_at_s"] = float(ls[i])
+    return out
 
 
 class GpuExecutor:
