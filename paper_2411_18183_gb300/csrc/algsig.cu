@@ -32,6 +32,7 @@ __device__ uint16_t g_const[17 * 512];
 }  // namespace algsig
 
 #include "rounds.cuh"
+static_assert(algsig::kConstEntries == 17 * 512, "g_const holds the combination tables");
 #include "baseline.cuh"
 
 namespace algsig {
@@ -1124,7 +1125,7 @@ static as_status ensure_device(DeviceState** out) {
     h_log[0] = 0;
     if ((e = cudaMemcpyToSymbol(g_log, h_log, sizeof(h_log))) != cudaSuccess) return cuda_fail(e, "table setup");
     if ((e = cudaMemcpyToSymbol(g_alog, h_alog, sizeof(h_alog))) != cudaSuccess) return cuda_fail(e, "table setup");
-    // constant-multiply tables: c_k^(2^s) = x^(k kTile/2 2^s) at (k-1)*5+s, then x^-32
+    // constant-multiply tables: c_k^(2^s) = x^(k kTile/2 2^s) at (k-1)*kScanLevels+s, then x^-32
     static uint16_t h_const[kConstEntries];
     auto mul = [&](uint32_t a, uint32_t b) -> uint32_t {
       if (a == 0 || b == 0) return 0;

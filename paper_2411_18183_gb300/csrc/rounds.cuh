@@ -347,7 +347,8 @@ __device__ __forceinline__ void tile_accumulate(const uint8_t* buf, uint64_t spa
 // computed as a reverse segmented scan over the lanes of the key (log2(32)
 // doubling steps, step s multiplying by c_k^(2^s)).  A multiplication by a
 // constant C is two lookups in a 512-entry table (low byte, high byte) held in
-// shared memory: tables for c_k^(2^s) (k = 1..4, s = 0..4) and for x^-32.
+// shared memory: tables for c_k^(2^s) (k = 1..4, s = 0..3; s = 4 applies the
+// s = 3 table twice) and for x^-32.
 //
 // A key whose tile 0 lies in the round gets its signature from B directly; the
 // shift of its first symbol to slot lo/2 of the chunk grid is undone once per
