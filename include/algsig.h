@@ -333,7 +333,12 @@ typedef struct as_batch {
     uint64_t n_joins;
     uint64_t slots_total;
     uint64_t mR, nS;
+    /* First row of the batch's R (S) rows when the joins' row ranges, taken in
+     * join order, form one ascending contiguous range (the signatures then run
+     * as those of a single relation); AS_ROWS_SCATTERED otherwise. */
+    uint64_t r_first, s_first;
 } as_batch;
+#define AS_ROWS_SCATTERED (~(uint64_t)0)
 
 /* Workspace of a batch (0 for invalid descriptors or load factor). */
 size_t as_join_batch_ws_bytes(const as_join_desc* descs, int n_joins, uint64_t mR, uint64_t nS, float load_factor);
@@ -346,8 +351,11 @@ as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t
 
 /* Run a prepared batch: clear the tables and counters, signatures of all R
  * keys, build of every join's table, signatures of all S keys, probe and
- * verification of every S key against its join's table.  Asynchronous; a
- * join's count may exceed its pair_cap (the excess pairs are not written). */
+ * verification of every S key against its join's table.  The signatures of a
+ * side whose rows form one run (r_first / s_first set) come from the
+ * single-relation kernel of as_sig_compute over that run; scattered rows take
+ * the batch walk over the joins' row ranges.  Asynchronous; a join's count may
+ * exceed its pair_cap (the excess pairs are not written). */
 as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR,
                             const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint32_t* d_pairs,
                             uint64_t* d_counts, as_stream stream);

@@ -269,6 +269,7 @@ def join_probe_sigs(t: Table, S: DeviceRelation, sigS: torch.Tensor, pairs: torc
 
 JOIN_MODES = {"inner": 0, "semi": 1, "anti": 2, "outer_s": 3, "sig_only": 4}    # AS_JOIN_*
 NO_ROW = 0xFFFFFFFF                                                  # AS_NO_ROW
+ROWS_SCATTERED = 0xFFFFFFFFFFFFFFFF                                  # AS_ROWS_SCATTERED
 
 
 def join_probe_mode(t: Table, S: DeviceRelation, sigS: torch.Tensor, pairs: torch.Tensor, count: torch.Tensor,
@@ -382,7 +383,8 @@ class Batch(ctypes.Structure):
     """as_batch: a prepared batch (device descriptors and workspace regions)."""
     _fields_ = [("descs", ctypes.c_void_p), ("slots", ctypes.c_void_p), ("sigR", ctypes.c_void_p),
                 ("sigS", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("n_joins", ctypes.c_uint64),
-                ("slots_total", ctypes.c_uint64), ("mR", ctypes.c_uint64), ("nS", ctypes.c_uint64)]
+                ("slots_total", ctypes.c_uint64), ("mR", ctypes.c_uint64), ("nS", ctypes.c_uint64),
+                ("r_first", ctypes.c_uint64), ("s_first", ctypes.c_uint64)]
 
 
 def _batch_lib():

@@ -1780,6 +1780,22 @@ as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t
   out->slots_total = tot;
   out->mR = vr;
   out->nS = vs;
+  // do the joins' rows, in join order, form one ascending run of the relation?
+  auto first_of_run = [&](bool s_side) -> uint64_t {
+    uint64_t first = 0, next = 0;
+    bool any = false;
+    for (int j = 0; j < n_joins; j++) {
+      const uint64_t b = s_side ? descs[j].s_begin : descs[j].r_begin;
+      const uint64_t e = s_side ? descs[j].s_end : descs[j].r_end;
+      if (e == b) continue;
+      if (!any) { first = b; any = true; }
+      else if (b != next) return AS_ROWS_SCATTERED;
+      next = e;
+    }
+    return first;
+  };
+  out->r_first = first_of_run(false);
+  out->s_first = first_of_run(true);
   return AS_OK;
 }
 
@@ -1806,14 +1822,22 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
   if ((e = cudaMemsetAsync(d_counts, 0, 8 * b->n_joins, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
   batch_bytes_kernel<<<1, 1024, 0, s>>>(J, nj, d_offR, d_offS);
   if (b->mR > 0) {
-    launch_sig_kernel<false>(d, walk_blocks(b->mR, d->sms), s, d_arenaR, d_offR, b->mR, b->sigR, J, nj);
+    if (b->r_first != AS_ROWS_SCATTERED) {             // one run of rows: the single-relation kernel
+      if ((st = launch_sig(d_arenaR, d_offR + b->r_first, b->mR, b->sigR, s)) != AS_OK) return st;
+    } else {
+      launch_sig_kernel<false>(d, walk_blocks(b->mR, d->sms), s, d_arenaR, d_offR, b->mR, b->sigR, J, nj);
+    }
     uint64_t blocks = (b->mR + 255) / 256;
     const uint64_t lim = (uint64_t)d->sms * 16;
     if (blocks > lim) blocks = lim;
     build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, 0, b->sigR, d_offR, b->mR, b->flags, J, nj);
   }
   if (b->nS > 0) {
-    launch_sig_kernel<true>(d, walk_blocks(b->nS, d->sms), s, d_arenaS, d_offS, b->nS, b->sigS, J, nj);
+    if (b->s_first != AS_ROWS_SCATTERED) {
+      if ((st = launch_sig(d_arenaS, d_offS + b->s_first, b->nS, b->sigS, s)) != AS_OK) return st;
+    } else {
+      launch_sig_kernel<true>(d, walk_blocks(b->nS, d->sms), s, d_arenaS, d_offS, b->nS, b->sigS, J, nj);
+    }
     VerifyParams P;
     P.slots = slots;
     P.mask = 0;
