@@ -1088,6 +1088,7 @@ struct DeviceState {
   bool ready = false;
   int sms = 0;
   int verify_blocks_per_sm = 1;
+  int prefix_blocks_per_sm = 1;
   bool tables_at400 = false;   // dynamic shared memory starts at shared address 0x400
 };
 
@@ -1146,6 +1147,18 @@ static as_status ensure_device(DeviceState** out) {
       }
     }
     if ((e = cudaMemcpyToSymbol(g_const, h_const, sizeof(h_const))) != cudaSuccess) return cuda_fail(e, "table setup");
+    // prefix-scan tables: x^(-8 k 2^s) at (k-1)*kPLevels+s
+    static uint16_t h_pconst[kPConst * 512];
+    for (int t = 0; t < kPConst; t++) {
+      const int k = t / kPLevels + 1, sh = t % kPLevels;
+      const uint64_t up = ((uint64_t)8 * k << sh) % kOrder;
+      const uint32_t C = h_alog[(kOrder - up) % kOrder];
+      for (uint32_t b = 0; b < 256; b++) {
+        h_pconst[t * 512 + b] = (uint16_t)mul(b, C);
+        h_pconst[t * 512 + 256 + b] = (uint16_t)mul(mul(b, h_alog[8]), C);
+      }
+    }
+    if ((e = cudaMemcpyToSymbol(g_pconst, h_pconst, sizeof(h_pconst))) != cudaSuccess) return cuda_fail(e, "table setup");
     if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return cuda_fail(e, "device query");
     {
@@ -1179,6 +1192,10 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaFuncSetAttribute(prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPrefix)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.prefix_blocks_per_sm, prefix_kernel, kPThreads,
+                                                           kSmemPrefix)) != cudaSuccess)
+      return cuda_fail(e, "occupancy query");
+    if (d.prefix_blocks_per_sm < 1) d.prefix_blocks_per_sm = 1;
     if ((e = cudaFuncSetAttribute(sig8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig8)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
@@ -1356,7 +1373,8 @@ as_status as_sig_prefixes(const uint8_t* d_arena, const uint64_t* d_off, uint64_
   if (st != AS_OK) return st;
   if (n == 0) return AS_OK;
   const uint64_t want = (n + kPThreads / 32 - 1) / (kPThreads / 32);
-  const unsigned blocks = (unsigned)(want < (uint64_t)d->sms * 8 ? want : (uint64_t)d->sms * 8);
+  const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->prefix_blocks_per_sm;   // persistent: one wave
+  const unsigned blocks = (unsigned)(want < lim ? want : lim);
   prefix_kernel<<<blocks, kPThreads, kSmemPrefix, (cudaStream_t)stream>>>(d_arena, d_off, n, block_bytes, d_pref_off,
                                                                           d_out);
   cudaError_t e = cudaGetLastError();

@@ -15,16 +15,34 @@
 // key, 512 key bytes per step, lane l taking the key's 16-byte chunk c = 32 s + l
 // (realigned to the key's first byte from two aligned chunks, the word part of
 // the realignment warp-uniform).  The chunk's value T_c = sum_j q_j x^(k j) is a
-// Horner step from zero (gf16.cuh); its term of the prefix sums is
-// x^(8 k c) T_c, formed through the log / antilog tables; an inclusive XOR scan
-// over the lanes plus the running total of the earlier steps gives C at every
-// chunk end, and the lanes whose chunk ends a block (or the key) store it.
+// Horner step from zero (gf16.cuh).  With C(c) = sum_{c' <= c} x^(8 k c') T_c'
+// the prefix through chunk c, the warp carries D(c) = x^(-8 k c) C(c), which
+// obeys D(c) = x^(-8 k) D(c-1) + T_c: an inclusive scan over the lanes whose
+// level s multiplies by the constant x^(-8 k 2^s) (tables in shared memory),
+// with the previous step's last D entering at lane 0.  Only the lanes whose
+// chunk ends a block (or the key) form C = x^(8 k c) D through the log /
+// antilog tables and store it.
 #pragma once
 #include <cstdint>
 
 namespace algsig {
 
 constexpr int kPThreads = 256;          // threads per block of the prefix kernels
+constexpr int kPLevels = 5;             // scan levels over 32 lanes
+constexpr int kPConst = 4 * kPLevels;   // tables x^(-8 k 2^s), k = 1..4, s = 0..4, at (k-1)*kPLevels+s
+// multiply-by-constant tables of the prefix scan (layout of rounds.cuh's), set up once per device
+__device__ uint16_t g_pconst[kPConst * 512];
+
+// component-wise multiply of a packed value by x^(-8 k 2^s)
+__device__ __forceinline__ uint64_t mul_pscan(const uint16_t* ptab, uint64_t v, int s) {
+  uint64_t r = 0;
+#pragma unroll
+  for (int k = 0; k < 4; k++) {
+    const uint32_t c = mulc(ptab + (size_t)(k * kPLevels + s) * 512, (uint32_t)(v >> (16 * k)) & 0xFFFFu);
+    r |= (uint64_t)c << (16 * k);
+  }
+  return r;
+}
 constexpr int kPItems = 4;              // keys per thread in the count / offset kernels
 constexpr int kPKeysPerBlock = kPThreads * kPItems;
 
@@ -138,70 +156,83 @@ struct BlockPos {
   }
 };
 
+// One warp step of a key: lane l's chunk c = c0 + l of the key (realigned to
+// the key's first byte from the two aligned chunks ra, rb loaded for it), the
+// scan of D over the lanes and the stores of the entries that end in this
+// step.  carry: D of the chunk before the step (updated); bp, e1: the lane's
+// block position and 8 c mod 65535 (advanced).
 template <class Cursor>
-__device__ __forceinline__ void prefix_key(const uint8_t* __restrict__ arena, uint64_t s0, uint64_t len,
-                                           BlockPos& bp, uint64_t* __restrict__ o,
-                                           const uint4* __restrict__ emask, const Cursor& rc) {
+__device__ __forceinline__ void prefix_step(const uint4& ra, const uint4& rb, uint32_t a, uint64_t len, uint64_t c0,
+                                            BlockPos& bp, uint32_t& e1, uint64_t& carry,
+                                            uint64_t* __restrict__ o, const uint4* __restrict__ emask,
+                                            const Cursor& rc, const uint16_t* ptab) {
   const uint32_t lane = threadIdx.x & 31u;
-  if (len == 0) {
-    if (lane == 0) o[0] = 0;
-    return;
-  }
-  const uint8_t* p = arena + s0;
-  const uint32_t a = (uint32_t)reinterpret_cast<uintptr_t>(p) & 15u;
-  const uint8_t* base = p - a;                       // aligned; key bytes are [a, a + len) from here
-  const uint32_t sh = 8u * (a & 3u);
   const uint64_t nchunks = (len + 15) / 16;
-  uint64_t carry = 0;
-  bp.start();
-  uint32_t e1 = 8u * lane;                           // 8 c mod 65535 for c = c0 + lane
-  for (uint64_t c0 = 0; c0 < nchunks; c0 += 32) {
-    const uint64_t c = c0 + lane;
-    uint64_t W = 0;
-    if (c < nchunks) {
-      const uint64_t o16 = 16 * c;                   // aligned offset of the chunk's first aligned chunk
-      const uint4 ra = ld16(base + o16);
-      const uint4 rb = o16 + 16 < a + len ? ld16(base + o16 + 16) : make_uint4(0, 0, 0, 0);
-      uint32_t v0, v1, v2, v3;
-      switch (a >> 2) {                              // warp-uniform
-        case 0:
-          v0 = __funnelshift_r(ra.x, ra.y, sh); v1 = __funnelshift_r(ra.y, ra.z, sh);
-          v2 = __funnelshift_r(ra.z, ra.w, sh); v3 = __funnelshift_r(ra.w, rb.x, sh);
-          break;
-        case 1:
-          v0 = __funnelshift_r(ra.y, ra.z, sh); v1 = __funnelshift_r(ra.z, ra.w, sh);
-          v2 = __funnelshift_r(ra.w, rb.x, sh); v3 = __funnelshift_r(rb.x, rb.y, sh);
-          break;
-        case 2:
-          v0 = __funnelshift_r(ra.z, ra.w, sh); v1 = __funnelshift_r(ra.w, rb.x, sh);
-          v2 = __funnelshift_r(rb.x, rb.y, sh); v3 = __funnelshift_r(rb.y, rb.z, sh);
-          break;
-        default:
-          v0 = __funnelshift_r(ra.w, rb.x, sh); v1 = __funnelshift_r(rb.x, rb.y, sh);
-          v2 = __funnelshift_r(rb.y, rb.z, sh); v3 = __funnelshift_r(rb.z, rb.w, sh);
-          break;
-      }
-      const uint64_t rest = len - o16;               // key bytes from this chunk on
-      const uint4 m = emask[rest < 16 ? rest : 16];
-      v0 &= m.x; v1 &= m.y; v2 &= m.z; v3 &= m.w;
-      uint32_t t1 = 0, t2 = 0, t3 = 0, t4 = 0;
-      horner_chunk(v0, v1, v2, v3, t1, t2, t3, t4, rc);
-      W = shift_chunk_value(t1, t2, t3, t4, e1);
+  const uint64_t c = c0 + lane;
+  const uint32_t sh = 8u * (a & 3u);
+  uint64_t W = 0;
+  if (c < nchunks) {
+    uint32_t v0, v1, v2, v3;
+    switch (a >> 2) {                              // warp-uniform
+      case 0:
+        v0 = __funnelshift_r(ra.x, ra.y, sh); v1 = __funnelshift_r(ra.y, ra.z, sh);
+        v2 = __funnelshift_r(ra.z, ra.w, sh); v3 = __funnelshift_r(ra.w, rb.x, sh);
+        break;
+      case 1:
+        v0 = __funnelshift_r(ra.y, ra.z, sh); v1 = __funnelshift_r(ra.z, ra.w, sh);
+        v2 = __funnelshift_r(ra.w, rb.x, sh); v3 = __funnelshift_r(rb.x, rb.y, sh);
+        break;
+      case 2:
+        v0 = __funnelshift_r(ra.z, ra.w, sh); v1 = __funnelshift_r(ra.w, rb.x, sh);
+        v2 = __funnelshift_r(rb.x, rb.y, sh); v3 = __funnelshift_r(rb.y, rb.z, sh);
+        break;
+      default:
+        v0 = __funnelshift_r(ra.w, rb.x, sh); v1 = __funnelshift_r(rb.x, rb.y, sh);
+        v2 = __funnelshift_r(rb.y, rb.z, sh); v3 = __funnelshift_r(rb.z, rb.w, sh);
+        break;
     }
+    const uint64_t rest = len - 16 * c;           // key bytes from this chunk on
+    const uint4 m = emask[rest < 16 ? rest : 16];
+    v0 &= m.x; v1 &= m.y; v2 &= m.z; v3 &= m.w;
+    uint32_t t1 = 0, t2 = 0, t3 = 0, t4 = 0;
+    horner_chunk(v0, v1, v2, v3, t1, t2, t3, t4, rc);
+    W = (uint64_t)t1 | ((uint64_t)t2 << 16) | ((uint64_t)t3 << 32) | ((uint64_t)t4 << 48);
+  }
+  const uint64_t cin = mul_pscan(ptab, carry, 0);   // x^(-8k) D(c0 - 1), enters at lane 0
+  if (lane == 0) W ^= cin;
 #pragma unroll
-    for (int d = 1; d < 32; d <<= 1) {
-      const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, W, d);
-      if (lane >= (uint32_t)d) W ^= t;
-    }
-    const uint64_t P = carry ^ W;
-    if (c < nchunks && (bp.r + 1 == bp.cpb || c + 1 == nchunks)) o[bp.q] = P;
-    carry = __shfl_sync(0xFFFFFFFFu, P, 31);
-    bp.advance();
-    e1 += 256u;
-    if (e1 >= kOrder) e1 -= kOrder;
+  for (int s = 0; s < kPLevels; s++) {
+    const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, W, 1u << s);
+    if (lane >= (1u << s)) W ^= mul_pscan(ptab, t, s);
+  }
+  if (c < nchunks && (bp.r + 1 == bp.cpb || c + 1 == nchunks))
+    o[bp.q] = shift_chunk_value((uint32_t)W & 0xFFFFu, (uint32_t)(W >> 16) & 0xFFFFu, (uint32_t)(W >> 32) & 0xFFFFu,
+                                (uint32_t)(W >> 48), e1);
+  carry = __shfl_sync(0xFFFFFFFFu, W, 31);
+  bp.advance();
+  e1 += 256u;
+  if (e1 >= kOrder) e1 -= kOrder;
+}
+
+// the two aligned chunks lane l's chunk c0 + l is realigned from (zero past the key)
+__device__ __forceinline__ void prefix_load(const uint8_t* __restrict__ arena, uint64_t s0, uint64_t len, uint64_t c0,
+                                            uint4& ra, uint4& rb) {
+  const uint64_t c = c0 + (threadIdx.x & 31u);
+  ra = make_uint4(0, 0, 0, 0);
+  rb = ra;
+  if (16 * c < len) {
+    const uint32_t a = (uint32_t)(s0 & 15u);
+    const uint8_t* base = arena + s0 - a;           // aligned; key bytes are [a, a + len) from here
+    const uint64_t o16 = 16 * c;
+    ra = ld16(base + o16);
+    if (o16 + 16 < a + len) rb = ld16(base + o16 + 16);
   }
 }
 
+// Warps take keys i = warp, warp + nwarps, ...; the work of a warp is the
+// sequence of (key, step) items, and the chunks of the next item (and the
+// offsets of the next key) are loaded before the current item is computed, so
+// the memory latency of a step overlaps the arithmetic of the one before.
 __global__ void __launch_bounds__(kPThreads) prefix_kernel(const uint8_t* __restrict__ arena,
                                                            const uint64_t* __restrict__ off, uint64_t n,
                                                            uint32_t block_bytes,
@@ -210,22 +241,66 @@ __global__ void __launch_bounds__(kPThreads) prefix_kernel(const uint8_t* __rest
   extern __shared__ __align__(16) uint8_t smem[];
   __shared__ uint4 emask[17];
   uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  uint16_t* ptab = reinterpret_cast<uint16_t*>(smem + kRedBytes + 512 * 4);
+  for (int i = threadIdx.x; i < kPConst * 512 / 2; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(ptab)[i] = reinterpret_cast<const uint32_t*>(g_pconst)[i];
   fill_emask(emask);
   init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
   const RedCursor rc = red_cursor(red);
+  const uint32_t lane = threadIdx.x & 31u;
   BlockPos bp;
   bp.cpb = block_bytes / 16u;
   bp.dq = 32u / bp.cpb;
   bp.dr = 32u % bp.cpb;
-  bp.q0 = (threadIdx.x & 31u) / bp.cpb;
-  bp.r0 = (threadIdx.x & 31u) % bp.cpb;
+  bp.q0 = lane / bp.cpb;
+  bp.r0 = lane % bp.cpb;
   const uint64_t nwarps = (uint64_t)gridDim.x * (kPThreads / 32);
-  for (uint64_t i = (uint64_t)blockIdx.x * (kPThreads / 32) + (threadIdx.x >> 5); i < n; i += nwarps) {
-    const uint64_t s0 = off[i];
-    prefix_key(arena, s0, off[i + 1] - s0, bp, out + pref_off[i], emask, rc);
+  uint64_t i = (uint64_t)blockIdx.x * (kPThreads / 32) + (threadIdx.x >> 5);
+  if (i >= n) return;                                // warp-uniform
+  // current key and its first step's chunks; the next key's offsets
+  uint64_t s0 = off[i], len = off[i + 1] - s0, po = pref_off[i];
+  uint64_t in = i + nwarps, s0n = 0, lenn = 0, pon = 0;
+  if (in < n) { s0n = off[in]; lenn = off[in + 1] - s0n; pon = pref_off[in]; }
+  uint64_t c0 = 0;
+  uint4 ra, rb;
+  prefix_load(arena, s0, len, 0, ra, rb);
+  uint64_t carry = 0;
+  uint32_t e1 = 8u * lane;
+  bp.start();
+  for (;;) {
+    // the item after this one: the key's next step, or the next key's first
+    const uint64_t nchunks = (len + 15) / 16;
+    const bool more = c0 + 32 < nchunks;
+    const bool next_key = !more && in < n;
+    uint4 ra2 = make_uint4(0, 0, 0, 0), rb2 = ra2;
+    if (more) prefix_load(arena, s0, len, c0 + 32, ra2, rb2);
+    else if (next_key) prefix_load(arena, s0n, lenn, 0, ra2, rb2);
+    uint64_t s0nn = 0, lennn = 0, ponn = 0;
+    const uint64_t inn = in + nwarps;
+    if (next_key && inn < n) { s0nn = off[inn]; lennn = off[inn + 1] - s0nn; ponn = pref_off[inn]; }
+    // this item
+    if (len == 0) {
+      if (lane == 0) out[po] = 0;
+    } else {
+      prefix_step(ra, rb, (uint32_t)(s0 & 15u), len, c0, bp, e1, carry, out + po, emask, rc, ptab);
+    }
+    if (more) {
+      c0 += 32;
+    } else if (next_key) {
+      i = in; s0 = s0n; len = lenn; po = pon;
+      in = inn; s0n = s0nn; lenn = lennn; pon = ponn;
+      c0 = 0;
+      carry = 0;
+      e1 = 8u * lane;
+      bp.start();
+    } else {
+      break;
+    }
+    ra = ra2;
+    rb = rb2;
   }
 }
 
-constexpr size_t kSmemPrefix = (size_t)kRedBytes + 512 * 4;
+constexpr size_t kSmemPrefix = (size_t)kRedBytes + 512 * 4 + (size_t)kPConst * 512 * 2;
 
 }  // namespace algsig
