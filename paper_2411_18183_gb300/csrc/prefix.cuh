@@ -198,10 +198,15 @@ __device__ __forceinline__ void prefix_step(const uint4& ra, const uint4& rb, ui
     horner_chunk(v0, v1, v2, v3, t1, t2, t3, t4, rc);
     W = (uint64_t)t1 | ((uint64_t)t2 << 16) | ((uint64_t)t3 << 32) | ((uint64_t)t4 << 48);
   }
-  const uint64_t cin = mul_pscan(ptab, carry, 0);   // x^(-8k) D(c0 - 1), enters at lane 0
-  if (lane == 0) W ^= cin;
+  if (c0 != 0) {                                   // x^(-8k) D(c0 - 1) enters at lane 0 (zero on a key's first step)
+    const uint64_t cin = mul_pscan(ptab, carry, 0);
+    if (lane == 0) W ^= cin;
+  }
+  // levels for the step's live chunks only (warp-uniform)
+  const uint32_t live = nchunks - c0 < 32 ? (uint32_t)(nchunks - c0) : 32u;
 #pragma unroll
   for (int s = 0; s < kPLevels; s++) {
+    if ((1u << s) >= live) break;
     const uint64_t t = __shfl_up_sync(0xFFFFFFFFu, W, 1u << s);
     if (lane >= (1u << s)) W ^= mul_pscan(ptab, t, s);
   }
