@@ -302,6 +302,30 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
                   uint64_t* d_count, uint64_t* h_count, as_stream stream);
 
 /*
+ * Radix-partitioned join: the same result as as_join, with R and S first split
+ * into 2^part_bits partitions by the top bits of the bucket hash of (signature,
+ * length), each partition joined with its own table (the partitioned, Grace
+ * style hash join of Sections 2 and 4, in device memory).  Partitions hold
+ * (signature, length | row) entries, not key bytes; the probe walks S in
+ * partition order and verifies candidates byte for byte from the arenas.
+ *
+ * as_join_part_ws_bytes -- workspace for |R| = m, |S| = n (0 for a load factor
+ *   outside (0, 1], m >= 2^32 - 1, n >= 2^32 or part_bits > 12).
+ * as_join_partitioned -- arguments as for as_join, plus part_bits: the number
+ *   of partition bits, 0..12, or AS_PART_BITS_AUTO (about 1024 R rows per
+ *   partition).  Errors: AS_ERR_INVALID (bad argument, misaligned arena or
+ *   pair buffer), AS_ERR_NOMEM (workspace too small), AS_ERR_TABLE_FULL,
+ *   AS_ERR_CAPACITY (more pairs than cap_pairs; the count is still written),
+ *   AS_ERR_CUDA.  Synchronises the stream when h_count is not NULL.
+ */
+#define AS_PART_BITS_AUTO 0xFFFFFFFFu
+size_t as_join_part_ws_bytes(uint64_t m, uint64_t n, float load_factor, uint32_t part_bits);
+as_status as_join_partitioned(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
+                              const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
+                              float load_factor, uint32_t part_bits, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
+                              uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream);
+
+/*
  * Batches of independent joins (many joins of uneven sizes and key lengths in
  * one set of launches).  All joins' R relations are packed into one R
  * relation (one arena, one offset array) and all S relations into one S

@@ -903,6 +903,7 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
 
 #include "prefix.cuh"
 #include "gf8.cuh"
+#include "partition.cuh"
 
 namespace algsig {
 
@@ -1608,6 +1609,134 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
   uint64_t* cnt = d_count ? d_count : (uint64_t*)rest;
   return as_join_probe(&t, d_arenaS, d_offS, d_idS, n, nullptr, rest + 256, need - tb - 256, d_pairs, cap_pairs, cnt,
                        h_count, stream);
+}
+
+// ----------------------------------------------------------------------------
+// Radix-partitioned join (partition.cuh)
+// ----------------------------------------------------------------------------
+
+static uint32_t part_bits_for(uint64_t m, uint32_t part_bits) {
+  if (part_bits != AS_PART_BITS_AUTO) return part_bits;
+  uint32_t b = 0;
+  while (b < (uint32_t)kPartMaxBits && (m >> (b + 10)) > 0) ++b;   // about 1024 R rows per partition
+  return b;
+}
+
+// workspace: sigR | sigS | entR | entS | 7 per-partition arrays | slots | flags, counter
+static bool part_layout(uint64_t m, uint64_t n, float lf, uint32_t pbits, uint64_t* slots_max, uint64_t* bytes) {
+  if (!(lf > 0.0f && lf <= 1.0f) || m >= 0xFFFFFFFFull || n >= 0x100000000ull || pbits > (uint32_t)kPartMaxBits)
+    return false;
+  const uint64_t P = 1ull << pbits;
+  // each partition's table is a power of two >= max(64, rows / lf), so below 2 rows / lf + 64
+  const uint64_t sm = (uint64_t)(2.0 * (double)m / (double)lf) + 64 * P + P;
+  *slots_max = sm;
+  *bytes = round256(m * 8) + round256(n * 8) + round256(m * 16) + round256(n * 16) + 7 * round256((P + 1) * 8) +
+           round256(sm * 16) + 512;
+  return true;
+}
+
+size_t as_join_part_ws_bytes(uint64_t m, uint64_t n, float load_factor, uint32_t part_bits) {
+  uint64_t sm, bytes;
+  if (!part_layout(m, n, load_factor, part_bits_for(m, part_bits), &sm, &bytes)) return 0;
+  return (size_t)bytes;
+}
+
+as_status as_join_partitioned(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
+                              const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
+                              float load_factor, uint32_t part_bits, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
+                              uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  NvtxRange nvtx_range("as_join_partitioned");
+  const uint32_t pbits = part_bits_for(m, part_bits);
+  uint64_t smax, need;
+  if (!part_layout(m, n, load_factor, pbits, &smax, &need))
+    return fail(AS_ERR_INVALID, "as_join_partitioned: need 0 < load_factor <= 1, m < 2^32-1, n < 2^32, part_bits <= %d",
+                kPartMaxBits);
+  if ((m > 0 && (!d_arenaR || !d_offR)) || (n > 0 && (!d_arenaS || !d_offS)) || (cap_pairs > 0 && !d_pairs))
+    return fail(AS_ERR_INVALID, "as_join_partitioned: null pointer");
+  if ((m > 0 && misaligned16(d_arenaR)) || (n > 0 && misaligned16(d_arenaS)))
+    return fail(AS_ERR_INVALID, "as_join_partitioned: arena not 16-byte aligned");
+  if (d_pairs && (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
+    return fail(AS_ERR_INVALID, "as_join_partitioned: pair buffer not 8-byte aligned");
+  if (!d_ws || ws_bytes < need)
+    return fail(AS_ERR_NOMEM, "as_join_partitioned: workspace of %zu bytes, need %llu", ws_bytes,
+                (unsigned long long)need);
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255u)
+    return fail(AS_ERR_INVALID, "as_join_partitioned: workspace not 256-byte aligned");
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  const uint64_t P = 1ull << pbits;
+  uint8_t* w = (uint8_t*)d_ws;
+  auto take = [&](uint64_t nbytes) { uint8_t* p = w; w += round256(nbytes); return p; };
+  uint64_t* sigR = (uint64_t*)take(m * 8);
+  uint64_t* sigS = (uint64_t*)take(n * 8);
+  PartEntry* entR = (PartEntry*)take(m * 16);
+  PartEntry* entS = (PartEntry*)take(n * 16);
+  unsigned long long* cntR = (unsigned long long*)take((P + 1) * 8);
+  unsigned long long* cntS = (unsigned long long*)take((P + 1) * 8);
+  unsigned long long* startR = (unsigned long long*)take((P + 1) * 8);
+  unsigned long long* startS = (unsigned long long*)take((P + 1) * 8);
+  unsigned long long* curR = (unsigned long long*)take((P + 1) * 8);
+  unsigned long long* curS = (unsigned long long*)take((P + 1) * 8);
+  unsigned long long* slot_off = (unsigned long long*)take((P + 1) * 8);
+  Slot* slots = (Slot*)take(smax * 16);
+  uint32_t* flags = (uint32_t*)w;
+  uint64_t* cnt = d_count ? d_count : (uint64_t*)(w + 256);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(cntR, 0, (P + 1) * 8, s)) != cudaSuccess) return cuda_fail(e, "partition counts");
+  if ((e = cudaMemsetAsync(cntS, 0, (P + 1) * 8, s)) != cudaSuccess) return cuda_fail(e, "partition counts");
+  if ((e = cudaMemsetAsync(slots, 0xFF, smax * 16, s)) != cudaSuccess) return cuda_fail(e, "table clear");
+  if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
+  if ((e = cudaMemsetAsync(cnt, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  if ((st = launch_sig(d_arenaR, d_offR, m, sigR, s)) != AS_OK) return st;
+  if ((st = launch_sig(d_arenaS, d_offS, n, sigS, s)) != AS_OK) return st;
+  const unsigned gb = (unsigned)d->sms * 4;
+  if (m > 0) part_hist_kernel<<<gb, kPartThreads, 0, s>>>(sigR, d_offR, m, pbits, cntR);
+  if (n > 0) part_hist_kernel<<<gb, kPartThreads, 0, s>>>(sigS, d_offS, n, pbits, cntS);
+  part_layout_kernel<<<1, 1024, 0, s>>>(cntR, cntS, pbits, load_factor, startR, startS, curR, curS, slot_off);
+  if (m > 0) part_scatter_kernel<<<gb, kPartThreads, 0, s>>>(sigR, d_offR, m, pbits, curR, entR);
+  if (n > 0) part_scatter_kernel<<<gb, kPartThreads, 0, s>>>(sigS, d_offS, n, pbits, curS, entS);
+  if (m > 0) part_build_kernel<<<gb, kPartThreads, 0, s>>>(entR, m, pbits, slot_off, slots, flags);
+  if (n > 0) {
+    PartProbeParams Q;
+    Q.entS = entS;
+    Q.n = n;
+    Q.pbits = pbits;
+    Q.slot_off = slot_off;
+    Q.slots = slots;
+    VerifyParams& V = Q.V;
+    memset(&V, 0, sizeof(V));
+    V.arenaR = d_arenaR;
+    V.offR = d_offR;
+    V.idR = d_idR;
+    V.arenaS = d_arenaS;
+    V.offS = d_offS;
+    V.idS = d_idS;
+    V.pairs = d_pairs;
+    V.cap = cap_pairs;
+    V.count = reinterpret_cast<unsigned long long*>(cnt);
+    V.mode = AS_JOIN_INNER;
+    uint64_t blocks = (n + kVThreads - 1) / kVThreads;
+    const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
+    if (blocks > lim) blocks = lim;
+    part_probe_kernel<<<(unsigned)blocks, kVThreads, 0, s>>>(Q);
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "partitioned join launch");
+  if (h_count) {
+    uint64_t c = 0;
+    uint32_t flags_h = 0;
+    if ((e = cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "count readback");
+    if ((e = cudaMemcpyAsync(&flags_h, flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_fail(e, "flag readback");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "partitioned join");
+    *h_count = c;
+    if (flags_h & kFlagTableFull) return fail(AS_ERR_TABLE_FULL, "as_join_partitioned: build overflow");
+    if (c > cap_pairs)
+      return fail(AS_ERR_CAPACITY, "as_join_partitioned: %llu pairs, capacity %llu", (unsigned long long)c,
+                  (unsigned long long)cap_pairs);
+  }
+  return AS_OK;
 }
 
 // ----------------------------------------------------------------------------
