@@ -17,6 +17,8 @@ It wraps oracle.c, a plain C statement of:
   * the n-component signature (the first n of the four components) and the
     signature-only join of Figure 2 (pairs of equal signature and length, no
     byte comparison; not exact, kept to count collisions), in Python;
+  * the prefix join T_L = {(r.id, s.id) : key(r)[:L] == key(s)[:L]} (the join
+    on the keys' first L bytes that cumulative signatures serve), in Python;
   * the exact equi-join T = {(r.id, s.id) : key(r) == key(s)} by a nested loop,
     a simple hash join on full strings and a Grace (partitioned) hash join
     (Section 2; Figure 2 without the signature shortcut, since the result must
@@ -281,6 +283,24 @@ def join_sig_only(R, S, n_components: int = 4, field: int = 16) -> np.ndarray:
     out = []
     for j in range(len(sS)):
         for rid in groups.get((int(sS[j]), int(lS[j])), ()):
+            out.append((rid, int(S.ids[j])))
+    return sort_pairs(np.array(out, dtype=np.uint32).reshape(-1, 2))
+
+
+def join_prefix(R, S, prefix_len: int) -> np.ndarray:
+    """The join on the keys' first prefix_len bytes, by its plain definition:
+    every (r.id, s.id) with key(r)[:L] == key(s)[:L] as byte strings (so the
+    truncated lengths are equal too).  Group R by its truncated key, look every
+    S key up.  Sorted like sort_pairs."""
+    L = int(prefix_len)
+    groups = {}
+    for i in range(len(R.off) - 1):
+        k = bytes(R.arena[int(R.off[i]):int(R.off[i + 1])])[:L]
+        groups.setdefault(k, []).append(int(R.ids[i]))
+    out = []
+    for j in range(len(S.off) - 1):
+        k = bytes(S.arena[int(S.off[j]):int(S.off[j + 1])])[:L]
+        for rid in groups.get(k, ()):
             out.append((rid, int(S.ids[j])))
     return sort_pairs(np.array(out, dtype=np.uint32).reshape(-1, 2))
 

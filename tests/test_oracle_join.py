@@ -153,3 +153,22 @@ def test_signature_only_join_by_definition():
         m = np.uint64(oracle.component_mask(n))
         brute = [[i, j] for i in range(R.n) for j in range(S.n) if (sR[i] & m) == (sS[j] & m) and lR[i] == lS[j]]
         assert oracle.join_sig_only(R, S, n).tolist() == brute
+
+
+def test_prefix_join_by_definition_and_brute_force():
+    """The prefix join against what fixes it: with L at least the longest key it
+    is the exact join; at L = 0 every pair joins; and a nested loop over
+    truncated keys on small random inputs, for lengths around the keys'."""
+    rng = random.Random(21)
+    pool = [bytes(rng.randrange(3) for _ in range(rng.randrange(0, 12))) for _ in range(25)]
+    rkeys = [rng.choice(pool) for _ in range(70)]
+    skeys = [rng.choice(pool) for _ in range(90)]
+    R = relation_from_keys(rkeys, ids=[rng.randrange(2 ** 32) for _ in rkeys])
+    S = relation_from_keys(skeys, ids=[rng.randrange(2 ** 32) for _ in skeys])
+    assert np.array_equal(oracle.join_prefix(R, S, 12), oracle.join_simple(R, S))
+    everything = oracle.sort_pairs(np.array([(int(r), int(s)) for r in R.ids for s in S.ids], dtype=np.uint32))
+    assert np.array_equal(oracle.join_prefix(R, S, 0), everything)
+    for L in (1, 2, 3, 5, 8):
+        want = [(int(R.ids[i]), int(S.ids[j])) for i, a in enumerate(rkeys) for j, b in enumerate(skeys)
+                if a[:L] == b[:L]]
+        assert np.array_equal(oracle.join_prefix(R, S, L), oracle.sort_pairs(np.array(want, dtype=np.uint32))), L
