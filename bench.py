@@ -469,6 +469,25 @@ def run_gpu(args):
                    "speedup_vs_unpartitioned": ms_per_step / pms}
     del pws
 
+    # the prefix join (keys equal on their first 256 bytes) on the same inputs
+    PREFIX_LEN = 256
+    xws = ag.alloc_ws(ag.join_prefix_ws_bytes(m, n, lf))
+    xpairs = torch.empty(2 * (2 * total_pairs + 1024), dtype=torch.int32, device="cuda")
+    st, xcnt = ag.join_prefix_into(dR, dS, PREFIX_LEN, xws, xpairs, bcount, lf, sync=True)
+    if xcnt < total_pairs:
+        raise SystemExit(f"prefix join found {xcnt} pairs, fewer than the exact join's {total_pairs}")
+    for _ in range(2):
+        ag.join_prefix_into(dR, dS, PREFIX_LEN, xws, xpairs, bcount, lf, sync=False, stream=stream)
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for _ in range(breps):
+        ag.join_prefix_into(dR, dS, PREFIX_LEN, xws, xpairs, bcount, lf, sync=False, stream=stream)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    xms = b0.elapsed_time(b1) / breps
+    prefix_join = {"prefix_len": PREFIX_LEN, "ms_per_join": xms, "tuples_per_s": n / (xms * 1e-3), "pairs": xcnt}
+    del xws, xpairs
+
     # the paper's own variants on the same resident inputs: the probe of Figure 2 on
     # signatures only (no byte verification; its extra pairs are signature collisions),
     # with four components and with the paper's two (sig_{alpha,2}), and the exact
@@ -646,6 +665,7 @@ def run_gpu(args):
         "kernels": kernels,
         "fullstring_gpu_join": baseline,
         "partitioned_join": partitioned,
+        "prefix_join": prefix_join,
         "speedup_vs_fullstring": {k: value / v["tuples_per_s"] for k, v in baseline.items()},
         "paper_variants": paper_variants,
         "cumulative_signatures": cumulative_sigs,

@@ -302,6 +302,25 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
                   uint64_t* d_count, uint64_t* h_count, as_stream stream);
 
 /*
+ * Prefix join: the join on the keys' first L bytes,
+ *     T_L = {(r.id, s.id) : r.key[0 .. min(L, |r|)) == s.key[0 .. min(L, |s|))},
+ * byte strings equal (so of equal length).  The signature of a key's L-byte
+ * prefix is its cumulative signature at L (Section 5's cumulative
+ * signatures); the build, probe and verification run on the truncated keys.
+ * With L at least the longest key it is as_join's result; with L = 0 every
+ * pair joins.
+ *
+ * as_join_prefix_ws_bytes -- workspace (0 for a bad load factor or m >= 2^32-1).
+ * as_join_prefix -- arguments as for as_join, plus prefix_len = L
+ *   (0 <= L <= 2^32 - 16).  Errors as for as_join_partitioned.
+ */
+size_t as_join_prefix_ws_bytes(uint64_t m, uint64_t n, float load_factor);
+as_status as_join_prefix(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
+                         const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
+                         uint64_t prefix_len, float load_factor, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
+                         uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream);
+
+/*
  * Radix-partitioned join: the same result as as_join, with R and S first split
  * into 2^part_bits partitions by the top bits of the bucket hash of (signature,
  * length), each partition joined with its own table (the partitioned, Grace

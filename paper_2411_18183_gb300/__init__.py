@@ -34,7 +34,7 @@ EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_device_faults"
            "as_sig_compute_gf8",
            "as_sig_prefix_ws_bytes", "as_sig_prefix_offsets", "as_sig_prefixes", "as_join_table_bytes",
            "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_probe_sigs", "as_join_probe_mode", "as_join_ws_bytes", "as_join",
-           "as_join_part_ws_bytes", "as_join_partitioned", "as_baseline_ws_bytes", "as_baseline_join")
+           "as_join_part_ws_bytes", "as_join_partitioned", "as_join_prefix_ws_bytes", "as_join_prefix", "as_baseline_ws_bytes", "as_baseline_join")
 
 
 class AlgsigError(RuntimeError):
@@ -100,6 +100,10 @@ def load(path: str | None = None):
         lib.as_join_probe_mode.restype = S
         lib.as_join.argtypes = [P, P, P, U64, P, P, P, U64, F, P, SZ, P, U64, P, P, P]
         lib.as_join.restype = S
+        lib.as_join_prefix_ws_bytes.argtypes = [U64, U64, F]
+        lib.as_join_prefix_ws_bytes.restype = SZ
+        lib.as_join_prefix.argtypes = [P, P, P, U64, P, P, P, U64, U64, F, P, SZ, P, U64, P, P, P]
+        lib.as_join_prefix.restype = S
         lib.as_join_part_ws_bytes.argtypes = [U64, U64, F, ctypes.c_uint32]
         lib.as_join_part_ws_bytes.restype = SZ
         lib.as_join_partitioned.argtypes = [P, P, P, U64, P, P, P, U64, F, ctypes.c_uint32, P, SZ, P, U64, P, P, P]
@@ -336,6 +340,40 @@ def join(R: DeviceRelation, S: DeviceRelation, load_factor: float = 0.5, cap_pai
     while True:
         pairs = torch.empty(2 * max(cap, 1), dtype=torch.int32, device=dev)
         st, cnt = join_into(R, S, ws, pairs, count, load_factor, sync=True, stream=stream, allow_capacity=True)
+        if st == AS_OK:
+            return pairs[:2 * cnt].view(-1, 2)
+        cap = cnt
+
+
+def join_prefix_ws_bytes(m: int, n: int, load_factor: float = 0.5) -> int:
+    return int(load().as_join_prefix_ws_bytes(m, n, load_factor))
+
+
+def join_prefix_into(R: DeviceRelation, S: DeviceRelation, prefix_len: int, ws: torch.Tensor, pairs: torch.Tensor,
+                     count: torch.Tensor, load_factor: float = 0.5, sync: bool = True, stream=None,
+                     allow_capacity: bool = False):
+    """as_join_prefix (the join on the keys' first prefix_len bytes) into caller buffers."""
+    lib = load()
+    cap = pairs.numel() // 2
+    h = ctypes.c_uint64(0)
+    st = lib.as_join_prefix(_ptr(R.arena), _ptr(R.off), _ptr(R.ids), R.n, _ptr(S.arena), _ptr(S.off), _ptr(S.ids),
+                            S.n, prefix_len, load_factor, _ptr(ws), ws.numel(), _ptr(pairs), cap, _ptr(count),
+                            ctypes.byref(h) if sync else None, _stream(stream))
+    _check(st, allow=(AS_ERR_CAPACITY,) if allow_capacity else ())
+    return st, (int(h.value) if sync else None)
+
+
+def join_prefix(R: DeviceRelation, S: DeviceRelation, prefix_len: int, load_factor: float = 0.5,
+                cap_pairs: int | None = None, stream=None) -> torch.Tensor:
+    """The join on the keys' first prefix_len bytes; (cnt, 2) int32 tensor of (r_id, s_id) pairs."""
+    dev = R.arena.device
+    ws = alloc_ws(join_prefix_ws_bytes(R.n, S.n, load_factor), dev)
+    cap = cap_pairs if cap_pairs is not None else max(1024, S.n)
+    count = torch.zeros(1, dtype=torch.int64, device=dev)
+    while True:
+        pairs = torch.empty(2 * max(cap, 1), dtype=torch.int32, device=dev)
+        st, cnt = join_prefix_into(R, S, prefix_len, ws, pairs, count, load_factor, sync=True, stream=stream,
+                                   allow_capacity=True)
         if st == AS_OK:
             return pairs[:2 * cnt].view(-1, 2)
         cap = cnt

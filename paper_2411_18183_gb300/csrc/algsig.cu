@@ -44,6 +44,7 @@ constexpr int kWarpsPerBlock = ALGSIG_WARPS;
 constexpr int kThreads = 32 * kWarpsPerBlock;   // one block per SM
 constexpr uint64_t kEmpty = ~0ull;              // empty hash slot
 constexpr uint32_t kFlagTableFull = 1u;
+constexpr uint64_t kMaxPrefixLen = 0xFFFFFFF0ull;  // the prefix join's L: one prefix block of at most this many bytes
 constexpr int kMaxDevices = 64;
 
 // shared memory: reduction tables | their scratch | per-warp double buffers | per-warp pair buffers
@@ -531,7 +532,7 @@ __device__ __forceinline__ uint32_t len32(uint64_t len) {
 // J == nullptr, the table is slots[0..mask].
 __global__ void build_kernel(Slot* __restrict__ slots, uint64_t mask, const uint64_t* __restrict__ sigR,
                              const uint64_t* __restrict__ offR, uint64_t m, uint32_t* __restrict__ flags,
-                             const BatchJoin* __restrict__ J, int nj) {
+                             const BatchJoin* __restrict__ J, int nj, uint64_t cap_len = ~0ull) {
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t v = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; v < m; v += stride) {
     Slot* tab = slots;
@@ -543,7 +544,8 @@ __global__ void build_kernel(Slot* __restrict__ slots, uint64_t mask, const uint
       tab = slots + __ldg(&J[j].slot_off);
       msk = __ldg(&J[j].mask);
     }
-    const uint64_t len = offR[row + 1] - offR[row];
+    const uint64_t full = offR[row + 1] - offR[row];
+    const uint64_t len = full < cap_len ? full : cap_len;   // the prefix join reads keys' first cap_len bytes
     const uint64_t sig = sigR[v];
     const uint64_t word = ((uint64_t)len32(len) << 32) | row;
     uint64_t b = sig_hash(sig, len) & msk;
@@ -596,6 +598,7 @@ struct VerifyParams {
   const BatchJoin* J;
   int nj;
   unsigned long long* counts;
+  uint64_t cap_len = ~0ull;    // keys compared on their first cap_len bytes (the prefix join)
 };
 
 __device__ __forceinline__ uint4 ld16(const uint8_t* p) { return __ldg(reinterpret_cast<const uint4*>(p)); }
@@ -819,6 +822,7 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
       sig = __ldg(P.sigS + vi);
       start = __ldg(P.offS + i);
       len = __ldg(P.offS + i + 1) - start;
+      if (len > P.cap_len) len = P.cap_len;
       b = sig_hash(sig, len) & mask;
       l32 = len32(len);
     }
@@ -852,7 +856,9 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
           eq = !verify || warp_equal(P.arenaR + rs, P.arenaS + stj, lj, emask);
         } else {                                      // lengths that the slot's 32-bit field saturates
           const uint64_t ls = __shfl_sync(kFull, len, j);
-          eq = __ldg(P.offR + rj + 1) - rs == ls && (!verify || warp_equal_wide(P.arenaR, rs, P.arenaS, stj, ls));
+          uint64_t lr = __ldg(P.offR + rj + 1) - rs;
+          if (lr > P.cap_len) lr = P.cap_len;
+          eq = lr == ls && (!verify || warp_equal_wide(P.arenaR, rs, P.arenaS, stj, ls));
         }
         if (eq) {
           const uint64_t srow = __shfl_sync(kFull, i, j);
@@ -1090,6 +1096,7 @@ struct DeviceState {
   int sms = 0;
   int verify_blocks_per_sm = 1;
   int prefix_blocks_per_sm = 1;
+  int capsig_blocks_per_sm = 1;
   bool tables_at400 = false;   // dynamic shared memory starts at shared address 0x400
 };
 
@@ -1197,6 +1204,13 @@ static as_status ensure_device(DeviceState** out) {
                                                            kSmemPrefix)) != cudaSuccess)
       return cuda_fail(e, "occupancy query");
     if (d.prefix_blocks_per_sm < 1) d.prefix_blocks_per_sm = 1;
+    if ((e = cudaFuncSetAttribute(capsig_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCapSig)) !=
+        cudaSuccess)
+      return cuda_fail(e, "kernel attribute");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.capsig_blocks_per_sm, capsig_kernel, kCapThreads,
+                                                           kSmemCapSig)) != cudaSuccess)
+      return cuda_fail(e, "occupancy query");
+    if (d.capsig_blocks_per_sm < 1) d.capsig_blocks_per_sm = 1;
     if ((e = cudaFuncSetAttribute(sig8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig8)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
@@ -1474,8 +1488,10 @@ static as_status probe_args(const char* fn, const as_table* t, const uint8_t* d_
 // table walk + verification + compaction of n S keys whose signatures are in sigS
 static as_status launch_verify(DeviceState* d, const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
                                const uint32_t* d_idS, uint64_t n, const uint64_t* sigS, uint32_t* d_pairs,
-                               uint64_t cap_pairs, uint64_t* d_count, cudaStream_t s, int mode = AS_JOIN_INNER) {
+                               uint64_t cap_pairs, uint64_t* d_count, cudaStream_t s, int mode = AS_JOIN_INNER,
+                               uint64_t cap_len = ~0ull) {
   VerifyParams P;
+  P.cap_len = cap_len;
   P.slots = reinterpret_cast<const Slot*>(t->slots);
   P.mask = t->cap - 1;
   P.arenaR = t->arenaR;
@@ -1612,6 +1628,106 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
 }
 
 // ----------------------------------------------------------------------------
+// Prefix join: the join on the keys' first L bytes
+// ----------------------------------------------------------------------------
+
+size_t as_join_prefix_ws_bytes(uint64_t m, uint64_t n, float load_factor) {
+  uint64_t cap;
+  uint32_t l2;
+  if (!table_geometry(m, load_factor, &cap, &l2)) return 0;
+  return (size_t)(round256(cap * 16) + round256(m * 8) + round256(n * 8) + 512);
+}
+
+// signatures of the first min(len, L) bytes of every key (one thread per key)
+static as_status launch_capped_sigs(DeviceState* d, const uint8_t* arena, const uint64_t* off, uint64_t n, uint64_t L,
+                                    uint64_t* out, cudaStream_t s) {
+  if (n == 0) return AS_OK;
+  const uint64_t want = (n + kCapThreads - 1) / kCapThreads;
+  const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->capsig_blocks_per_sm;
+  const unsigned blocks = (unsigned)(want < lim ? want : lim);
+  capsig_kernel<<<blocks, kCapThreads, kSmemCapSig, s>>>(arena, off, n, L, out);
+  cudaError_t e = cudaGetLastError();
+  return e == cudaSuccess ? AS_OK : cuda_fail(e, "prefix signature launch");
+}
+
+as_status as_join_prefix(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
+                         const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
+                         uint64_t prefix_len, float load_factor, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
+                         uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  NvtxRange nvtx_range("as_join_prefix");
+  uint64_t cap;
+  uint32_t l2;
+  if (!table_geometry(m, load_factor, &cap, &l2))
+    return fail(AS_ERR_INVALID, "as_join_prefix: need 0 < load_factor <= 1 and m < 2^32-1");
+  if (prefix_len > kMaxPrefixLen)
+    return fail(AS_ERR_INVALID, "as_join_prefix: prefix_len above %llu", (unsigned long long)kMaxPrefixLen);
+  if ((m > 0 && (!d_arenaR || !d_offR)) || (n > 0 && (!d_arenaS || !d_offS)) || (cap_pairs > 0 && !d_pairs))
+    return fail(AS_ERR_INVALID, "as_join_prefix: null pointer");
+  if ((m > 0 && misaligned16(d_arenaR)) || (n > 0 && misaligned16(d_arenaS)))
+    return fail(AS_ERR_INVALID, "as_join_prefix: arena not 16-byte aligned");
+  if (d_pairs && (reinterpret_cast<uintptr_t>(d_pairs) & 7u))
+    return fail(AS_ERR_INVALID, "as_join_prefix: pair buffer not 8-byte aligned");
+  const size_t need = as_join_prefix_ws_bytes(m, n, load_factor);
+  if (!d_ws || ws_bytes < need)
+    return fail(AS_ERR_NOMEM, "as_join_prefix: workspace of %zu bytes, need %zu", ws_bytes, need);
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return fail(AS_ERR_INVALID, "as_join_prefix: workspace alignment");
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
+  if (st != AS_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  uint8_t* ws = (uint8_t*)d_ws;
+  Slot* slots = (Slot*)ws;
+  uint64_t* sigR = (uint64_t*)(ws + round256(cap * 16));
+  uint64_t* sigS = (uint64_t*)(ws + round256(cap * 16) + round256(m * 8));
+  uint8_t* tail = ws + round256(cap * 16) + round256(m * 8) + round256(n * 8);
+  uint32_t* flags = (uint32_t*)tail;
+  uint64_t* cnt = d_count ? d_count : (uint64_t*)(tail + 256);
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(slots, 0xFF, cap * 16, s)) != cudaSuccess) return cuda_fail(e, "table clear");
+  if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
+  if ((e = cudaMemsetAsync(cnt, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  if ((st = launch_capped_sigs(d, d_arenaR, d_offR, m, prefix_len, sigR, s)) != AS_OK) return st;
+  if (m > 0) {
+    uint64_t blocks = (m + 255) / 256;
+    const uint64_t lim = (uint64_t)d->sms * 16;
+    if (blocks > lim) blocks = lim;
+    build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, cap - 1, sigR, d_offR, m, flags, nullptr, 0, prefix_len);
+  }
+  if ((st = launch_capped_sigs(d, d_arenaS, d_offS, n, prefix_len, sigS, s)) != AS_OK) return st;
+  if (n > 0) {
+    as_table t;
+    memset(&t, 0, sizeof(t));
+    t.slots = reinterpret_cast<uint64_t*>(slots);
+    t.sigR = sigR;
+    t.arenaR = d_arenaR;
+    t.offR = d_offR;
+    t.idR = d_idR;
+    t.flags = flags;
+    t.m = m;
+    t.cap = cap;
+    t.log2cap = l2;
+    if ((st = launch_verify(d, &t, d_arenaS, d_offS, d_idS, n, sigS, d_pairs, cap_pairs, cnt, s, AS_JOIN_INNER,
+                            prefix_len)) != AS_OK)
+      return st;
+  }
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "prefix join launch");
+  if (h_count) {
+    uint64_t c = 0;
+    uint32_t flags_h = 0;
+    if ((e = cudaMemcpyAsync(&c, cnt, 8, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(e, "count readback");
+    if ((e = cudaMemcpyAsync(&flags_h, flags, 4, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return cuda_fail(e, "flag readback");
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(e, "prefix join");
+    *h_count = c;
+    if (flags_h & kFlagTableFull) return fail(AS_ERR_TABLE_FULL, "as_join_prefix: build overflow");
+    if (c > cap_pairs)
+      return fail(AS_ERR_CAPACITY, "as_join_prefix: %llu pairs, capacity %llu", (unsigned long long)c,
+                  (unsigned long long)cap_pairs);
+  }
+  return AS_OK;
+}
+
+// ----------------------------------------------------------------------------
 // Radix-partitioned join (partition.cuh)
 // ----------------------------------------------------------------------------
 
@@ -1707,6 +1823,7 @@ as_status as_join_partitioned(const uint8_t* d_arenaR, const uint64_t* d_offR, c
     Q.slots = slots;
     VerifyParams& V = Q.V;
     memset(&V, 0, sizeof(V));
+    V.cap_len = ~0ull;
     V.arenaR = d_arenaR;
     V.offR = d_offR;
     V.idR = d_idR;

@@ -20,7 +20,7 @@
 //   part_layout_kernel  exclusive scans: entry starts per partition, and the
 //                       partitions' table sizes (power of two >= max(64, rows / lf))
 //                       and slot offsets
-//   part_scatter_kernel entries into partition order (warp-aggregated cursors)
+//   part_scatter_kernel entries into partition order (block-aggregated cursors)
 //   part_build_kernel   R entries into their partition's table (linear probing)
 //   part_probe_kernel   S entries: table walk, byte verification, compaction
 #pragma once
@@ -115,36 +115,40 @@ __global__ void __launch_bounds__(1024) part_layout_kernel(const unsigned long l
   }
 }
 
-// entries of one relation into partition order; the lanes of a warp that land
-// in the same partition take one cursor increment between them
+// Entries of one relation into partition order.  Each block takes a run of
+// rows, counts them per partition in shared memory, reserves its range of every
+// partition with one global atomic (a partition that many rows share, a Zipf-hot
+// key's, then takes one increment per block, not per row), and writes its
+// entries through shared-memory cursors.
 __global__ void __launch_bounds__(kPartThreads) part_scatter_kernel(const uint64_t* __restrict__ sig,
                                                                     const uint64_t* __restrict__ off, uint64_t n,
                                                                     uint32_t pbits,
                                                                     unsigned long long* __restrict__ cur,
                                                                     PartEntry* __restrict__ ent) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  const uint64_t n_pad = (n + 31) & ~31ull;                         // whole warps iterate together
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n_pad; i += stride) {
-    const bool live = i < n;
-    uint64_t s = 0, len = 0;
-    uint32_t p = 0xFFFFFFFFu;
-    if (live) {
-      s = sig[i];
-      len = off[i + 1] - off[i];
-      p = part_of(sig_hash(s, len32(len)), pbits);
-    }
-    const uint32_t same = __match_any_sync(kFull, p);
-    const int leader = __ffs(same) - 1;
-    unsigned long long base = 0;
-    if (live && (int)lane == leader) base = atomicAdd(cur + p, (unsigned long long)__popc(same));
-    base = __shfl_sync(kFull, base, leader);
-    if (live) {
-      PartEntry e;
-      e.sig = s;
-      e.key = ((uint64_t)len32(len) << 32) | (uint64_t)i;
-      ent[base + __popc(same & lanemask_lt())] = e;
-    }
+  __shared__ uint32_t cnt[1 << kPartMaxBits];
+  __shared__ uint32_t base[1 << kPartMaxBits];      // entry indices fit 32 bits (n < 2^32)
+  const uint32_t P = 1u << pbits;
+  const uint64_t per = (n + gridDim.x - 1) / gridDim.x;
+  const uint64_t r0 = (uint64_t)blockIdx.x * per;
+  const uint64_t r1 = r0 + per < n ? r0 + per : n;
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) cnt[i] = 0;
+  __syncthreads();
+  for (uint64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x)
+    atomicAdd(&cnt[part_of(sig_hash(sig[i], len32(off[i + 1] - off[i])), pbits)], 1u);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < P; i += blockDim.x) {
+    if (cnt[i]) base[i] = (uint32_t)atomicAdd(cur + i, (unsigned long long)cnt[i]);
+    cnt[i] = 0;
+  }
+  __syncthreads();
+  for (uint64_t i = r0 + threadIdx.x; i < r1; i += blockDim.x) {
+    const uint64_t s = sig[i];
+    const uint64_t len = off[i + 1] - off[i];
+    const uint32_t p = part_of(sig_hash(s, len32(len)), pbits);
+    PartEntry e;
+    e.sig = s;
+    e.key = ((uint64_t)len32(len) << 32) | i;
+    ent[base[p] + atomicAdd(&cnt[p], 1u)] = e;
   }
 }
 

@@ -306,6 +306,61 @@ __global__ void __launch_bounds__(kPThreads) prefix_kernel(const uint8_t* __rest
   }
 }
 
+// Signatures of the first min(len, cap_len) bytes of every key, one thread per
+// key (the prefix join's keys, all about equally long once capped).  A thread
+// runs Horner's rule over its key's realigned chunks from the last to the
+// first (gf16.cuh's step; the last chunk masked past the key's end, the first
+// below its even start lo), then moves the result back by x^-(k lo/2).
+constexpr int kCapThreads = 1024;       // threads per block of capsig_kernel (39 registers a thread)
+
+__global__ void __launch_bounds__(kCapThreads) capsig_kernel(const uint8_t* __restrict__ arena,
+                                                           const uint64_t* __restrict__ off, uint64_t n,
+                                                           uint64_t cap_len, uint64_t* __restrict__ out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint4 emask[17];
+  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  uint16_t* inv32 = reinterpret_cast<uint16_t*>(smem + kRedBytes + 512 * 4);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)      // the x^-32 table of the tile combination
+    reinterpret_cast<uint32_t*>(inv32)[i] = reinterpret_cast<const uint32_t*>(g_const + 4 * kScanLevels * 512)[i];
+  fill_emask(emask);
+  init_red_tables(red, red + kRedWords);                     // ends with __syncthreads()
+  const RedCursor rc = red_cursor(red);
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t s0 = off[i];
+    uint64_t len = off[i + 1] - s0;
+    if (len > cap_len) len = cap_len;
+    uint32_t a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    const uint32_t a = (uint32_t)(s0 & 15u), odd = a & 1u, lo = a - odd, sh = 8u * odd;
+    if (len > 0) {
+      const uint8_t* base = arena + (s0 - a);                // aligned chunk holding the key's first byte
+      const uint64_t C = (lo + len + 15) >> 4;               // realigned chunks: bytes [16 c + odd, 16 c + 16 + odd)
+      const uint32_t tail_e = (uint32_t)(lo + len - 16 * (C - 1));
+      // the odd realignment of chunk c reads the first word of chunk c + 1
+      uint32_t nxt0 = (odd && tail_e == 16) ? __ldg(reinterpret_cast<const uint32_t*>(base + 16 * C)) : 0u;
+      for (uint64_t c = C; c-- > 0;) {
+        const uint4 w = __ldg(reinterpret_cast<const uint4*>(base + 16 * c));
+        uint32_t v0 = __funnelshift_r(w.x, w.y, sh), v1 = __funnelshift_r(w.y, w.z, sh);
+        uint32_t v2 = __funnelshift_r(w.z, w.w, sh), v3 = __funnelshift_r(w.w, nxt0, sh);
+        if (c == C - 1) {
+          const uint4 m = emask[tail_e];
+          v0 &= m.x; v1 &= m.y; v2 &= m.z; v3 &= m.w;
+        }
+        if (c == 0) {
+          const uint4 m = emask[lo];
+          v0 &= ~m.x; v1 &= ~m.y; v2 &= ~m.z; v3 &= ~m.w;
+        }
+        horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, rc);
+        nxt0 = w.x;
+      }
+    }
+    const uint64_t P = (uint64_t)a1 | ((uint64_t)a2 << 16) | ((uint64_t)a3 << 32) | ((uint64_t)a4 << 48);
+    out[i] = lo_correct_inv(inv32, P, lo, rc);
+  }
+}
+
+constexpr size_t kSmemCapSig = (size_t)kRedBytes + 512 * 4 + 512 * 2;
+
 constexpr size_t kSmemPrefix = (size_t)kRedBytes + 512 * 4 + (size_t)kPConst * 512 * 2;
 
 }  // namespace algsig

@@ -384,10 +384,9 @@ __device__ __forceinline__ uint64_t mul_scan(const uint16_t* ctab, uint64_t v, i
   return r;
 }
 
-// x^-(k lo/2) * P, component-wise
+// x^-(k lo/2) * P, component-wise; inv32: the table of x^-32
 template <class Cursor>
-__device__ __forceinline__ uint64_t lo_correct(const uint16_t* ctab, uint64_t P, uint32_t lo, const Cursor& rc) {
-  const uint16_t* inv32 = ctab + (size_t)(4 * kScanLevels) * 512;
+__device__ __forceinline__ uint64_t lo_correct_inv(const uint16_t* inv32, uint64_t P, uint32_t lo, const Cursor& rc) {
   uint64_t out = 0;
 #pragma unroll
   for (int k = 1; k <= 4; k++) {
@@ -399,6 +398,10 @@ __device__ __forceinline__ uint64_t lo_correct(const uint16_t* ctab, uint64_t P,
     out |= (uint64_t)r << (16 * (k - 1));
   }
   return out;
+}
+template <class Cursor>
+__device__ __forceinline__ uint64_t lo_correct(const uint16_t* ctab, uint64_t P, uint32_t lo, const Cursor& rc) {
+  return lo_correct_inv(ctab + (size_t)(4 * kScanLevels) * 512, P, lo, rc);
 }
 
 // packed tile value of a lane
