@@ -1097,6 +1097,7 @@ struct DeviceState {
   int verify_blocks_per_sm = 1;
   int prefix_blocks_per_sm = 1;
   int capsig_blocks_per_sm = 1;
+  int prefix_thread_blocks_per_sm = 1;
   bool tables_at400 = false;   // dynamic shared memory starts at shared address 0x400
 };
 
@@ -1211,6 +1212,13 @@ static as_status ensure_device(DeviceState** out) {
                                                            kSmemCapSig)) != cudaSuccess)
       return cuda_fail(e, "occupancy query");
     if (d.capsig_blocks_per_sm < 1) d.capsig_blocks_per_sm = 1;
+    if ((e = cudaFuncSetAttribute(prefix_thread_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)kSmemCapSig)) != cudaSuccess)
+      return cuda_fail(e, "kernel attribute");
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.prefix_thread_blocks_per_sm, prefix_thread_kernel,
+                                                           kCapThreads, kSmemCapSig)) != cudaSuccess)
+      return cuda_fail(e, "occupancy query");
+    if (d.prefix_thread_blocks_per_sm < 1) d.prefix_thread_blocks_per_sm = 1;
     if ((e = cudaFuncSetAttribute(sig8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig8)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
@@ -1387,11 +1395,21 @@ as_status as_sig_prefixes(const uint8_t* d_arena, const uint64_t* d_off, uint64_
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
   if (n == 0) return AS_OK;
-  const uint64_t want = (n + kPThreads / 32 - 1) / (kPThreads / 32);
-  const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->prefix_blocks_per_sm;   // persistent: one wave
-  const unsigned blocks = (unsigned)(want < lim ? want : lim);
-  prefix_kernel<<<blocks, kPThreads, kSmemPrefix, (cudaStream_t)stream>>>(d_arena, d_off, n, block_bytes, d_pref_off,
-                                                                          d_out);
+  if (block_bytes >= 32) {
+    // entries at most every other chunk: one thread per key, the suffix snapshots of prefix_thread_kernel
+    const uint64_t want = (n + kCapThreads - 1) / kCapThreads;
+    const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->prefix_thread_blocks_per_sm;
+    const unsigned blocks = (unsigned)(want < lim ? want : lim);
+    prefix_thread_kernel<<<blocks, kCapThreads, kSmemCapSig, (cudaStream_t)stream>>>(d_arena, d_off, n, block_bytes,
+                                                                                       d_pref_off, d_out);
+  } else {
+    // an entry after every chunk: one warp per key, the scan of D over the lanes
+    const uint64_t want = (n + kPThreads / 32 - 1) / (kPThreads / 32);
+    const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->prefix_blocks_per_sm;   // persistent: one wave
+    const unsigned blocks = (unsigned)(want < lim ? want : lim);
+    prefix_kernel<<<blocks, kPThreads, kSmemPrefix, (cudaStream_t)stream>>>(d_arena, d_off, n, block_bytes, d_pref_off,
+                                                                            d_out);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "prefix kernel launch");
   return AS_OK;

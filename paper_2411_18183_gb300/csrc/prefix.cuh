@@ -11,7 +11,9 @@
 //
 // Kernels.  prefix_count_kernel / prefix_total_kernel / prefix_offset_kernel
 // lay out the output: key i's entries start at pref_off[i], an exclusive scan
-// of max(1, ceil(len_i / B)).  prefix_kernel computes the entries: one warp per
+// of max(1, ceil(len_i / B)).  For B >= 32, prefix_thread_kernel (below)
+// computes the entries, one thread per key.  For B = 16 (an entry after every
+// chunk) prefix_kernel computes them: one warp per
 // key, 512 key bytes per step, lane l taking the key's 16-byte chunk c = 32 s + l
 // (realigned to the key's first byte from two aligned chunks, the word part of
 // the realignment warp-uniform).  The chunk's value T_c = sum_j q_j x^(k j) is a
@@ -356,6 +358,76 @@ __global__ void __launch_bounds__(kCapThreads) capsig_kernel(const uint8_t* __re
     }
     const uint64_t P = (uint64_t)a1 | ((uint64_t)a2 << 16) | ((uint64_t)a3 << 32) | ((uint64_t)a4 << 48);
     out[i] = lo_correct_inv(inv32, P, lo, rc);
+  }
+}
+
+// Cumulative signatures, one thread per key.  The thread runs the backward
+// Horner rule of capsig_kernel over the key's realigned chunks; since B is a
+// multiple of 16 every block boundary b_j = lo + (j+1) B falls at offset lo of
+// chunk c_j = (j+1) B/16, and the suffix of the key from b_j is one more Horner
+// step at c_j with the bytes below lo masked (acc'_j, relative to the chunk's
+// start).  It is parked in out[j]; once the whole signature S is known,
+//     C_j = S + x^(8 k c_j - k lo/2) acc'_j
+// (prefix = whole key minus suffix, the suffix moved to its place), formed
+// through the log / antilog tables, once per stored entry.
+__global__ void __launch_bounds__(kCapThreads) prefix_thread_kernel(const uint8_t* __restrict__ arena,
+                                                                    const uint64_t* __restrict__ off, uint64_t n,
+                                                                    uint32_t block_bytes,
+                                                                    const uint64_t* __restrict__ pref_off,
+                                                                    uint64_t* __restrict__ out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  __shared__ uint4 emask[17];
+  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  uint16_t* inv32 = reinterpret_cast<uint16_t*>(smem + kRedBytes + 512 * 4);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)
+    reinterpret_cast<uint32_t*>(inv32)[i] = reinterpret_cast<const uint32_t*>(g_const + 4 * kScanLevels * 512)[i];
+  fill_emask(emask);
+  init_red_tables(red, red + kRedWords);                     // ends with __syncthreads()
+  const RedCursor rc = red_cursor(red);
+  const uint64_t cpb = block_bytes / 16u;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+    const uint64_t s0 = off[i], len = off[i + 1] - s0;
+    uint64_t* o = out + pref_off[i];
+    if (len == 0) {
+      o[0] = 0;
+      continue;
+    }
+    const uint64_t nb = (len + block_bytes - 1) / block_bytes;
+    const uint32_t a = (uint32_t)(s0 & 15u), odd = a & 1u, lo = a - odd, sh = 8u * odd;
+    const uint8_t* base = arena + (s0 - a);
+    const uint64_t C = (lo + len + 15) >> 4;
+    const uint32_t tail_e = (uint32_t)(lo + len - 16 * (C - 1));
+    const uint4 mlo = emask[lo];
+    uint32_t a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    uint32_t nxt0 = (odd && tail_e == 16) ? __ldg(reinterpret_cast<const uint32_t*>(base + 16 * C)) : 0u;
+    for (uint64_t c = C; c-- > 0;) {
+      const uint4 w = __ldg(reinterpret_cast<const uint4*>(base + 16 * c));
+      uint32_t v0 = __funnelshift_r(w.x, w.y, sh), v1 = __funnelshift_r(w.y, w.z, sh);
+      uint32_t v2 = __funnelshift_r(w.z, w.w, sh), v3 = __funnelshift_r(w.w, nxt0, sh);
+      if (c == C - 1) {
+        const uint4 m = emask[tail_e];
+        v0 &= m.x; v1 &= m.y; v2 &= m.z; v3 &= m.w;
+      }
+      if (c > 0 && c % cpb == 0 && c / cpb <= nb - 1) {      // block boundary c_j, j = c / cpb - 1
+        uint32_t b1 = a1, b2 = a2, b3 = a3, b4 = a4;
+        horner_chunk(v0 & ~mlo.x, v1 & ~mlo.y, v2 & ~mlo.z, v3 & ~mlo.w, b1, b2, b3, b4, rc);
+        o[c / cpb - 1] = (uint64_t)b1 | ((uint64_t)b2 << 16) | ((uint64_t)b3 << 32) | ((uint64_t)b4 << 48);
+      }
+      if (c == 0) { v0 &= ~mlo.x; v1 &= ~mlo.y; v2 &= ~mlo.z; v3 &= ~mlo.w; }
+      horner_chunk(v0, v1, v2, v3, a1, a2, a3, a4, rc);
+      nxt0 = w.x;
+    }
+    const uint64_t S = lo_correct_inv(inv32, (uint64_t)a1 | ((uint64_t)a2 << 16) | ((uint64_t)a3 << 32) |
+                                                 ((uint64_t)a4 << 48), lo, rc);
+    for (uint64_t j = 0; j + 1 < nb; j++) {
+      const uint64_t v = o[j];
+      // e1 = 8 c_j - lo/2 (mod 65535), c_j = (j + 1) cpb; component k uses k e1
+      const uint32_t e1 = (uint32_t)((8 * ((j + 1) * cpb) + kOrder - lo / 2) % kOrder);
+      o[j] = S ^ shift_chunk_value((uint32_t)v & 0xFFFFu, (uint32_t)(v >> 16) & 0xFFFFu, (uint32_t)(v >> 32) & 0xFFFFu,
+                                   (uint32_t)(v >> 48), e1);
+    }
+    o[nb - 1] = S;
   }
 }
 

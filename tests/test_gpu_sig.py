@@ -95,7 +95,7 @@ def test_two_component_signatures(cuda):
         ag.sig_compute(ag.DeviceRelation.from_host(rels[0].arena, rels[0].off, rels[0].ids), n_components=3)
 
 
-@pytest.mark.parametrize("block_bytes", [16, 48, 256, 4096])
+@pytest.mark.parametrize("block_bytes", [16, 32, 48, 256, 4096])
 def test_cumulative_signatures(cuda, block_bytes):
     """as_sig_prefix_offsets / as_sig_prefixes against the oracle's definition:
     the layout (an exclusive scan of max(1, ceil(len / B))) and every prefix
