@@ -1762,7 +1762,9 @@ static bool part_layout(uint64_t m, uint64_t n, float lf, uint32_t pbits, uint64
     return false;
   const uint64_t P = 1ull << pbits;
   // each partition's table is a power of two >= max(64, rows / lf), so below 2 rows / lf + 64
-  const uint64_t sm = (uint64_t)(2.0 * (double)m / (double)lf) + 64 * P + P;
+  const double want = 2.0 * (double)m / (double)lf;
+  if (want > (double)(1ull << 40)) return false;                     // the one-table join's limit too
+  const uint64_t sm = (uint64_t)want + 64 * P + P;
   *slots_max = sm;
   *bytes = round256(m * 8) + round256(n * 8) + round256(m * 16) + round256(n * 16) + 7 * round256((P + 1) * 8) +
            round256(sm * 16) + 512;
