@@ -99,29 +99,36 @@ def test_batch_subset_of_pool(cuda, batch):
 def test_batch_contiguous_run_and_gapped_run(cuda, batch):
     """Joins whose rows form one run of the relations (starting mid-pool) take the
     single-relation signature kernel; the same joins with one left out (a gap in
-    the rows) take the batch walk.  Both give every join the oracle's pairs."""
+    the rows) take the batch walk; with a gap in S's rows only, R takes the
+    single-relation kernel and S the walk.  Every join gets the oracle's pairs."""
     ag = cuda
     Rd, Sd = dev(ag, batch.R), dev(ag, batch.S)
     R = ag.DeviceRelation(Rd.arena, Rd.off, None)
     S = ag.DeviceRelation(Sd.arena, Sd.off, None)
     run = list(range(3, 10))
-    for order, contiguous in ((run, True), (run[:3] + run[4:], False)):
-        ranges = [batch.ranges[j] for j in order]
-        caps = [max(64, 2 * batch.expected[j] + 64) for j in order]
+    mixed = [batch.ranges[j] for j in run]
+    r0, r1, s0, s1 = mixed[3]
+    mixed[3] = (r0, r1, min(s0 + 5, s1), s1)          # R rows still one run, S rows with a gap
+    cases = (([batch.ranges[j] for j in run], "both"), ([batch.ranges[j] for j in run[:3] + run[4:]], "neither"),
+             (mixed, "R only"))
+    for ranges, kind in cases:
+        caps = [max(64, 2 * len(oracle.join_simple(
+            workloads.relation_from_keys([batch.R.key(i) for i in range(rb, re_)]),
+            workloads.relation_from_keys([batch.S.key(i) for i in range(sb, se)]))) + 64)
+            for rb, re_, sb, se in ranges]
         descs = ag.make_descs(ranges, caps)
         ws = ag.alloc_ws(ag.join_batch_ws_bytes(descs, R.n, S.n, 0.5))
         b = ag.join_batch_prepare(descs, R, S, ws, 0.5)
-        if contiguous:
-            assert (b.r_first, b.s_first) == (ranges[0][0], ranges[0][2])
-        else:
-            assert (b.r_first, b.s_first) == (ag.ROWS_SCATTERED, ag.ROWS_SCATTERED)
+        want_r = ranges[0][0] if kind in ("both", "R only") else ag.ROWS_SCATTERED
+        want_s = ranges[0][2] if kind == "both" else ag.ROWS_SCATTERED
+        assert (b.r_first, b.s_first) == (want_r, want_s), kind
         out = ag.join_batch(R, S, ranges, caps, load_factor=0.5)
         for k, (rb, re_, sb, se) in enumerate(ranges):
             Rj = workloads.relation_from_keys([batch.R.key(i) for i in range(rb, re_)])
             Sj = workloads.relation_from_keys([batch.S.key(i) for i in range(sb, se)])
             want = oracle.join_simple(Rj, Sj)
             got = oracle.sort_pairs(out[k].cpu().numpy().view(np.uint32))
-            assert np.array_equal(got, want), (contiguous, k)
+            assert np.array_equal(got, want), (kind, k)
 
 
 def test_batch_single_join_equals_join(cuda, batch):
