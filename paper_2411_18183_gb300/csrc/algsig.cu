@@ -849,6 +849,16 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         const uint32_t rj = __shfl_sync(kFull, row, j);
         const uint32_t lj = __shfl_sync(kFull, l32, j);   // the slot holds the same length
         const uint64_t stj = __shfl_sync(kFull, start, j);
+        if (cm) {                                    // the next candidate's S bytes and R offset, ahead
+          const int j2 = __ffs(cm) - 1;
+          const uint64_t st2 = __shfl_sync(kFull, start, j2);
+          const uint32_t l2 = __shfl_sync(kFull, l32, j2);
+          const uint32_t r2 = __shfl_sync(kFull, row, j2);
+          const uint64_t o = 32u * (uint64_t)lane;   // one 32-byte sector per lane, the first 1 KB
+          if (o < (uint64_t)l2)                     // addresses inside the key only
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(P.arenaS + st2 + o));
+          if (lane == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(P.offR + r2));
+        }
         const uint64_t rs = __ldg(P.offR + rj);
         const bool verify = batch || P.mode != AS_JOIN_SIG_ONLY;   // signature-only: no byte comparison
         bool eq;
