@@ -1062,6 +1062,17 @@ __global__ void __launch_bounds__(kVThreads, 4) bl_verify_kernel(BVerifyParams P
         const uint64_t lj = __shfl_sync(kFull, len, j);
         const uint64_t sj = __shfl_sync(kFull, start, j);
         const uint64_t rsj = __shfl_sync(kFull, rs, j);
+        if (cm) {                                    // the next candidate's S and R bytes, ahead (as the
+          const int j2 = __ffs(cm) - 1;              // signature join's probe does for S)
+          const uint64_t l2 = __shfl_sync(kFull, len, j2);
+          const uint64_t s2 = __shfl_sync(kFull, start, j2);
+          const uint64_t r2 = __shfl_sync(kFull, rs, j2);
+          const uint64_t o = 32u * (uint64_t)lane;
+          if (o < l2) {
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(P.arenaS + s2 + o));
+            asm volatile("prefetch.global.L1 [%0];" ::"l"(P.arenaR + r2 + o));
+          }
+        }
         const bool eq = lj < kNarrowLen ? warp_equal(P.arenaR + rsj, P.arenaS + sj, (uint32_t)lj, emask)
                                         : warp_equal_wide(P.arenaR, rsj, P.arenaS, sj, lj);
         if (eq) {
