@@ -691,7 +691,7 @@ def run_gpu(args):
 
 
 # revision of each kernel's code; profiles/traffic.json holds counters per revision
-KERNEL_REVS = {"sig_kernel_ws": "v3", "build_kernel": "v8", "verify_kernel": "v14"}
+KERNEL_REVS = {"sig_kernel_ws": "v3", "build_kernel": "v8", "verify_kernel": "v15"}
 KERNEL_NAMES = {"sig_R": "sig_kernel_ws", "sig_S": "sig_kernel_ws", "build": "build_kernel", "verify": "verify_kernel"}
 
 

@@ -840,6 +840,21 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
           }
           b = (b + 1) & mask;
           if (++steps > mask) live = false;
+          // a slot at an even index shares its 32-byte sector with the next one: look at that one
+          // too in this step (an L1 hit), unless this one was already a candidate
+          if (!cand && live && (b & 1u)) {
+            const ulonglong2 v2 = __ldg(reinterpret_cast<const ulonglong2*>(slots + b));
+            if (v2.y == kEmpty) {
+              live = false;
+            } else {
+              if (v2.x == sig && (uint32_t)(v2.y >> 32) == l32) {
+                cand = true;
+                row = (uint32_t)v2.y;
+              }
+              b = (b + 1) & mask;
+              if (++steps > mask) live = false;
+            }
+          }
         }
       }
       uint32_t cm = __ballot_sync(kFull, cand);
