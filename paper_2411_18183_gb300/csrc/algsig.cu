@@ -1055,19 +1055,23 @@ __global__ void __launch_bounds__(kVThreads, 4) bl_verify_kernel(BVerifyParams P
       bool cand = false;
       uint32_t row = 0;
       uint64_t rs = 0;
-      if (live) {
+      // a tag miss (tagged slots) moves on to the next slot of the same 32-byte sector in the same step,
+      // as the signature join's probe does with its 16-byte slots
+      while (live) {
         const uint64_t v = __ldg(P.slots + b);
         if (v == kEmpty) {
           live = false;
-        } else {
-          row = (uint32_t)v;
-          if (!P.tagged || (uint32_t)(v >> 32) == (uint32_t)(h >> 32)) {
-            rs = __ldg(P.offR + row);                 // every visited slot: length check
-            cand = __ldg(P.offR + row + 1) - rs == len;
-          }
-          b = (b + 1) & P.mask;
-          if (++steps > P.mask) live = false;
+          break;
         }
+        row = (uint32_t)v;
+        const bool tag_ok = !P.tagged || (uint32_t)(v >> 32) == (uint32_t)(h >> 32);
+        if (tag_ok) {
+          rs = __ldg(P.offR + row);                   // every visited slot: length check
+          cand = __ldg(P.offR + row + 1) - rs == len;
+        }
+        b = (b + 1) & P.mask;
+        if (++steps > P.mask) live = false;
+        if (tag_ok || (b & 3u) == 0) break;
       }
       uint32_t cm = __ballot_sync(kFull, cand);
       while (cm) {                                   // full byte comparison, whole warp
