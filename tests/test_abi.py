@@ -56,3 +56,46 @@ def test_argument_errors_before_any_device_work(lib):
     import paper_2411_18183_gb300 as ag
     t = ag.Table()
     assert lib.as_join_build(base, 64, base, base, None, 4, None, ctypes.c_float(2.0), ctypes.byref(t), None) == 1
+
+
+def r256(x):
+    return (x + 255) // 256 * 256
+
+
+def test_partitioned_and_prefix_workspace_queries(lib):
+    """Workspace sizes of the partitioned and prefix joins are host arithmetic:
+    they follow the documented layouts, reject what the calls would reject, and
+    the automatic partition count keeps about 1024 R rows per partition."""
+    import paper_2411_18183_gb300 as ag
+    m, n, lf = 100_000, 400_000, 0.5
+    # prefix join: the one-table join's slots, R's and S's signatures, flags and counter
+    assert ag.join_prefix_ws_bytes(m, n, lf) == 262144 * 16 + r256(m * 8) + r256(n * 8) + 512
+    assert ag.join_prefix_ws_bytes(m, n, 0.0) == 0
+    # partitioned join: signatures, entries, 7 per-partition arrays, slots (< 2 m / lf + 65 per partition)
+    for bits in (0, 4, 12):
+        P = 1 << bits
+        slots = int(2.0 * m / lf) + 64 * P + P
+        want = (r256(m * 8) + r256(n * 8) + r256(m * 16) + r256(n * 16) + 7 * r256((P + 1) * 8)
+                + r256(slots * 16) + 512)
+        assert ag.join_part_ws_bytes(m, n, lf, bits) == want, bits
+    assert ag.join_part_ws_bytes(m, n, lf, 13) == 0
+    assert ag.join_part_ws_bytes(m, n, 1e-9) == 0                      # beyond 2^40 slots
+    assert ag.join_part_ws_bytes(2 ** 32, n, lf) == 0
+    # automatic bits: the smallest b with m >> (b + 10) == 0 (at most 12)
+    for mm, bits in ((1000, 0), (1024, 1), (100_000, 7), (10 ** 9, 12)):
+        assert ag.join_part_ws_bytes(mm, 10, lf) == ag.join_part_ws_bytes(mm, 10, lf, bits), mm
+
+
+def test_new_join_argument_errors_before_any_device_work(lib):
+    import paper_2411_18183_gb300 as ag
+    buf = (ctypes.c_uint8 * 64)()
+    base = (ctypes.addressof(buf) + 15) // 16 * 16
+    # misaligned arena, null pointers, oversize prefix: rejected on the host
+    assert lib.as_join_prefix(base + 1, base, None, 1, base, base, None, 1, 16, ctypes.c_float(0.5), base, 64,
+                              base, 1, None, None, None) == 1
+    assert lib.as_join_prefix(base, base, None, 1, base, base, None, 1, 2 ** 40, ctypes.c_float(0.5), base, 64,
+                              base, 1, None, None, None) == 1
+    assert lib.as_join_partitioned(None, None, None, 5, base, base, None, 1, ctypes.c_float(0.5), ag.PART_BITS_AUTO,
+                                   base, 64, base, 1, None, None, None) == 1
+    assert lib.as_join_partitioned(base, base, None, 1, base, base, None, 1, ctypes.c_float(0.5), 13, base, 64,
+                                   base, 1, None, None, None) == 1
