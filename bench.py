@@ -191,6 +191,7 @@ def run_reference(args):
 BATCH_SCALE = 100        # batch leg: the 512-join batch with relation sizes / 100
 SERVE_SCALE = 50         # serving leg: request relation sizes / 50
 SERVE_SECONDS = 2.0
+LOAD_FACTORS = (0.5, 0.35, 0.25)   # candidates of the single join's load-factor tuning
 
 
 def batch_leg(ag, steps: int):
@@ -364,12 +365,8 @@ def run_gpu(args):
     hR, hS = host_rel(wl.R), host_rel(wl.S)
     dR = ag.DeviceRelation(hR[0].cuda(), hR[1].cuda(), hR[2].cuda())
     dS = ag.DeviceRelation(hS[0].cuda(), hS[1].cuda(), hS[2].cuda())
-    lf = args.load_factor
-    ws = ag.alloc_ws(ag.join_ws_bytes(m, n, lf))
-    tb = ag.join_table_bytes(m, lf)
     cap = int(max(1024, wl.expected_pairs() * 1.25 + 1024))
     pairs = torch.empty(2 * cap, dtype=torch.int32, device="cuda")
-    count = ws[tb:tb + 8].view(torch.int64)
     sigR = torch.empty(m, dtype=torch.int64, device="cuda")
     sigS = torch.empty(n, dtype=torch.int64, device="cuda")
     stream = torch.cuda.current_stream()
@@ -379,21 +376,51 @@ def run_gpu(args):
     PH = ("sig_R", "build", "sig_S", "verify")
     ev = [[torch.cuda.Event(enable_timing=True) for _ in range(len(PH) + 1)] for _ in range(args.steps)]
 
-    def step(evs=None):
-        if evs:
-            evs[0].record(stream)
-        ag.sig_compute(dR, sigR, stream=stream)
-        if evs:
-            evs[1].record(stream)
-        t = ag.join_build(dR, ws[:tb], lf, sigR=sigR, stream=stream)
-        if evs:
-            evs[2].record(stream)
-        ag.sig_compute(dS, sigS, stream=stream)
-        if evs:
-            evs[3].record(stream)
-        ag.join_probe_sigs(t, dS, sigS, pairs, count, sync=False, stream=stream)
-        if evs:
-            evs[4].record(stream)
+    def make_step(lf):
+        ws = ag.alloc_ws(ag.join_ws_bytes(m, n, lf))
+        tb = ag.join_table_bytes(m, lf)
+        count = ws[tb:tb + 8].view(torch.int64)
+
+        def step(evs=None):
+            if evs:
+                evs[0].record(stream)
+            ag.sig_compute(dR, sigR, stream=stream)
+            if evs:
+                evs[1].record(stream)
+            t = ag.join_build(dR, ws[:tb], lf, sigR=sigR, stream=stream)
+            if evs:
+                evs[2].record(stream)
+            ag.sig_compute(dS, sigS, stream=stream)
+            if evs:
+                evs[3].record(stream)
+            ag.join_probe_sigs(t, dS, sigS, pairs, count, sync=False, stream=stream)
+            if evs:
+                evs[4].record(stream)
+        return step, ws, tb, count
+
+    # the table's load factor: given, or the fastest of a few, each timed over two
+    # joins before the timed region (the batch leg tunes its own the same way)
+    lf_tuning = {}
+    if args.load_factor is None:
+        best = None
+        for cand in LOAD_FACTORS:
+            cstep, cws, _, _ = make_step(cand)
+            cstep()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                cstep()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            lf_tuning[str(cand)] = e0.elapsed_time(e1) / 2
+            if best is None or lf_tuning[str(cand)] < lf_tuning[str(best)]:
+                best = cand
+            del cstep, cws
+        lf = best
+    else:
+        lf = args.load_factor
+    step, ws, tb, count = make_step(lf)
 
     # correctness of the timed configuration: total pairs = the generator's ground truth
     step()
@@ -657,6 +684,7 @@ def run_gpu(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": workload_desc(args.workload, spec), "load_factor": lf,
+                   "load_factor_tuning_ms": lf_tuning or None,
                    "l2": f"inputs larger than L2 ({key_bytes / 1e9:.2f} GB of keys), no flush",
                    "parallelism": f"replicas{world}"},
         "p50_ms": pct(step_ms, 50), "p99_ms": pct(step_ms, 99),
@@ -701,7 +729,9 @@ def main():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--workload", default="large", choices=sorted(workloads.CONFIGS))
-    ap.add_argument("--load-factor", type=float, default=0.5)
+    ap.add_argument("--load-factor", type=float, default=None,
+                    help="table load factor; default: the fastest of %s, tuned before the timed steps" %
+                         (LOAD_FACTORS,))
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline leg")
     ap.add_argument("--no-extra", action="store_true", help="skip the batch and serving legs")
