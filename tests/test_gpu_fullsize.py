@@ -32,15 +32,16 @@ def test_full_size_sampled_parity(cuda, name):
     want_sig = oracle.sig_batch(sample.arena, sample.off, nthreads=8)
     assert np.array_equal(got_sig, want_sig)
 
-    # the whole join as bench.py runs it (load factor 0.5)
-    ws = ag.alloc_ws(ag.join_ws_bytes(R.n, S.n, 0.5))
+    # the whole join as bench.py runs it, at each load factor its tuning picks from
+    want_sample = oracle.join_simple(wl.R, sample)
     cap = wl.expected_pairs() + 4096
     pairs = torch.empty(2 * cap, dtype=torch.int32, device="cuda")
     count = torch.zeros(1, dtype=torch.int64, device="cuda")
-    _, cnt = ag.join_into(R, S, ws, pairs, count, 0.5, sync=True)
-    assert cnt == wl.expected_pairs()
-    got = pairs[: 2 * cnt].cpu().numpy().view(np.uint32).reshape(-1, 2)
-    keep = np.isin(got[:, 1], wl.S.ids[rows])
-    got_sample = oracle.sort_pairs(got[keep])
-    want_sample = oracle.join_simple(wl.R, sample)
-    assert np.array_equal(got_sample, want_sample)
+    for lf in (0.5, 0.35, 0.25):
+        ws = ag.alloc_ws(ag.join_ws_bytes(R.n, S.n, lf))
+        _, cnt = ag.join_into(R, S, ws, pairs, count, lf, sync=True)
+        assert cnt == wl.expected_pairs(), lf
+        got = pairs[: 2 * cnt].cpu().numpy().view(np.uint32).reshape(-1, 2)
+        keep = np.isin(got[:, 1], wl.S.ids[rows])
+        assert np.array_equal(oracle.sort_pairs(got[keep]), want_sample), lf
+        del ws
