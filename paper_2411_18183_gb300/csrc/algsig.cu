@@ -438,6 +438,12 @@ __global__ void __launch_bounds__(kWSThreads, 1) sig_kernel_ws(const uint8_t* __
   }
 }
 
+}  // namespace algsig
+
+#include "sigkey.cuh"
+
+namespace algsig {
+
 // first actual key of join j whose start lies at or after virtual byte t
 // (t inside join j's byte range), as a virtual row
 template <bool S_SIDE>
@@ -1227,6 +1233,13 @@ static as_status ensure_device(DeviceState** out) {
       for (const void* f : wfns)
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWS)) != cudaSuccess)
           return cuda_fail(e, "kernel attribute");
+      const void* kfns[4] = {reinterpret_cast<const void*>(sig_key_kernel<false, 4>),
+                             reinterpret_cast<const void*>(sig_key_kernel<true, 4>),
+                             reinterpret_cast<const void*>(sig_key_kernel<false, 2>),
+                             reinterpret_cast<const void*>(sig_key_kernel<true, 2>)};
+      for (const void* f : kfns)
+        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLK)) != cudaSuccess)
+          return cuda_fail(e, "kernel attribute");
     }
     // where dynamic shared memory starts (the tables are its first bytes)
     if ((e = cudaFuncSetAttribute(dyn_smem_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
@@ -1309,14 +1322,14 @@ static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t 
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
   if (n == 0) return AS_OK;
-  const uint64_t want = (n + 64ull * kWSPairs - 1) / (64ull * kWSPairs);
+  const uint64_t want = (n + 32ull * kLKWarps - 1) / (32ull * kLKWarps);
   const unsigned blocks = (unsigned)(want < (uint64_t)d->sms ? (want < 1 ? 1 : want) : (uint64_t)d->sms);
   if (ncomp == 2) {
-    if (d->tables_at400) sig_kernel_ws<true, 2><<<blocks, kWSThreads, kSmemWS, s>>>(arena, off, n, out);
-    else sig_kernel_ws<false, 2><<<blocks, kWSThreads, kSmemWS, s>>>(arena, off, n, out);
+    if (d->tables_at400) sig_key_kernel<true, 2><<<blocks, kLKThreads, kSmemLK, s>>>(arena, off, n, out);
+    else sig_key_kernel<false, 2><<<blocks, kLKThreads, kSmemLK, s>>>(arena, off, n, out);
   } else {
-    if (d->tables_at400) sig_kernel_ws<true, 4><<<blocks, kWSThreads, kSmemWS, s>>>(arena, off, n, out);
-    else sig_kernel_ws<false, 4><<<blocks, kWSThreads, kSmemWS, s>>>(arena, off, n, out);
+    if (d->tables_at400) sig_key_kernel<true, 4><<<blocks, kLKThreads, kSmemLK, s>>>(arena, off, n, out);
+    else sig_key_kernel<false, 4><<<blocks, kLKThreads, kSmemLK, s>>>(arena, off, n, out);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "signature kernel launch");

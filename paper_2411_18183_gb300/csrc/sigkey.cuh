@@ -1,0 +1,406 @@
+// sigkey.cuh -- the signature kernel: one key per lane, keys grouped by
+// length, components 1, 2 and 4 from a bit-sliced GF(2) Horner state.
+//
+// Arithmetic (Section 3.1: sig^k = sum_i p_i x^(k i), k = 1..4).  A key is
+// read as 32-bit words v_t = p_{2t} | p_{2t+1} << 16 of its realigned stream
+// (shifted by one byte when the key starts at an odd byte, so that symbols
+// sit on 16-bit boundaries; word 0 starts at the key's first 32-byte block).
+// Bit b of v_t is bit b of symbol 2t (b < 16) or bit b-16 of symbol 2t+1.
+// For each of the 32 bit positions b ("planes") let
+//     D_b(y) = sum_t bit_b(v_t) y^t,   a polynomial over GF(2).
+// Then, with weights W_k(b) = x^b (b < 16) and x^(b - 16 + k) (b >= 16),
+//     sig^k = sum_b W_k(b) D_b(x^(2k)).
+// For k = 1, 2, 4 the exponent 2k is a power of two, and evaluating a GF(2)
+// polynomial commutes with squaring (Frobenius): D_b(x^(2k)) = D_b(x)^(2k).
+// So the 32 field elements S_b = D_b(x) determine components 1, 2 and 4.
+// They are kept transposed ("bit-sliced"): register c_m holds, in bit b,
+// coefficient m of S_b.  Horner's rule over the words, from the last to the
+// first, S <- S * x + v_t, is then a fixed XOR network on the 16 registers
+// (multiplication by x shifts the registers and folds c_15 back through
+// x^16 = x^12 + x^3 + x + 1), 12 logic operations per 16 bytes for all 32
+// planes at once.  At the end of the key,
+//     sig^k = sum_m x^(2 k m) (lo16(c_m) + x^k hi16(c_m))   (mod P),
+// since S_b^(2k) = sum_m c_m[b] x^(2 k m).  Component 3 (2k = 6 is not a power
+// of two) keeps the table-driven delayed-reduction Horner step of gf16.cuh.
+//
+// Scheduling.  Each warp owns a byte-balanced range of keys and walks it in
+// windows of kLKWin keys.  A window's keys are sorted by length, and the warp
+// computes them in groups of 32 consecutive sorted keys, one key per lane, so
+// the lanes of a group have (nearly) the same amount of work.  A lane streams
+// its key from global memory in 32-byte blocks (one 256-bit load per block,
+// read-only path, no L1 allocation: every DRAM sector is fetched once), from
+// the key's last block to its first, kLKDepth blocks ahead of the arithmetic
+// in registers.  Lanes of a group whose keys are shorter start later, so all
+// lanes reach their first block in the group's last iteration and finish the
+// signatures together.  (Staging the keys through shared memory was measured
+// slower: per-lane 16-byte copies fetch each 32-byte sector twice, and a TMA
+// bulk copy per lane is serialised because its operands are warp-uniform.)
+#pragma once
+#include <cstdint>
+
+namespace algsig {
+
+#ifndef ALGSIG_LK_WARPS
+#define ALGSIG_LK_WARPS 20
+#endif
+#ifndef ALGSIG_LK_FINISH
+#define ALGSIG_LK_FINISH __forceinline__
+#endif
+#ifndef ALGSIG_LK_DEPTH
+#define ALGSIG_LK_DEPTH 2
+#endif
+constexpr int kLKWarps = ALGSIG_LK_WARPS;             // warps per block (one block per SM)
+constexpr int kLKThreads = 32 * kLKWarps;
+constexpr int kLKDepth = ALGSIG_LK_DEPTH;             // 32-byte blocks in flight per lane
+constexpr int kLKWin = 256;                           // keys per sorting window
+constexpr uint32_t kLKNoKey = 0xFFFFFFFFu;            // empty sorting entry
+
+struct LKWarp {
+  uint64_t woff[kLKWin + 2];       // offsets of the window's keys (woff[i] = off[wb + i]), i <= wn
+  uint32_t order[kLKWin];          // window entries sorted by (block count << 8 | index)
+};
+constexpr size_t kSmemLKMasks = 1056;                 // 33 rows of 32 bytes
+constexpr size_t kSmemLK = (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)kLKWarps * sizeof(LKWarp);
+static_assert(kSmemLK <= 232448, "lane-per-key signature kernel: shared memory");
+
+__device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+
+// One 32-byte block of key bytes.
+struct Blk {
+  uint32_t w[8];
+};
+
+// 32 bytes at the 32-byte aligned address p, read-only path without L1
+// allocation.  Bytes outside [lim_lo, lim_hi) (the arena's readable range) are
+// not read and come back as zero; they never hold key bytes.
+__device__ __forceinline__ Blk ld_blk(const uint8_t* p, const uint8_t* lim_lo, const uint8_t* lim_hi) {
+  Blk b;
+  if (p >= lim_lo && p + 32 <= lim_hi) {
+    asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(b.w[0]), "=r"(b.w[1]), "=r"(b.w[2]), "=r"(b.w[3]), "=r"(b.w[4]), "=r"(b.w[5]),
+                   "=r"(b.w[6]), "=r"(b.w[7])
+                 : "l"(p));
+  } else {                                          // a block at the arena's first or last 16 bytes
+#pragma unroll
+    for (int i = 0; i < 8; i++) b.w[i] = 0;
+    if (p >= lim_lo && p + 16 <= lim_hi) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+      b.w[0] = v.x; b.w[1] = v.y; b.w[2] = v.z; b.w[3] = v.w;
+    }
+    if (p + 16 >= lim_lo && p + 32 <= lim_hi) {
+      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p + 16));
+      b.w[4] = v.x; b.w[5] = v.y; b.w[6] = v.z; b.w[7] = v.w;
+    }
+  }
+  return b;
+}
+
+// Bit-sliced Horner step over one 16-byte chunk (words v0..v3, v3 last in the
+// key): S <- S x^4 + v3 x^3 + v2 x^2 + v1 x + v0, with x^16 = x^12 + x^3 + x + 1.
+__device__ __forceinline__ void xs_chunk(uint32_t (&c)[16], uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3) {
+  const uint32_t n0 = c[12] ^ v0;
+  const uint32_t n1 = c[12] ^ c[13] ^ v1;
+  const uint32_t n2 = c[13] ^ c[14] ^ v2;
+  const uint32_t n3 = c[12] ^ c[14] ^ c[15] ^ v3;
+  const uint32_t n4 = c[0] ^ c[13] ^ c[15];
+  const uint32_t n5 = c[1] ^ c[14];
+  const uint32_t n6 = c[2] ^ c[15];
+  const uint32_t n12 = c[8] ^ c[12];
+  const uint32_t n13 = c[9] ^ c[13];
+  const uint32_t n14 = c[10] ^ c[14];
+  const uint32_t n15 = c[11] ^ c[15];
+  c[15] = n15; c[14] = n14; c[13] = n13; c[12] = n12;
+  c[11] = c[7]; c[10] = c[6]; c[9] = c[5]; c[8] = c[4]; c[7] = c[3];
+  c[6] = n6; c[5] = n5; c[4] = n4; c[3] = n3; c[2] = n2; c[1] = n1; c[0] = n0;
+}
+
+// Component K (1, 2 or 4) from the bit-sliced state:
+//   sum_m x^(2 K m) (lo16(c_m) + x^K hi16(c_m)) mod P,
+// by Horner over m with a 32-bit accumulator reduced every 8/K steps.
+template <int K, class Cursor>
+__device__ __forceinline__ uint32_t xs_component(const uint32_t (&c)[16], const Cursor& rc) {
+  constexpr int kEvery = 8 / K;
+  uint32_t acc = 0;
+#pragma unroll
+  for (int m = 15; m >= 0; --m) {
+    acc = (acc << (2 * K)) ^ (c[m] & 0xFFFFu) ^ ((c[m] >> 16) << K);
+    if ((16 - m) % kEvery == 0) acc = red32(acc, rc);
+  }
+  return acc;
+}
+
+// Component 3's Horner step over one realigned chunk (delayed reduction; see
+// horner_chunk in gf16.cuh): a3 <- a3 x^24 + sum_j q_j x^(3 j).
+template <class Cursor>
+__device__ __forceinline__ uint32_t c3_chunk(uint32_t a3, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
+                                             const Cursor& rc) {
+  const uint32_t h0 = __umulhi(v0, rc.k16), l0 = h0 * rc.nk16 + v0;
+  const uint32_t h1 = __umulhi(v1, rc.k16), l1 = h1 * rc.nk16 + v1;
+  const uint32_t h2 = __umulhi(v2, rc.k16), l2 = h2 * rc.nk16 + v2;
+  const uint32_t h3 = __umulhi(v3, rc.k16), l3 = h3 * rc.nk16 + v3;
+  uint32_t u = (a3 << 12) ^ l2 ^ (h2 << 3) ^ (l3 << 6) ^ (h3 << 9);
+  a3 = red32(u, rc);
+  u = (a3 << 12) ^ l0 ^ (h0 << 3) ^ (l1 << 6) ^ (h1 << 9);
+  return red32(u, rc);
+}
+
+// x^-m * v in GF(2^16) for 0 <= m <= 60; inv32: the multiply table of x^-32
+template <class Cursor>
+__device__ __forceinline__ uint32_t mul_xinv(const uint16_t* inv32, uint32_t v, uint32_t m, const Cursor& rc) {
+  if (m >= 32) {
+    v = mulc(inv32, v);
+    m -= 32;
+  }
+  const uint32_t d = mulc(inv32, v);                     // v x^-32
+  const uint64_t E = (uint64_t)d << (32 - m);            // v x^-32 x^(32-m), < 2^48
+  const uint32_t r1 = red32((uint32_t)(E >> 16), rc);
+  return red32(((uint32_t)E & 0xFFFFu) ^ (r1 << 16), rc);
+}
+
+// A lane's key in the current group.
+struct LKKey {
+  uint64_t kq;          // key index
+  const uint8_t* base;  // 32-byte aligned address of the key's first block
+  uint32_t nb;          // realigned 32-byte blocks (0: empty key)
+  uint32_t a;           // offset of the key's first byte in its first block (0..31)
+  uint32_t tail;        // bytes of the last aligned block that belong to the key, counted from its start
+  bool valid;
+};
+
+// prefetch the offsets of the window starting at key wb (cp.async, one group)
+__device__ __forceinline__ void lk_prefetch_window(LKWarp& W, const uint64_t* __restrict__ off, uint64_t wb,
+                                                   uint64_t k_hi) {
+  const uint32_t lane = threadIdx.x & 31u;
+  if (wb < k_hi) {
+    const uint64_t left = k_hi - wb;
+    const uint32_t wn = left < (uint64_t)kLKWin ? (uint32_t)left : (uint32_t)kLKWin;
+    for (uint32_t e = lane; e <= wn; e += 32) cp_async8(&W.woff[e], off + wb + e);
+  }
+  cp_async_commit();
+}
+
+// realigned 32-byte blocks of the key at absolute address abs
+__device__ __forceinline__ uint32_t lk_blocks(uintptr_t abs, uint64_t len) {
+  if (len == 0) return 0u;
+  const uint64_t lo = (abs & 31u) & ~1ull;
+  const uint64_t nb = (lo + len + 31) >> 5;
+  return nb < 0xFFFFFFFFull ? (uint32_t)nb : 0xFFFFFFFFu;
+}
+
+// sort the window's entries by block count (bitonic network over kLKWin entries)
+__device__ __forceinline__ void lk_sort_window(LKWarp& W, uint32_t wn, uintptr_t arena) {
+  const uint32_t lane = threadIdx.x & 31u;
+  for (uint32_t i = lane; i < (uint32_t)kLKWin; i += 32) {
+    uint32_t e = kLKNoKey;
+    if (i < wn) {
+      const uint64_t ks = W.woff[i], len = W.woff[i + 1] - ks;
+      const uint32_t nb = lk_blocks(arena + ks, len);
+      e = ((nb < 0x7FFFFFu ? nb : 0x7FFFFFu) << 8) | i;
+    }
+    W.order[i] = e;
+  }
+  __syncwarp();
+  for (uint32_t k = 2; k <= (uint32_t)kLKWin; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t t = lane; t < (uint32_t)kLKWin / 2; t += 32) {
+        const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
+        const uint32_t p = i + j;
+        const uint32_t a = W.order[i], b = W.order[p];
+        const bool up = (i & k) == 0;
+        if ((a > b) == up) {
+          W.order[i] = b;
+          W.order[p] = a;
+        }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+// group g of the window (wb: its first key) into the lanes; returns the
+// group's iteration count (its longest key's blocks, at least 1)
+__device__ __forceinline__ uint32_t lk_load_group(LKKey& k, const LKWarp& W, uint64_t wb, uint32_t g,
+                                                  const uint8_t* arena) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t e = W.order[32 * g + lane];
+  k.valid = e != kLKNoKey;
+  k.kq = 0; k.base = arena; k.nb = 0; k.a = 0; k.tail = 0;
+  if (k.valid) {
+    const uint32_t i = e & 0xFFu;
+    const uint64_t ks = W.woff[i], len = W.woff[i + 1] - ks;
+    const uintptr_t abs = reinterpret_cast<uintptr_t>(arena) + ks;
+    k.kq = wb + i;
+    k.base = reinterpret_cast<const uint8_t*>(abs & ~(uintptr_t)31);
+    k.a = (uint32_t)(abs & 31u);
+    k.nb = lk_blocks(abs, len);
+    if (k.nb) k.tail = (uint32_t)((uint64_t)k.a + len - 32ull * (k.nb - 1));
+  }
+  const uint32_t G = __reduce_max_sync(kFull, k.nb);
+  return G < 1u ? 1u : G;
+}
+
+// Byte masks of a 32-byte block in shared memory: row e (0..32) keeps bytes
+// [0, e).  Masking a block is two 16-byte loads and eight logic operations.
+constexpr int kLKMaskRows = 33;
+__device__ __forceinline__ void lk_fill_masks(uint4* mt) {
+  for (int i = threadIdx.x; i < kLKMaskRows * 2; i += blockDim.x) {
+    const int e = i >> 1, h = i & 1;
+    uint32_t m[4];
+#pragma unroll
+    for (int j = 0; j < 4; j++) {
+      const int r = e - 16 * h - 4 * j;
+      m[j] = r <= 0 ? 0u : (r >= 4 ? ~0u : ((1u << (8 * r)) - 1u));
+    }
+    mt[i] = make_uint4(m[0], m[1], m[2], m[3]);
+  }
+}
+// keep bytes [0, e) of a block (e >= 32 keeps all)
+__device__ __forceinline__ void blk_keep_below(Blk& b, uint32_t e, const uint4* mt) {
+  const uint32_t r = e < 32u ? e : 32u;
+  const uint4 m0 = mt[2 * r], m1 = mt[2 * r + 1];
+  b.w[0] &= m0.x; b.w[1] &= m0.y; b.w[2] &= m0.z; b.w[3] &= m0.w;
+  b.w[4] &= m1.x; b.w[5] &= m1.y; b.w[6] &= m1.z; b.w[7] &= m1.w;
+}
+// zero bytes [0, a) of a block (a < 32)
+__device__ __forceinline__ void blk_zero_below(Blk& b, uint32_t a, const uint4* mt) {
+  const uint4 m0 = mt[2 * a], m1 = mt[2 * a + 1];
+  b.w[0] &= ~m0.x; b.w[1] &= ~m0.y; b.w[2] &= ~m0.z; b.w[3] &= ~m0.w;
+  b.w[4] &= ~m1.x; b.w[5] &= ~m1.y; b.w[6] &= ~m1.z; b.w[7] &= ~m1.w;
+}
+
+// the Horner steps of one 32-byte block (its two chunks, the upper one first)
+template <int NCOMP, class Cursor>
+__device__ __forceinline__ void lk_block(const Blk& w, uint32_t sh, uint32_t& nxt0, uint32_t (&c)[16], uint32_t& a3,
+                                         const Cursor& rc) {
+  uint32_t v[8];
+#pragma unroll
+  for (int i = 0; i < 7; i++) v[i] = __funnelshift_r(w.w[i], w.w[i + 1], sh);
+  v[7] = __funnelshift_r(w.w[7], nxt0, sh);
+  nxt0 = w.w[0];
+  xs_chunk(c, v[4], v[5], v[6], v[7]);
+  xs_chunk(c, v[0], v[1], v[2], v[3]);
+  if constexpr (NCOMP == 4) {
+    a3 = c3_chunk(a3, v[4], v[5], v[6], v[7], rc);
+    a3 = c3_chunk(a3, v[0], v[1], v[2], v[3], rc);
+  }
+}
+
+// A key's signature from the Horner state of its blocks (values counted from
+// the first block's start; the key starts s = (a & ~1) / 2 symbols later).
+template <int NCOMP, class Cursor>
+__device__ ALGSIG_LK_FINISH uint64_t lk_finish(const uint32_t (&c)[16], uint32_t a3, uint32_t a, const uint16_t* inv32,
+                                              const Cursor& rc) {
+  const uint32_t v1 = xs_component<1>(c, rc);
+  const uint32_t v2 = xs_component<2>(c, rc);
+  const uint32_t s = (a & ~1u) >> 1;
+  uint64_t sig = (uint64_t)mul_xinv(inv32, v1, s, rc) | ((uint64_t)mul_xinv(inv32, v2, 2 * s, rc) << 16);
+  if constexpr (NCOMP == 4) {
+    const uint32_t v4 = xs_component<4>(c, rc);
+    sig |= ((uint64_t)mul_xinv(inv32, a3, 3 * s, rc) << 32) | ((uint64_t)mul_xinv(inv32, v4, 4 * s, rc) << 48);
+  }
+  return sig;
+}
+
+// The signatures of one group: the lane's block at iteration it is
+// vb = G - 1 - it (its own blocks are vb < nb), so the lanes of shorter keys
+// start later and all lanes reach block 0 in the group's last iteration.  An
+// odd key whose last aligned block ends with a key byte needs the next
+// block's first byte.
+template <int NCOMP, class Cursor>
+__device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8_t* lim_lo, const uint8_t* lim_hi,
+                                         const uint16_t* inv32, const uint4* mt, uint64_t* __restrict__ sig_out,
+                                         const Cursor& rc) {
+  const uint32_t sh = 8u * (k.a & 1u);
+  uint32_t nxt0 = 0;
+  if (k.nb && k.tail > 32u) nxt0 = __ldg(reinterpret_cast<const uint32_t*>(k.base + 32ull * k.nb));
+  // kLKDepth blocks in flight: iteration it takes its block out of ring slot it % kLKDepth and
+  // refills the slot with block it + kLKDepth before computing (a ring of kLKDepth + 1 slots
+  // written in place measured slower: its loads stall longer)
+  Blk ring[kLKDepth];
+#pragma unroll
+  for (int u = 0; u < kLKDepth; ++u) {
+#pragma unroll
+    for (int i = 0; i < 8; i++) ring[u].w[i] = 0;
+    const int vb = (int)G - 1 - u;
+    if (vb >= 0 && (uint32_t)vb < k.nb) ring[u] = ld_blk(k.base + 32ull * (uint32_t)vb, lim_lo, lim_hi);
+  }
+  uint32_t c[16];
+#pragma unroll
+  for (int i = 0; i < 16; i++) c[i] = 0;
+  uint32_t a3 = 0;
+  for (uint32_t it0 = 0; it0 < G; it0 += kLKDepth) {
+#pragma unroll
+    for (int u = 0; u < kLKDepth; ++u) {
+      const uint32_t it = it0 + (uint32_t)u;
+      if (it >= G) break;
+      const uint32_t vb = G - 1 - it;
+      Blk w = ring[u];
+      if (it + kLKDepth < G) {
+        const uint32_t vb2 = vb - kLKDepth;
+        if (vb2 < k.nb) ring[u] = ld_blk(k.base + 32ull * vb2, lim_lo, lim_hi);
+      }
+      if (vb < k.nb) {
+        if (vb + 1 == k.nb) blk_keep_below(w, k.tail, mt);   // bytes after the key's end
+        if (vb == 0) blk_zero_below(w, k.a, mt);             // bytes before its start
+        lk_block<NCOMP>(w, sh, nxt0, c, a3, rc);
+      }
+    }
+  }
+  if (k.valid) sig_out[k.kq] = lk_finish<NCOMP>(c, a3, k.a, inv32, rc);
+}
+
+template <bool AT400, int NCOMP>
+__global__ void __launch_bounds__(kLKThreads, 1) sig_key_kernel(const uint8_t* __restrict__ arena,
+                                                                const uint64_t* __restrict__ off, uint64_t n,
+                                                                uint64_t* __restrict__ sig_out) {
+  extern __shared__ __align__(16) uint8_t smem[];
+  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
+  uint16_t* inv32 = reinterpret_cast<uint16_t*>(smem + kRedBytes);
+  uint4* mt = reinterpret_cast<uint4*>(smem + kRedBytes + 1024);
+  LKWarp* warps = reinterpret_cast<LKWarp*>(smem + kRedBytes + 1024 + kSmemLKMasks);
+  lk_fill_masks(mt);
+  for (int i = threadIdx.x; i < 256; i += blockDim.x)   // the x^-32 multiply table (512 entries)
+    reinterpret_cast<uint32_t*>(inv32)[i] = reinterpret_cast<const uint32_t*>(g_const + 16 * 512)[i];
+  const int wib = threadIdx.x >> 5;
+  LKWarp& W = warps[wib];
+  static_assert(sizeof(LKWarp) >= 2048, "table scratch fits warp 0's window state");
+  init_red_tables(red, reinterpret_cast<uint32_t*>(&warps[0]));   // ends with __syncthreads()
+  using Cursor = typename std::conditional<AT400, RedCursorAt400, RedCursor>::type;
+  Cursor rc;
+  if constexpr (AT400) rc = red_cursor_at400(); else rc = red_cursor(red);
+
+  const uint64_t warp = (uint64_t)blockIdx.x * kLKWarps + wib;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kLKWarps;
+  uint64_t k_lo, k_hi;
+  warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
+  if (k_lo >= k_hi) return;
+  // readable bytes of the arena: from its start to the 16-byte boundary after the last key byte
+  const uint8_t* lim_lo = arena;
+  const uint8_t* lim_hi = arena + ((off[n] + 15) & ~15ull);
+
+  lk_prefetch_window(W, off, k_lo, k_hi);
+  for (uint64_t wb = k_lo; wb < k_hi;) {
+    cp_async_wait_all();                            // the window's offsets
+    __syncwarp();
+    const uint64_t left = k_hi - wb;
+    const uint32_t wn = left < (uint64_t)kLKWin ? (uint32_t)left : (uint32_t)kLKWin;
+    lk_sort_window(W, wn, reinterpret_cast<uintptr_t>(arena));
+    const uint32_t ng = (wn + 31) / 32;
+    for (uint32_t g = 0; g < ng; ++g) {
+      LKKey k;
+      const uint32_t G = lk_load_group(k, W, wb, g, arena);
+      if (g + 1 == ng) {                            // the window's offsets are free: fetch the next ones
+        __syncwarp();
+        lk_prefetch_window(W, off, wb + wn, k_hi);
+      }
+      lk_group<NCOMP>(k, G, lim_lo, lim_hi, inv32, mt, sig_out, rc);
+    }
+    wb += wn;
+  }
+  cp_async_wait_all();
+}
+
+}  // namespace algsig
