@@ -41,19 +41,28 @@
 namespace algsig {
 
 #ifndef ALGSIG_LK_WARPS
-#define ALGSIG_LK_WARPS 20
+#define ALGSIG_LK_WARPS 24
 #endif
 #ifndef ALGSIG_LK_FINISH
 #define ALGSIG_LK_FINISH __forceinline__
+#endif
+#ifndef ALGSIG_LK_LDQUAL
+#define ALGSIG_LK_LDQUAL volatile
 #endif
 #ifndef ALGSIG_LK_DEPTH
 #define ALGSIG_LK_DEPTH 2
 #endif
 constexpr int kLKWarps = ALGSIG_LK_WARPS;             // warps per block (one block per SM)
 constexpr int kLKThreads = 32 * kLKWarps;
-constexpr int kLKDepth = ALGSIG_LK_DEPTH;             // 32-byte blocks in flight per lane
-constexpr int kLKWin = 256;                           // keys per sorting window
+constexpr int kLKDepth = ALGSIG_LK_DEPTH;             // 32-byte blocks in flight per key
+#ifndef ALGSIG_LK_WIN
+#define ALGSIG_LK_WIN 256
+#endif
+constexpr int kLKWin = ALGSIG_LK_WIN;                 // keys per sorting window (a power of two)
 constexpr uint32_t kLKNoKey = 0xFFFFFFFFu;            // empty sorting entry
+constexpr int kLKIdxBits = kLKWin == 256 ? 8 : (kLKWin == 512 ? 9 : (kLKWin == 128 ? 7 : 10));
+static_assert((1 << kLKIdxBits) == kLKWin, "window sizes 128, 256, 512, 1024");
+constexpr uint32_t kLKNbCap = (1u << (31 - kLKIdxBits)) - 1u;   // block counts above sort together
 
 struct LKWarp {
   uint64_t woff[kLKWin + 2];       // offsets of the window's keys (woff[i] = off[wb + i]), i <= wn
@@ -74,26 +83,30 @@ struct Blk {
 };
 
 // 32 bytes at the 32-byte aligned address p, read-only path without L1
-// allocation.  Bytes outside [lim_lo, lim_hi) (the arena's readable range) are
-// not read and come back as zero; they never hold key bytes.
-__device__ __forceinline__ Blk ld_blk(const uint8_t* p, const uint8_t* lim_lo, const uint8_t* lim_hi) {
+// allocation.
+__device__ __forceinline__ Blk ld_blk(const uint8_t* p) {
   Blk b;
-  if (p >= lim_lo && p + 32 <= lim_hi) {
-    asm volatile("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(b.w[0]), "=r"(b.w[1]), "=r"(b.w[2]), "=r"(b.w[3]), "=r"(b.w[4]), "=r"(b.w[5]),
-                   "=r"(b.w[6]), "=r"(b.w[7])
-                 : "l"(p));
-  } else {                                          // a block at the arena's first or last 16 bytes
+  asm ALGSIG_LK_LDQUAL("ld.global.nc.L1::no_allocate.v8.u32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(b.w[0]), "=r"(b.w[1]), "=r"(b.w[2]), "=r"(b.w[3]), "=r"(b.w[4]), "=r"(b.w[5]),
+                         "=r"(b.w[6]), "=r"(b.w[7])
+                       : "l"(p));
+  return b;
+}
+// The same with bytes outside [lim_lo, lim_hi) (the arena's readable range)
+// not read and returned as zero; they never hold key bytes.  Only keys in the
+// arena's first or last 32 bytes need it (lk_edge_key).
+__device__ __forceinline__ Blk ld_blk_checked(const uint8_t* p, const uint8_t* lim_lo, const uint8_t* lim_hi) {
+  if (p >= lim_lo && p + 32 <= lim_hi) return ld_blk(p);
+  Blk b;
 #pragma unroll
-    for (int i = 0; i < 8; i++) b.w[i] = 0;
-    if (p >= lim_lo && p + 16 <= lim_hi) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
-      b.w[0] = v.x; b.w[1] = v.y; b.w[2] = v.z; b.w[3] = v.w;
-    }
-    if (p + 16 >= lim_lo && p + 32 <= lim_hi) {
-      const uint4 v = __ldg(reinterpret_cast<const uint4*>(p + 16));
-      b.w[4] = v.x; b.w[5] = v.y; b.w[6] = v.z; b.w[7] = v.w;
-    }
+  for (int i = 0; i < 8; i++) b.w[i] = 0;
+  if (p >= lim_lo && p + 16 <= lim_hi) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p));
+    b.w[0] = v.x; b.w[1] = v.y; b.w[2] = v.z; b.w[3] = v.w;
+  }
+  if (p + 16 >= lim_lo && p + 32 <= lim_hi) {
+    const uint4 v = __ldg(reinterpret_cast<const uint4*>(p + 16));
+    b.w[4] = v.x; b.w[5] = v.y; b.w[6] = v.z; b.w[7] = v.w;
   }
   return b;
 }
@@ -168,6 +181,7 @@ struct LKKey {
   uint32_t a;           // offset of the key's first byte in its first block (0..31)
   uint32_t tail;        // bytes of the last aligned block that belong to the key, counted from its start
   bool valid;
+  bool edge;            // a block of the key reaches outside the arena's readable range
 };
 
 // prefetch the offsets of the window starting at key wb (cp.async, one group)
@@ -198,7 +212,7 @@ __device__ __forceinline__ void lk_sort_window(LKWarp& W, uint32_t wn, uintptr_t
     if (i < wn) {
       const uint64_t ks = W.woff[i], len = W.woff[i + 1] - ks;
       const uint32_t nb = lk_blocks(arena + ks, len);
-      e = ((nb < 0x7FFFFFu ? nb : 0x7FFFFFu) << 8) | i;
+      e = ((nb < kLKNbCap ? nb : kLKNbCap) << kLKIdxBits) | i;
     }
     W.order[i] = e;
   }
@@ -223,13 +237,14 @@ __device__ __forceinline__ void lk_sort_window(LKWarp& W, uint32_t wn, uintptr_t
 // group g of the window (wb: its first key) into the lanes; returns the
 // group's iteration count (its longest key's blocks, at least 1)
 __device__ __forceinline__ uint32_t lk_load_group(LKKey& k, const LKWarp& W, uint64_t wb, uint32_t g,
-                                                  const uint8_t* arena) {
+                                                  const uint8_t* arena, const uint8_t* lim_lo,
+                                                  const uint8_t* lim_hi) {
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t e = W.order[32 * g + lane];
   k.valid = e != kLKNoKey;
-  k.kq = 0; k.base = arena; k.nb = 0; k.a = 0; k.tail = 0;
+  k.kq = 0; k.base = arena; k.nb = 0; k.a = 0; k.tail = 0; k.edge = false;
   if (k.valid) {
-    const uint32_t i = e & 0xFFu;
+    const uint32_t i = e & (kLKWin - 1);
     const uint64_t ks = W.woff[i], len = W.woff[i + 1] - ks;
     const uintptr_t abs = reinterpret_cast<uintptr_t>(arena) + ks;
     k.kq = wb + i;
@@ -237,9 +252,18 @@ __device__ __forceinline__ uint32_t lk_load_group(LKKey& k, const LKWarp& W, uin
     k.a = (uint32_t)(abs & 31u);
     k.nb = lk_blocks(abs, len);
     if (k.nb) k.tail = (uint32_t)((uint64_t)k.a + len - 32ull * (k.nb - 1));
+    k.edge = k.nb && (k.base < lim_lo || k.base + 32ull * k.nb > lim_hi);
   }
-  const uint32_t G = __reduce_max_sync(kFull, k.nb);
+  // an edge key is computed apart (lk_edge_key); the group's loop skips it
+  const uint32_t G = __reduce_max_sync(kFull, k.edge ? 0u : k.nb);
   return G < 1u ? 1u : G;
+}
+
+// an empty slot (no key) for a lane
+__device__ __forceinline__ uint32_t lk_no_group(LKKey& k, const uint8_t* arena) {
+  k.valid = false;
+  k.kq = 0; k.base = arena; k.nb = 0; k.a = 0; k.tail = 0; k.edge = false;
+  return 1u;
 }
 
 // Byte masks of a 32-byte block in shared memory: row e (0..32) keeps bytes
@@ -304,52 +328,91 @@ __device__ ALGSIG_LK_FINISH uint64_t lk_finish(const uint32_t (&c)[16], uint32_t
   return sig;
 }
 
-// The signatures of one group: the lane's block at iteration it is
-// vb = G - 1 - it (its own blocks are vb < nb), so the lanes of shorter keys
-// start later and all lanes reach block 0 in the group's last iteration.  An
-// odd key whose last aligned block ends with a key byte needs the next
-// block's first byte.
+// The signature of a key with a block outside the arena's readable range
+// (its first 32 bytes or its last): the blocks one by one with checked loads.
+// At most a few keys per relation take this path.
+template <int NCOMP, class Cursor>
+__device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_lo, const uint8_t* lim_hi,
+                                             const uint16_t* inv32, const uint4* mt, const Cursor& rc) {
+  const uint32_t sh = 8u * (k.a & 1u);
+  uint32_t nxt0 = 0;
+  if (k.tail > 32u) nxt0 = __ldg(reinterpret_cast<const uint32_t*>(k.base + 32ull * k.nb));
+  uint32_t c[16];
+#pragma unroll
+  for (int i = 0; i < 16; i++) c[i] = 0;
+  uint32_t a3 = 0;
+  for (uint32_t vb = k.nb; vb-- > 0;) {
+    Blk w = ld_blk_checked(k.base + 32ull * vb, lim_lo, lim_hi);
+    if (vb + 1 == k.nb) blk_keep_below(w, k.tail, mt);
+    if (vb == 0) blk_zero_below(w, k.a, mt);
+    lk_block<NCOMP>(w, sh, nxt0, c, a3, rc);
+  }
+  return lk_finish<NCOMP>(c, a3, k.a, inv32, rc);
+}
+
+// The signatures of one group of keys: in iteration it of the group's G
+// iterations the lane takes block vb = G - 1 - it of its key (its own blocks
+// are vb < nb), so the lanes of shorter keys start later and every key reaches
+// its block 0 in the group's last iteration.  An odd key whose last aligned
+// block ends with a key byte needs the next block's first byte.  Keys with a
+// block outside the arena's readable range are computed apart (lk_edge_key).
 template <int NCOMP, class Cursor>
 __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8_t* lim_lo, const uint8_t* lim_hi,
                                          const uint16_t* inv32, const uint4* mt, uint64_t* __restrict__ sig_out,
                                          const Cursor& rc) {
+  const uint32_t nb = k.edge ? 0u : k.nb;
   const uint32_t sh = 8u * (k.a & 1u);
   uint32_t nxt0 = 0;
-  if (k.nb && k.tail > 32u) nxt0 = __ldg(reinterpret_cast<const uint32_t*>(k.base + 32ull * k.nb));
+  if (nb && k.tail > 32u) nxt0 = __ldg(reinterpret_cast<const uint32_t*>(k.base + 32ull * nb));
   // kLKDepth blocks in flight: iteration it takes its block out of ring slot it % kLKDepth and
   // refills the slot with block it + kLKDepth before computing (a ring of kLKDepth + 1 slots
-  // written in place measured slower: its loads stall longer)
+  // written in place, and loads that run on into the next group, measured slower)
   Blk ring[kLKDepth];
 #pragma unroll
   for (int u = 0; u < kLKDepth; ++u) {
 #pragma unroll
     for (int i = 0; i < 8; i++) ring[u].w[i] = 0;
     const int vb = (int)G - 1 - u;
-    if (vb >= 0 && (uint32_t)vb < k.nb) ring[u] = ld_blk(k.base + 32ull * (uint32_t)vb, lim_lo, lim_hi);
+    if (vb >= 0 && (uint32_t)vb < nb) ring[u] = ld_blk(k.base + 32ull * (uint32_t)vb);
   }
   uint32_t c[16];
 #pragma unroll
   for (int i = 0; i < 16; i++) c[i] = 0;
   uint32_t a3 = 0;
-  for (uint32_t it0 = 0; it0 < G; it0 += kLKDepth) {
+  // all iterations but the last (block 0, the bytes before the key's start masked)
+  const uint32_t M = G - 1;
+  for (uint32_t it0 = 0; it0 < M; it0 += kLKDepth) {
 #pragma unroll
     for (int u = 0; u < kLKDepth; ++u) {
       const uint32_t it = it0 + (uint32_t)u;
-      if (it >= G) break;
+      if (it >= M) break;
       const uint32_t vb = G - 1 - it;
       Blk w = ring[u];
       if (it + kLKDepth < G) {
         const uint32_t vb2 = vb - kLKDepth;
-        if (vb2 < k.nb) ring[u] = ld_blk(k.base + 32ull * vb2, lim_lo, lim_hi);
+        if (vb2 < nb) ring[u] = ld_blk(k.base + 32ull * vb2);
       }
-      if (vb < k.nb) {
-        if (vb + 1 == k.nb) blk_keep_below(w, k.tail, mt);   // bytes after the key's end
-        if (vb == 0) blk_zero_below(w, k.a, mt);             // bytes before its start
+      if (vb < nb) {
+        if (vb + 1 == nb) blk_keep_below(w, k.tail, mt);   // bytes after the key's end
         lk_block<NCOMP>(w, sh, nxt0, c, a3, rc);
       }
     }
   }
-  if (k.valid) sig_out[k.kq] = lk_finish<NCOMP>(c, a3, k.a, inv32, rc);
+  {                                                   // the last iteration: block 0 of every key
+    static_assert(kLKDepth == 1 || kLKDepth == 2, "the last iteration's ring slot: depths 1 and 2");
+    Blk w = ring[0];
+    if constexpr (kLKDepth == 2) {
+      if (M & 1u) w = ring[kLKDepth - 1];
+    }
+    if (nb) {
+      if (nb == 1) blk_keep_below(w, k.tail, mt);
+      blk_zero_below(w, k.a, mt);
+      lk_block<NCOMP>(w, sh, nxt0, c, a3, rc);
+    }
+  }
+  if (k.valid && !k.edge) sig_out[k.kq] = lk_finish<NCOMP>(c, a3, k.a, inv32, rc);
+  if (__any_sync(kFull, k.edge))
+    if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP>(k, lim_lo, lim_hi, inv32, mt, rc);
 }
 
 template <bool AT400, int NCOMP>
@@ -366,7 +429,7 @@ __global__ void __launch_bounds__(kLKThreads, 1) sig_key_kernel(const uint8_t* _
     reinterpret_cast<uint32_t*>(inv32)[i] = reinterpret_cast<const uint32_t*>(g_const + 16 * 512)[i];
   const int wib = threadIdx.x >> 5;
   LKWarp& W = warps[wib];
-  static_assert(sizeof(LKWarp) >= 2048, "table scratch fits warp 0's window state");
+  static_assert(kLKWarps * sizeof(LKWarp) >= 2048, "table scratch fits the warps' window state");
   init_red_tables(red, reinterpret_cast<uint32_t*>(&warps[0]));   // ends with __syncthreads()
   using Cursor = typename std::conditional<AT400, RedCursorAt400, RedCursor>::type;
   Cursor rc;
@@ -391,7 +454,7 @@ __global__ void __launch_bounds__(kLKThreads, 1) sig_key_kernel(const uint8_t* _
     const uint32_t ng = (wn + 31) / 32;
     for (uint32_t g = 0; g < ng; ++g) {
       LKKey k;
-      const uint32_t G = lk_load_group(k, W, wb, g, arena);
+      const uint32_t G = lk_load_group(k, W, wb, g, arena, lim_lo, lim_hi);
       if (g + 1 == ng) {                            // the window's offsets are free: fetch the next ones
         __syncwarp();
         lk_prefetch_window(W, off, wb + wn, k_hi);
