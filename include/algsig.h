@@ -36,7 +36,10 @@
  * Ownership and memory: the caller owns every buffer.  The library never
  * allocates device memory; it only keeps fixed-size tables in module-scope
  * device memory that is set up once per device on first use.  Workspace sizes
- * are queried with the *_bytes functions.
+ * are queried with the *_bytes functions.  cudaDeviceReset discards those
+ * tables (and as_join_probe_noalloc's scratch address) without the library
+ * noticing: do not call the library on a device again after resetting it in
+ * the same process.
  *
  * Streams: every call is asynchronous on the given stream (a cudaStream_t
  * passed as void*, NULL = legacy default stream) unless it is given a host
@@ -176,12 +179,16 @@ typedef struct as_table {
     uint64_t cap;             /* power of two */
     uint32_t log2cap;
     uint32_t reserved;
+    uint32_t* matched;        /* device: ceil(m/32) words, one bit per R row, set by
+                                 the R-side output modes of as_join_probe_mode;
+                                 NULL: the table supports no R-side mode */
 } as_table;
 
 /*
- * Workspace of as_join_build: the slots (16 bytes each), R's signatures and
- * the flags, each 256-byte aligned.  load_factor must be in (0, 1].  Returns 0
- * for invalid arguments.
+ * Workspace of as_join_build: the slots (16 bytes each), R's signatures, the
+ * flags and a bitmap of R's rows (for the R-side output modes of
+ * as_join_probe_mode), each 256-byte aligned.  load_factor must be in (0, 1].
+ * Returns 0 for invalid arguments.
  */
 size_t as_join_table_bytes(uint64_t m, float load_factor);
 
@@ -256,6 +263,14 @@ as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const u
  *   AS_JOIN_ANTI    : one (AS_NO_ROW, s_id) per S row with no match
  *   AS_JOIN_OUTER_S : the inner pairs plus one (AS_NO_ROW, s_id) per S row
  *                     with no match (outer join preserving S)
+ *   AS_JOIN_OUTER_R : the inner pairs plus one (r_id, AS_NO_ROW) per R row
+ *                     with no match (outer join preserving R)
+ *   AS_JOIN_SEMI_R  : one (r_id, AS_NO_ROW) per R row with at least one match
+ *   AS_JOIN_ANTI_R  : one (r_id, AS_NO_ROW) per R row with no match
+ *                     (the R-side modes mark R's matched rows in the table's
+ *                     bitmap during the probe, then list the selected rows;
+ *                     they need a table from as_join_build, and two R-side
+ *                     probes of one table must not overlap)
  *   AS_JOIN_SIG_ONLY: the probe of Figure 2 as the paper runs it: one
  *                     (r_id, s_id) pair per slot whose signature and key
  *                     length equal the S key's, with no byte comparison.
@@ -270,7 +285,10 @@ enum {
     AS_JOIN_SEMI = 1,
     AS_JOIN_ANTI = 2,
     AS_JOIN_OUTER_S = 3,
-    AS_JOIN_SIG_ONLY = 4
+    AS_JOIN_SIG_ONLY = 4,
+    AS_JOIN_OUTER_R = 5,
+    AS_JOIN_SEMI_R = 6,
+    AS_JOIN_ANTI_R = 7
 };
 #define AS_NO_ROW 0xFFFFFFFFu
 
@@ -444,6 +462,8 @@ as_status as_baseline_join(const uint8_t* d_arenaR, const uint64_t* d_offR, cons
  * The first call on a device (with that device current) does one-time setup:
  * the library's tables and kernel attributes, and the scratch address
  * (cudaGetSymbolAddress); make that first call before any stream capture.
+ * The address is kept for the life of the process (see cudaDeviceReset
+ * above).  Error messages name as_join_probe_noalloc.
  * Other arguments, results and errors as for as_join_probe with
  * d_sigS_out = NULL.
  */

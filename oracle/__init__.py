@@ -242,21 +242,38 @@ MODES = {"inner": 0, "semi": 1, "anti": 2, "outer_s": 3}
 def join_mode(R, S, mode: str) -> np.ndarray:
     """The join's output in one of the modes of the left/right/semi-join
     extensions (Section 5), by their plain definitions on the exact inner join
-    T: semi = {(NO_ROW, s.id) : s has a partner in T}, anti = the S rows without
-    one, outer_s = T plus the anti rows.  Sorted like sort_pairs."""
+    T (R the build side, S the probe side):
+      semi    = {(NO_ROW, s.id) : s has a partner in T}, anti = the S rows without one,
+      outer_s = T plus the S anti rows (outer join preserving S);
+      semi_r  = {(r.id, NO_ROW) : r has a partner in T}, anti_r = the R rows without one,
+      outer_r = T plus the R anti rows (outer join preserving R).
+    Sorted like sort_pairs."""
     T = join_simple(R, S)
-    matched_ids = set(T[:, 1].tolist())
+    s_matched = set(T[:, 1].tolist())
+    r_matched = set(T[:, 0].tolist())
     sids = [int(x) for x in S.ids]
-    semi = [(NO_ROW, s) for s in sids if s in matched_ids]
-    anti = [(NO_ROW, s) for s in sids if s not in matched_ids]
+    rids = [int(x) for x in R.ids]
+    semi = [(NO_ROW, s) for s in sids if s in s_matched]
+    anti = [(NO_ROW, s) for s in sids if s not in s_matched]
+    semi_r = [(r, NO_ROW) for r in rids if r in r_matched]
+    anti_r = [(r, NO_ROW) for r in rids if r not in r_matched]
+
+    def arr(rows):
+        return np.array(rows, dtype=np.uint32).reshape(-1, 2)
     if mode == "inner":
         out = T
     elif mode == "semi":
-        out = np.array(semi, dtype=np.uint32).reshape(-1, 2)
+        out = arr(semi)
     elif mode == "anti":
-        out = np.array(anti, dtype=np.uint32).reshape(-1, 2)
+        out = arr(anti)
     elif mode == "outer_s":
-        out = np.concatenate([T, np.array(anti, dtype=np.uint32).reshape(-1, 2)])
+        out = np.concatenate([T, arr(anti)])
+    elif mode == "semi_r":
+        out = arr(semi_r)
+    elif mode == "anti_r":
+        out = arr(anti_r)
+    elif mode == "outer_r":
+        out = np.concatenate([T, arr(anti_r)])
     else:
         raise ValueError(mode)
     return sort_pairs(out)

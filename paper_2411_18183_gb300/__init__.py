@@ -48,7 +48,7 @@ class Table(ctypes.Structure):
     _fields_ = [("slots", ctypes.c_void_p), ("sigR", ctypes.c_void_p), ("arenaR", ctypes.c_void_p),
                 ("offR", ctypes.c_void_p), ("idR", ctypes.c_void_p), ("flags", ctypes.c_void_p),
                 ("m", ctypes.c_uint64), ("cap", ctypes.c_uint64), ("log2cap", ctypes.c_uint32),
-                ("reserved", ctypes.c_uint32)]
+                ("reserved", ctypes.c_uint32), ("matched", ctypes.c_void_p)]
 
 
 _lock = threading.Lock()
@@ -275,7 +275,8 @@ def join_probe_sigs(t: Table, S: DeviceRelation, sigS: torch.Tensor, pairs: torc
     return int(h.value) if sync else None
 
 
-JOIN_MODES = {"inner": 0, "semi": 1, "anti": 2, "outer_s": 3, "sig_only": 4}    # AS_JOIN_*
+JOIN_MODES = {"inner": 0, "semi": 1, "anti": 2, "outer_s": 3, "sig_only": 4,
+              "outer_r": 5, "semi_r": 6, "anti_r": 7}                # AS_JOIN_*
 NO_ROW = 0xFFFFFFFF                                                  # AS_NO_ROW
 ROWS_SCATTERED = 0xFFFFFFFFFFFFFFFF                                  # AS_ROWS_SCATTERED
 
@@ -283,7 +284,8 @@ ROWS_SCATTERED = 0xFFFFFFFFFFFFFFFF                                  # AS_ROWS_S
 def join_probe_mode(t: Table, S: DeviceRelation, sigS: torch.Tensor, pairs: torch.Tensor, count: torch.Tensor,
                     mode: str = "inner", sync: bool = True, stream=None) -> int | None:
     """as_join_probe_mode: inner pairs, or per-S-row (NO_ROW, s_id) records (semi, anti), or
-    inner pairs plus the unmatched S rows (outer_s), or the signature-only pairs of the
+    inner pairs plus the unmatched S rows (outer_s), or the R-side counterparts with per-R-row
+    (r_id, NO_ROW) records (semi_r, anti_r, outer_r), or the signature-only pairs of the
     paper's probe without byte verification (sig_only; not exact)."""
     lib = load()
     cap = pairs.numel() // 2

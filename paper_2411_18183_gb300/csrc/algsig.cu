@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/algsig.h"
+#include "loopbounds.h"
 #include <nvtx3/nvToolsExt.h>
 #include "gf16.cuh"
 
@@ -599,7 +600,8 @@ struct VerifyParams {
   uint32_t* pairs;
   uint64_t cap;
   unsigned long long* count;
-  int mode;                    // AS_JOIN_INNER / SEMI / ANTI / OUTER_S / SIG_ONLY (single joins)
+  int mode;                    // AS_JOIN_* (single joins)
+  uint32_t* matched;           // R-side modes: bit per R row, set for every verified pair
   // batch mode (J != nullptr): per-join tables, output regions and counters
   const BatchJoin* J;
   int nj;
@@ -653,8 +655,7 @@ __device__ __noinline__ bool warp_equal_wide(const uint8_t* __restrict__ aR, uin
   return true;
 }
 
-// Keys below this length are compared with 32-bit offsets (warp_equal).
-constexpr uint32_t kNarrowLen = 0xFFFFFFC0u;
+// Keys below kNarrowLen (loopbounds.h) are compared with 32-bit offsets (warp_equal).
 
 // emask[e]: the first e bytes of a 16-byte chunk (e = 0..16), in shared memory.
 __device__ __forceinline__ void fill_emask(uint4* emask) {
@@ -721,7 +722,9 @@ __device__ __forceinline__ bool warp_equal(const uint8_t* __restrict__ pR, const
   const uint32_t sh = 8u * (d & 3u);
   const uint32_t kend = sa + len;                  // S key bytes: [sa, kend) from bS
   const uint32_t rlo = sa + d, rend = kend + d;    // R key bytes: [rlo, rend) from bR
-  for (uint32_t base = 0; base < kend; base += 1024u) {
+  const uint32_t nsteps = narrow_steps(sa, len);   // offsets stay below 2^32 (len < kNarrowLen)
+  for (uint32_t step = 0; step < nsteps; ++step) {
+    const uint32_t base = step << 10;
     uint4 sv[2], ra[2], rb[2];
 #pragma unroll
     for (int h = 0; h < 2; h++) {
@@ -894,6 +897,10 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         if (eq) {
           const uint64_t srow = __shfl_sync(kFull, i, j);
           if (lane == j) matched = true;
+          if (!batch && P.mode >= AS_JOIN_OUTER_R) {  // R-side modes: mark the R row
+            if (lane == 0) atomicOr(P.matched + (rj >> 5), 1u << (rj & 31u));
+            if (P.mode != AS_JOIN_OUTER_R) continue;   // rows, not pairs
+          }
           if (!batch && (P.mode == AS_JOIN_SEMI || P.mode == AS_JOIN_ANTI)) continue;   // rows, not pairs
           const int jj = __shfl_sync(kFull, jn, j);
           if (batch && np && jj != sj) {              // the stage holds one join's pairs
@@ -913,7 +920,8 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         }
       }
     }
-    if (!batch && P.mode != AS_JOIN_INNER && P.mode != AS_JOIN_SIG_ONLY) {   // one (AS_NO_ROW, s_id) per selected S row
+    if (!batch && (P.mode == AS_JOIN_SEMI || P.mode == AS_JOIN_ANTI || P.mode == AS_JOIN_OUTER_S)) {
+      // one (AS_NO_ROW, s_id) per selected S row
       const bool emit = row_live && (P.mode == AS_JOIN_SEMI ? matched : !matched);
       const uint32_t em = __ballot_sync(kFull, emit);
       if (em) {
@@ -933,6 +941,33 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
   }
   if (np) {
     if (batch) flush_stage_join(stage, np, P, sj); else flush_stage(stage, np, P);
+  }
+}
+
+// The R-side output modes' rows: one (r_id, AS_NO_ROW) per R row whose bit in
+// `matched` is `want` (1: semi-join rows, 0: anti-join / outer-join rows),
+// appended to the pairs after those of the probe.  One warp per 32 rows: a
+// ballot, one atomic per warp, lanes write their records in order.
+__global__ void r_rows_kernel(const uint32_t* __restrict__ matched, uint64_t m, uint32_t want,
+                              const uint32_t* __restrict__ idR, uint32_t* pairs, uint64_t cap,
+                              unsigned long long* count) {
+  const int lane = threadIdx.x & 31;
+  const uint64_t nwarps = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t w = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); w * 32 < m; w += nwarps) {
+    const uint64_t r = w * 32 + (uint64_t)lane;
+    const bool emit = r < m && ((__ldg(matched + w) >> lane) & 1u) == want;
+    const uint32_t em = __ballot_sync(kFull, emit);
+    if (!em) continue;
+    unsigned long long base = 0;
+    if (lane == 0) base = atomicAdd(count, (unsigned long long)__popc(em));
+    base = __shfl_sync(kFull, base, 0);
+    if (emit) {
+      const unsigned long long idx = base + (unsigned long long)__popc(em & lanemask_lt());
+      if (idx < cap) {
+        const uint32_t rid = idR ? __ldg(idR + r) : (uint32_t)r;
+        reinterpret_cast<uint64_t*>(pairs)[idx] = (uint64_t)rid | ((uint64_t)AS_NO_ROW << 32);
+      }
+    }
   }
 }
 
@@ -1482,7 +1517,7 @@ size_t as_join_table_bytes(uint64_t m, float load_factor) {
   uint64_t cap;
   uint32_t l2;
   if (!table_geometry(m, load_factor, &cap, &l2)) return 0;
-  return (size_t)(round256(cap * 16) + round256(m * 8) + 256);
+  return (size_t)(round256(cap * 16) + round256(m * 8) + 256 + round256((m + 31) / 32 * 4));
 }
 
 size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor) {
@@ -1539,6 +1574,7 @@ as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, co
   out->cap = cap;
   out->log2cap = l2;
   out->reserved = 0;
+  out->matched = reinterpret_cast<uint32_t*>(ws + round256(cap * 16) + round256(m * 8) + 256);
   return AS_OK;
 }
 
@@ -1562,6 +1598,7 @@ static as_status launch_verify(DeviceState* d, const as_table* t, const uint8_t*
                                uint64_t cap_pairs, uint64_t* d_count, cudaStream_t s, int mode = AS_JOIN_INNER,
                                uint64_t cap_len = ~0ull) {
   VerifyParams P;
+  P.matched = mode >= AS_JOIN_OUTER_R ? t->matched : nullptr;
   P.cap_len = cap_len;
   P.slots = reinterpret_cast<const Slot*>(t->slots);
   P.mask = t->cap - 1;
@@ -1609,19 +1646,21 @@ static as_status finish_probe(const char* fn, const as_table* t, uint64_t cap_pa
   return AS_OK;
 }
 
-as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS,
-                        uint64_t n, uint64_t* d_sigS_out, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
-                        uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
-  NvtxRange nvtx_range("as_join_probe");
-  as_status st = probe_args("as_join_probe", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
+}  // extern "C"
+
+// as_join_probe's work, for it and for as_join_probe_noalloc; fn names the caller in error messages
+static as_status probe_impl(const char* fn, const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
+                            const uint32_t* d_idS, uint64_t n, uint64_t* d_sigS_out, void* d_ws, size_t ws_bytes,
+                            uint32_t* d_pairs, uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count,
+                            as_stream stream) {
+  as_status st = probe_args(fn, t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
   if (st != AS_OK) return st;
   uint64_t* sigS = d_sigS_out;
   if (!sigS && n > 0) {
     const size_t need = as_join_probe_ws_bytes(n);
     if (!d_ws || ws_bytes < need)
-      return fail(AS_ERR_NOMEM, "as_join_probe: workspace of %zu bytes, need %zu", d_ws ? ws_bytes : 0, need);
-    if (reinterpret_cast<uintptr_t>(d_ws) & 255u)
-      return fail(AS_ERR_INVALID, "as_join_probe: workspace not 256-byte aligned");
+      return fail(AS_ERR_NOMEM, "%s: workspace of %zu bytes, need %zu", fn, d_ws ? ws_bytes : 0, need);
+    if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return fail(AS_ERR_INVALID, "%s: workspace not 256-byte aligned", fn);
     sigS = reinterpret_cast<uint64_t*>(d_ws);
   }
   DeviceState* d = nullptr;
@@ -1636,7 +1675,17 @@ as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64
     st = launch_verify(d, t, d_arenaS, d_offS, d_idS, n, sigS, d_pairs, cap_pairs, d_count, s);
     if (st != AS_OK) return st;
   }
-  return finish_probe("as_join_probe", t, cap_pairs, d_count, h_count, s);
+  return finish_probe(fn, t, cap_pairs, d_count, h_count, s);
+}
+
+extern "C" {
+
+as_status as_join_probe(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS,
+                        uint64_t n, uint64_t* d_sigS_out, void* d_ws, size_t ws_bytes, uint32_t* d_pairs,
+                        uint64_t cap_pairs, uint64_t* d_count, uint64_t* h_count, as_stream stream) {
+  NvtxRange nvtx_range("as_join_probe");
+  return probe_impl("as_join_probe", t, d_arenaS, d_offS, d_idS, n, d_sigS_out, d_ws, ws_bytes, d_pairs, cap_pairs,
+                    d_count, h_count, stream);
 }
 
 as_status as_join_probe_sigs(const as_table* t, const uint8_t* d_arenaS, const uint64_t* d_offS,
@@ -1665,17 +1714,30 @@ as_status as_join_probe_mode(const as_table* t, const uint8_t* d_arenaS, const u
   NvtxRange nvtx_range("as_join_probe_mode");
   as_status st = probe_args("as_join_probe_mode", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
   if (st != AS_OK) return st;
-  if (mode < AS_JOIN_INNER || mode > AS_JOIN_SIG_ONLY) return fail(AS_ERR_INVALID, "as_join_probe_mode: mode %d", mode);
+  if (mode < AS_JOIN_INNER || mode > AS_JOIN_ANTI_R) return fail(AS_ERR_INVALID, "as_join_probe_mode: mode %d", mode);
   if (n > 0 && !d_sigS) return fail(AS_ERR_INVALID, "as_join_probe_mode: null signatures");
+  const bool r_side = mode >= AS_JOIN_OUTER_R;
+  if (r_side && t->m > 0 && !t->matched)
+    return fail(AS_ERR_INVALID, "as_join_probe_mode: R-side mode %d needs a table from as_join_build (row bitmap)", mode);
   DeviceState* d = nullptr;
   st = ensure_device(&d);
   if (st != AS_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if ((e = cudaMemsetAsync(d_count, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  if (r_side && t->m > 0 && (e = cudaMemsetAsync(t->matched, 0, (t->m + 31) / 32 * 4, s)) != cudaSuccess)
+    return cuda_fail(e, "row bitmap clear");
   if (n > 0) {
     st = launch_verify(d, t, d_arenaS, d_offS, d_idS, n, d_sigS, d_pairs, cap_pairs, d_count, s, mode);
     if (st != AS_OK) return st;
+  }
+  if (r_side && t->m > 0) {                          // the selected R rows after the probe's pairs
+    uint64_t blocks = (t->m + 255) / 256;
+    const uint64_t lim = (uint64_t)d->sms * 8;
+    if (blocks > lim) blocks = lim;
+    r_rows_kernel<<<(unsigned)blocks, 256, 0, s>>>(t->matched, t->m, mode == AS_JOIN_SEMI_R ? 1u : 0u, t->idR,
+                                                   d_pairs, cap_pairs, reinterpret_cast<unsigned long long*>(d_count));
+    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "R-row kernel launch");
   }
   return finish_probe("as_join_probe_mode", t, cap_pairs, d_count, h_count, s);
 }
@@ -2236,6 +2298,8 @@ extern "C" as_status as_join_probe_noalloc(const as_table* t, const uint8_t* d_a
   if (n > (uint64_t)AS_PROBE_NOALLOC_MAX_KEYS)
     return fail(AS_ERR_INVALID, "as_join_probe_noalloc: %llu keys, the fixed scratch holds at most %u",
                 (unsigned long long)n, (unsigned)AS_PROBE_NOALLOC_MAX_KEYS);
+  as_status st = probe_args("as_join_probe_noalloc", t, d_arenaS, d_offS, n, d_pairs, cap_pairs, d_count);
+  if (st != AS_OK) return st;
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return fail(AS_ERR_UNSUPPORTED, "no CUDA device: %s", cudaGetErrorString(e));
@@ -2252,6 +2316,6 @@ extern "C" as_status as_join_probe_noalloc(const as_table* t, const uint8_t* d_a
     }
     scratch = g_probe_noalloc_addr[dev];
   }
-  return as_join_probe(t, d_arenaS, d_offS, d_idS, n, static_cast<uint64_t*>(scratch), nullptr, 0, d_pairs,
-                       cap_pairs, d_count, h_count, stream);
+  return probe_impl("as_join_probe_noalloc", t, d_arenaS, d_offS, d_idS, n, static_cast<uint64_t*>(scratch), nullptr,
+                    0, d_pairs, cap_pairs, d_count, h_count, stream);
 }

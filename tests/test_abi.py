@@ -37,8 +37,9 @@ def test_every_declared_symbol_is_exported(lib):
 def test_host_queries(lib):
     assert lib.as_version() >= 100
     assert lib.as_status_string(3) == b"AS_ERR_CAPACITY"
-    # cap = next power of two >= m / lf (at least 64); slots + signatures + flags
-    assert lib.as_join_table_bytes(1000, 0.5) == 2048 * 16 + ((1000 * 8 + 255) // 256) * 256 + 256
+    # cap = next power of two >= m / lf (at least 64); slots + signatures + flags + R-row bitmap
+    assert lib.as_join_table_bytes(1000, 0.5) == (2048 * 16 + ((1000 * 8 + 255) // 256) * 256 + 256
+                                                  + ((1000 + 31) // 32 * 4 + 255) // 256 * 256)
     assert lib.as_join_table_bytes(10, 0.0) == 0
     assert lib.as_join_table_bytes(10, 1.5) == 0
     assert lib.as_join_probe_ws_bytes(5000) == (5000 * 8 + 255) // 256 * 256 + 256

@@ -102,8 +102,9 @@ def test_large_workload_ground_truth_scaled():
 
 
 def test_join_modes_by_definition_and_brute_force():
-    """semi / anti / outer_s of the oracle against a brute-force statement on
-    small relations with duplicates, empty keys and ids that are not rows."""
+    """semi / anti / outer_s and their R-side counterparts (semi_r / anti_r /
+    outer_r) of the oracle against a brute-force statement on small relations
+    with duplicates, empty keys and ids that are not rows."""
     import random
     rng = random.Random(11)
     pool = [b"", b"a", b"ab", b"abc", b"xyz" * 5, bytes(range(40))]
@@ -114,12 +115,18 @@ def test_join_modes_by_definition_and_brute_force():
     NO = oracle.NO_ROW
     inner = sorted((1000 + i, 7 * j + 3) for j, s in enumerate(sk) for i, r in enumerate(rk) if r == s)
     has = {j for j, s in enumerate(sk) if s in rk}
+    r_has = {i for i, r in enumerate(rk) if r in sk}
     want = {
         "inner": inner,
         "semi": sorted((NO, 7 * j + 3) for j in range(len(sk)) if j in has),
         "anti": sorted((NO, 7 * j + 3) for j in range(len(sk)) if j not in has),
         "outer_s": sorted(inner + [(NO, 7 * j + 3) for j in range(len(sk)) if j not in has]),
+        "semi_r": sorted((1000 + i, NO) for i in range(len(rk)) if i in r_has),
+        "anti_r": sorted((1000 + i, NO) for i in range(len(rk)) if i not in r_has),
+        "outer_r": sorted(inner + [(1000 + i, NO) for i in range(len(rk)) if i not in r_has]),
     }
+    # the R-side modes partition R, and every R row appears once
+    assert len(want["semi_r"]) + len(want["anti_r"]) == len(rk)
     for mode, w in want.items():
         got = [tuple(int(x) for x in row) for row in oracle.join_mode(R, S, mode)]
         assert got == w, mode

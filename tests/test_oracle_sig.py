@@ -43,10 +43,14 @@ def test_against_polynomial_definition(method):
 
 
 def test_worked_values_from_definition():
-    # values of the definition computed by independent polynomial arithmetic
-    for key in (b"ABC", b"ABCD", b"Paul Sabatier University"):
-        assert oracle.sig(key) == sig_by_polynomial(key)
-    assert oracle.sig(b"ABCD") == 0x465D404F4346CAC7
+    # values of the definition computed by independent polynomial arithmetic, and the constants
+    # worked out from the definition for these keys (the last one is the paper's example string)
+    worked = {b"ABC": 0x46714059434D42C7, b"ABCD": 0x465D404F4346CAC7,
+              b"Paul Sabatier University": 0x8FD210505191A40E}
+    for key, value in worked.items():
+        assert sig_by_polynomial(key) == value, key
+        assert oracle.sig(key) == value, key
+        assert oracle.sig(key, "horner") == value, key
 
 
 def test_linearity():
