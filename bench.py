@@ -15,6 +15,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -116,71 +117,63 @@ def pct(xs, q):
 
 # --------------------------------------------------------------------------- reference arm (the CPU oracle)
 
-def cpu_oracle_run(wl, n_s: int, cores: int) -> float:
-    """Oracle on the host: signatures of all of R and of the first n_s S keys,
-    then the exact Grace hash join of R with those S keys.  Returns seconds."""
+def cpu_oracle_slice(wl, frac0: float, frac1: float, cores: int) -> tuple[float, int]:
+    """The oracle on the host on the rows [frac0, frac1) of both relations (the
+    same fraction of R and of S, consecutive rows): signatures of every key of
+    both slices, then the exact Grace hash join of the two slices.  Returns
+    (seconds, S keys of the slice).  The whole relations are frac 0..1."""
     import oracle
     from workloads import Relation
-    S = wl.S
-    Ss = Relation(S.arena, S.off[: n_s + 1].copy(), S.ids[:n_s].copy())
+
+    def part(rel):
+        a, b = int(rel.n * frac0), int(rel.n * frac1)
+        return Relation(rel.arena, rel.off[a:b + 1].copy(), rel.ids[a:b].copy())
+    Rs, Ss = part(wl.R), part(wl.S)
     t0 = time.perf_counter()
-    oracle.sig_batch(wl.R.arena, wl.R.off, nthreads=cores)
+    oracle.sig_batch(Rs.arena, Rs.off, nthreads=cores)
     oracle.sig_batch(Ss.arena, Ss.off, nthreads=cores)
-    oracle.join_grace(wl.R, Ss, log2_parts=10, nthreads=cores)
-    return time.perf_counter() - t0
+    oracle.join_grace(Rs, Ss, log2_parts=10, nthreads=cores)
+    return time.perf_counter() - t0, Ss.n
 
 
-class CpuModel:
-    """Time of the oracle as a + b * n_s (fixed R work + per-S-key work), fitted
-    from two sample sizes; value = |S| / (a + b |S|) S tuples per second."""
-
-    def __init__(self, wl, cores: int, budget_s: float = 12.0):
-        self.wl, self.cores = wl, cores
-        n = wl.S.n
-        self.n1 = max(1, min(n, max(2000, n // 50)))
-        t1 = cpu_oracle_run(wl, self.n1, cores)
-        t1b = cpu_oracle_run(wl, self.n1, cores)
-        t1 = min(t1, t1b)
-        if self.n1 >= n:
-            self.a, self.b, self.n2, self.t2 = 0.0, t1 / n, n, t1
-            return
-        per = t1 / self.n1
-        self.n2 = int(min(n, max(2 * self.n1, budget_s / max(per, 1e-12))))
-        self.t2 = cpu_oracle_run(wl, self.n2, cores)
-        self.b = max(1e-12, (self.t2 - t1) / (self.n2 - self.n1))
-        self.a = max(0.0, t1 - self.b * self.n1)
-
-    def value_from(self, t: float, n_s: int) -> float:
-        """S tuples/s of the whole join, extrapolating one run of n_s S keys."""
-        n = self.wl.S.n
-        per = max(1e-12, (t - self.a) / n_s)
-        return n / (self.a + per * n)
-
-    def sample_text(self) -> str:
-        return (f"all {self.wl.R.n:,} R keys with the first {self.n1:,} and {self.n2:,} of {self.wl.S.n:,} S keys "
-                f"(signatures + Grace join); time fitted as fixed + per-S-key and extrapolated to all of S")
+def cpu_baseline_full(wl, cores: int) -> dict:
+    """The oracle timed once on all of R and all of S (signatures of every key,
+    then the Grace hash join): S tuples per second of the whole join."""
+    t, n_s = cpu_oracle_slice(wl, 0.0, 1.0, cores)
+    return {"value": n_s / t, "unit": UNIT, "cores": cores, "kind": "oracle", "seconds": t,
+            "sample": f"all of R ({wl.R.n:,} keys) and all of S ({wl.S.n:,} keys): signatures of every key and "
+                      f"the Grace hash join, one timed run"}
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, each step on a consecutive 1/k of R and
+    of S (k sized so that the whole run takes about a minute); value = the S
+    keys of a step / its time, median over the steps."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     spec = workloads.CONFIGS[args.workload]
     wl = workloads.generate(spec)
     cores = os.cpu_count() or 1
-    model = CpuModel(wl, cores, budget_s=max(4.0, 60.0 / max(1, args.steps + args.warmup)))
-    for _ in range(args.warmup):
-        cpu_oracle_run(wl, model.n2, cores)
-    vals = []
-    for _ in range(args.steps):
-        vals.append(model.value_from(cpu_oracle_run(wl, model.n2, cores), model.n2))
+    t_cal, _ = cpu_oracle_slice(wl, 0.0, 1.0 / 200, cores)        # calibration on 1/200 of the join
+    budget = 45.0 / max(1, args.steps + args.warmup)
+    k = int(min(200, max(1, math.ceil(t_cal * 200 / budget))))
+    secs, vals = [], []
+    for i in range(args.warmup + args.steps):
+        j = i % k
+        t, n_s = cpu_oracle_slice(wl, j / k, (j + 1) / k, cores)
+        if i >= args.warmup:
+            secs.append(t)
+            vals.append(n_s / t)
     value = statistics.median(vals)
+    ms = statistics.median(secs) * 1e3
+    sample = (f"each step: a consecutive 1/{k} of R and of S ({wl.R.n // k:,} R and {wl.S.n // k:,} S keys), "
+              f"signatures of every key and the Grace hash join of the two slices")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wl.S.n / value * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
             "data": "synthetic", "config": {"workload": workload_desc(args.workload, spec)},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": model.sample_text()},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -319,6 +312,47 @@ def replica_value(units_per_rank: int, world: int, max_ms: float) -> float:
 
 # --------------------------------------------------------------------------- GPU arm
 
+TUNE_ROUNDS = 3
+FLUSH_BYTES = 512 << 20          # written between timed steps: four times the 129 MB L2
+_flush_buf = None
+
+
+def flush_l2(stream):
+    """Evict L2 by writing a buffer four times its size on the stream."""
+    global _flush_buf
+    if _flush_buf is None:
+        _flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    with torch.cuda.stream(stream):
+        _flush_buf.fill_(0x5A)
+
+
+def tune_load_factor(make_run, stream):
+    """The fastest of LOAD_FACTORS for a join: each candidate's run() is timed
+    over two joins per round, in TUNE_ROUNDS rounds that interleave the
+    candidates (so a drift of the clock or the memory system hits them all);
+    a candidate's time is its median round.  Returns (best, {lf: ms})."""
+    runs = {}
+    for cand in LOAD_FACTORS:
+        runs[cand] = make_run(cand)
+        runs[cand]()
+    torch.cuda.synchronize()
+    times = {cand: [] for cand in LOAD_FACTORS}
+    for _ in range(TUNE_ROUNDS):
+        for cand in LOAD_FACTORS:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(2):
+                runs[cand]()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times[cand].append(e0.elapsed_time(e1) / 2)
+    med = {str(c): statistics.median(v) for c, v in times.items()}
+    best = min(LOAD_FACTORS, key=lambda c: med[str(c)])
+    runs.clear()
+    torch.cuda.empty_cache()
+    return best, med
+
+
 def run_gpu(args):
     import torch
     import paper_2411_18183_gb300 as ag
@@ -402,22 +436,7 @@ def run_gpu(args):
     # joins before the timed region (the batch leg tunes its own the same way)
     lf_tuning = {}
     if args.load_factor is None:
-        best = None
-        for cand in LOAD_FACTORS:
-            cstep, cws, _, _ = make_step(cand)
-            cstep()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(2):
-                cstep()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            lf_tuning[str(cand)] = e0.elapsed_time(e1) / 2
-            if best is None or lf_tuning[str(cand)] < lf_tuning[str(best)]:
-                best = cand
-            del cstep, cws
-        lf = best
+        lf, lf_tuning = tune_load_factor(lambda cand: make_step(cand)[0], stream)
     else:
         lf = args.load_factor
     step, ws, tb, count = make_step(lf)
@@ -442,6 +461,7 @@ def run_gpu(args):
     t0.record(stream)
     for k in range(args.steps):
         step(ev[k])
+        flush_l2(stream)                                # between steps, outside the steps' events
     t1.record(stream)
     barrier()
     clk = clocks.stop()
@@ -449,29 +469,47 @@ def run_gpu(args):
     phase_ms = {ph: [e[i].elapsed_time(e[i + 1]) for e in ev] for i, ph in enumerate(PH)}
     step_ms = [e[0].elapsed_time(e[len(PH)]) for e in ev]
     total_ms = ranks_max(total_ms)
-    ms_per_step = total_ms / args.steps
+    ms_per_step = ranks_max(sum(step_ms)) / args.steps   # the K steps' own event time, flushes excluded
     value = replica_value(n, world, ms_per_step)
 
-    # the same-GPU comparison join on full strings (plain and tagged variants)
-    bws = ag.alloc_ws(ag.baseline_ws_bytes(m, n, lf))
-    bcount = torch.zeros(1, dtype=torch.int64, device="cuda")
+    # the same-GPU comparison join on full strings (plain and tagged variants), each
+    # with its own load factor tuned the same way, timed like the signature join's steps
+    # (L2 flushed between joins, each join's own CUDA-event time)
+    def timed_reps(run, reps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for a, b in evs:
+            a.record(stream)
+            run()
+            b.record(stream)
+            flush_l2(stream)
+        torch.cuda.synchronize()
+        return statistics.mean(a.elapsed_time(b) for a, b in evs)
+
     baseline = {}
     for tagged in (False, True):
-        st, bcnt = ag.baseline_join_into(dR, dS, bws, pairs, bcount, lf, tagged=tagged, sync=True)
+        def make_brun(cand, tagged=tagged):
+            bws_c = ag.alloc_ws(ag.baseline_ws_bytes(m, n, cand))
+            bcount_c = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+            def run():
+                ag.baseline_join_into(dR, dS, bws_c, pairs, bcount_c, cand, tagged=tagged, sync=False, stream=stream)
+            return run
+        if args.load_factor is None:
+            blf, btune = tune_load_factor(make_brun, stream)
+        else:
+            blf, btune = args.load_factor, None
+        bws = ag.alloc_ws(ag.baseline_ws_bytes(m, n, blf))
+        bcount = torch.zeros(1, dtype=torch.int64, device="cuda")
+        st, bcnt = ag.baseline_join_into(dR, dS, bws, pairs, bcount, blf, tagged=tagged, sync=True)
         if bcnt != total_pairs:
             raise SystemExit(f"comparison join found {bcnt} pairs, signature join {total_pairs}")
         for _ in range(2):
-            ag.baseline_join_into(dR, dS, bws, pairs, bcount, lf, tagged=tagged, sync=False, stream=stream)
-        b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        breps = max(3, min(10, args.steps))
-        b0.record(stream)
-        for _ in range(breps):
-            ag.baseline_join_into(dR, dS, bws, pairs, bcount, lf, tagged=tagged, sync=False, stream=stream)
-        b1.record(stream)
-        torch.cuda.synchronize()
-        bms = b0.elapsed_time(b1) / breps
-        baseline["tagged" if tagged else "plain"] = {"ms_per_join": bms, "tuples_per_s": n / (bms * 1e-3)}
-    del bws
+            ag.baseline_join_into(dR, dS, bws, pairs, bcount, blf, tagged=tagged, sync=False, stream=stream)
+        bms = timed_reps(lambda: ag.baseline_join_into(dR, dS, bws, pairs, bcount, blf, tagged=tagged, sync=False,
+                                                       stream=stream), max(3, min(10, args.steps)))
+        baseline["tagged" if tagged else "plain"] = {"ms_per_join": bms, "tuples_per_s": n / (bms * 1e-3),
+                                                     "load_factor": blf, "load_factor_tuning_ms": btune}
+        del bws
 
     # the radix-partitioned signature join (R and S split by the bucket hash's top
     # bits, one table per partition) on the same inputs, against the step above
@@ -624,6 +662,20 @@ def run_gpu(args):
     h2d = (sum(int(t.numel() * t.element_size()) for t in hR)
            + sum((((int(wl.S.off[b]) + 15) & ~15) + 16 - (int(wl.S.off[a]) & ~15)) + 8 * (b - a + 1) + 4 * (b - a)
                  for a, b in zip(cuts, cuts[1:])))
+    # the host link's pinned copy rate alone (1 GiB host -> device), for the record next to e2e
+    hprobe = hS[0][: min(hS[0].numel(), 1 << 30)]
+    dprobe = torch.empty(hprobe.numel(), dtype=torch.uint8, device="cuda")
+    dprobe.copy_(hprobe, non_blocking=True)
+    torch.cuda.synchronize()
+    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h0.record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            dprobe.copy_(hprobe, non_blocking=True)
+    h1.record(stream)
+    torch.cuda.synchronize()
+    h2d_gbs = 3 * hprobe.numel() / (h0.elapsed_time(h1) * 1e-3) / 1e9
+    del dprobe
     e2e_steps = max(2, min(args.steps, 5))
     if sj.run(hR, hS, cuts, out_host) != expected:
         raise SystemExit("end-to-end join: wrong pair count")
@@ -674,10 +726,7 @@ def run_gpu(args):
 
     cpu = None
     if rank == 0 and not args.no_cpu:
-        cores = os.cpu_count() or 1
-        model = CpuModel(wl, cores)
-        cpu = {"value": model.value_from(model.t2, model.n2), "unit": UNIT, "cores": cores, "kind": "oracle",
-               "sample": model.sample_text()}
+        cpu = cpu_baseline_full(wl, os.cpu_count() or 1)
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -685,7 +734,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
         "config": {"workload": workload_desc(args.workload, spec), "load_factor": lf,
                    "load_factor_tuning_ms": lf_tuning or None,
-                   "l2": f"inputs larger than L2 ({key_bytes / 1e9:.2f} GB of keys), no flush",
+                   "l2": f"L2 flushed between timed steps ({FLUSH_BYTES >> 20} MB written); ms_per_step is the "
+                         f"steps' own CUDA-event time, flushes excluded; inputs {key_bytes / 1e9:.2f} GB of keys",
                    "parallelism": f"replicas{world}"},
         "p50_ms": pct(step_ms, 50), "p99_ms": pct(step_ms, 99),
         "probe_tuples_per_s_probe_phase": n / ((kernels["sig_S"]["ms"] + kernels["verify"]["ms"]) * 1e-3),
@@ -700,17 +750,30 @@ def run_gpu(args):
         "pairs": total_pairs,
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_s * 1e3, "chunks": len(cuts) - 1,
+                "ms_per_step": e2e_s * 1e3, "chunks": len(cuts) - 1, "h2d_pinned_gbs": h2d_gbs,
+                "copy_bound_ms": (h2d + d2h) / (h2d_gbs * 1e9) * 1e3,
                 "path": "stream.HostStreamJoin: pinned host R and S, S copied in chunks under the kernels"},
         "gpu_launches": 4 * args.steps,
         "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": kernels[dom]["gbps"], "peak": hbm,
                      "peak_kind": f"{peak_kind} (copy bandwidth, burst)", "unit": "GB/s",
                      "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
-                     "algorithmic_bytes": alg[dom]},
+                     "algorithmic_bytes": alg[dom],
+                     "kernels": {ph: {"kernel": KERNEL_NAMES[ph], "ms": round(kernels[ph]["ms"], 4),
+                                      "achieved": round(kernels[ph]["gbps"], 1),
+                                      "frac": round(kernels[ph]["frac_hbm"], 4)} for ph in PH}},
         "cpu_baseline": cpu,
         "gen_s": t_gen,
         **extra,
     }
+    # a compact summary at the end of the line (where a truncated tail still shows it)
+    summ = {"step_ms": round(ms_per_step, 4),
+            "kernel_frac_hbm": {ph: round(kernels[ph]["frac_hbm"], 3) for ph in PH},
+            "speedup_vs_fullstring": {k: round(v, 3) for k, v in line["speedup_vs_fullstring"].items()},
+            "e2e_ms": round(e2e_s * 1e3, 2), "h2d_pinned_gbs": round(h2d_gbs, 1)}
+    if "length_sweep" in extra:
+        summ["length_sweep_speedup_vs_tagged"] = {str(r["key_bytes"]): round(r["speedup_vs_tagged"], 3)
+                                                  for r in extra["length_sweep"]["rows"]}
+    line["summary"] = summ
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -719,8 +782,9 @@ def run_gpu(args):
 
 
 # revision of each kernel's code; profiles/traffic.json holds counters per revision
-KERNEL_REVS = {"sig_kernel_ws": "v3", "build_kernel": "v8", "verify_kernel": "v15"}
-KERNEL_NAMES = {"sig_R": "sig_kernel_ws", "sig_S": "sig_kernel_ws", "build": "build_kernel", "verify": "verify_kernel"}
+KERNEL_REVS = {"sig_key_kernel": "v1", "build_kernel": "v8", "verify_kernel": "v16"}
+KERNEL_NAMES = {"sig_R": "sig_key_kernel", "sig_S": "sig_key_kernel", "build": "build_kernel",
+                "verify": "verify_kernel"}
 
 
 def main():

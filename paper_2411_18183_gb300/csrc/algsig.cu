@@ -30,6 +30,10 @@ __device__ uint16_t g_log[65536];
 __device__ uint16_t g_alog[65536];
 // constant-multiply tables of the tile combination (rounds.cuh), set up once per device
 __device__ uint16_t g_const[17 * 512];
+// image of the shared-memory reduction tables (gf16.cuh: 256 rows, each entry
+// replicated once per bank), set up once per device and copied by the blocks
+// that need the tables, so that no block computes them
+__device__ uint4 g_red_img[256 * 64 / 4];
 }  // namespace algsig
 
 #include "rounds.cuh"
@@ -1237,6 +1241,18 @@ static as_status ensure_device(DeviceState** out) {
       }
     }
     if ((e = cudaMemcpyToSymbol(g_const, h_const, sizeof(h_const))) != cudaSuccess) return cuda_fail(e, "table setup");
+    {  // the reduction tables' shared-memory image: row b, word l: T16[b] (l < 32), T24[b] (l >= 32)
+      static uint32_t h_red[kRedWords];
+      for (uint32_t b = 0; b < 256; b++) {
+        uint32_t t16 = b, t24 = b;
+        for (int i = 0; i < 16; i++) t16 = gf_times_x(t16);
+        for (int i = 0; i < 24; i++) t24 = gf_times_x(t24);
+        t16 ^= b << 16;
+        t24 ^= b << 24;
+        for (int l = 0; l < 64; l++) h_red[b * 64 + l] = l < 32 ? t16 : t24;
+      }
+      if ((e = cudaMemcpyToSymbol(g_red_img, h_red, sizeof(h_red))) != cudaSuccess) return cuda_fail(e, "table setup");
+    }
     // prefix-scan tables: x^(-8 k 2^s) at (k-1)*kPLevels+s
     static uint16_t h_pconst[kPConst * 512];
     for (int t = 0; t < kPConst; t++) {

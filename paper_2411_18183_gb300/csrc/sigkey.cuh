@@ -60,6 +60,10 @@ constexpr int kLKDepth = ALGSIG_LK_DEPTH;             // 32-byte blocks in fligh
 #endif
 constexpr int kLKWin = ALGSIG_LK_WIN;                 // keys per sorting window (a power of two)
 constexpr uint32_t kLKNoKey = 0xFFFFFFFFu;            // empty sorting entry
+// relations of this many keys and more are split over the warps by key bytes (a
+// search in the offsets); smaller ones by key count, which saves the search's
+// dependent loads where they would be a large share of the kernel's time
+constexpr uint64_t kLKSearchFrom = 1ull << 19;
 constexpr int kLKIdxBits = kLKWin == 256 ? 8 : (kLKWin == 512 ? 9 : (kLKWin == 128 ? 7 : 10));
 static_assert((1 << kLKIdxBits) == kLKWin, "window sizes 128, 256, 512, 1024");
 constexpr uint32_t kLKNbCap = (1u << (31 - kLKIdxBits)) - 1u;   // block counts above sort together
@@ -217,6 +221,7 @@ __device__ __forceinline__ void lk_sort_window(LKWarp& W, uint32_t wn, uintptr_t
     W.order[i] = e;
   }
   __syncwarp();
+  if (wn <= 32) return;                              // one group: nothing to balance
   for (uint32_t k = 2; k <= (uint32_t)kLKWin; k <<= 1) {
     for (uint32_t j = k >> 1; j > 0; j >>= 1) {
       for (uint32_t t = lane; t < (uint32_t)kLKWin / 2; t += 32) {
@@ -429,22 +434,28 @@ __global__ void __launch_bounds__(kLKThreads, 1) sig_key_kernel(const uint8_t* _
     reinterpret_cast<uint32_t*>(inv32)[i] = reinterpret_cast<const uint32_t*>(g_const + 16 * 512)[i];
   const int wib = threadIdx.x >> 5;
   LKWarp& W = warps[wib];
-  static_assert(kLKWarps * sizeof(LKWarp) >= 2048, "table scratch fits the warps' window state");
-  init_red_tables(red, reinterpret_cast<uint32_t*>(&warps[0]));   // ends with __syncthreads()
+  // the warp's keys and its first window's offsets first, so that their loads overlap the tables' copy
+  const uint64_t warp = (uint64_t)blockIdx.x * kLKWarps + wib;
+  const uint64_t nwarps = (uint64_t)gridDim.x * kLKWarps;
+  uint64_t k_lo, k_hi;
+  if (n < kLKSearchFrom) {                          // small relation: equal key counts, no search
+    k_lo = (uint64_t)((unsigned __int128)n * warp / nwarps);
+    k_hi = (uint64_t)((unsigned __int128)n * (warp + 1) / nwarps);
+  } else {
+    warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
+  }
+  if (k_lo < k_hi) lk_prefetch_window(W, off, k_lo, k_hi);
+  // readable bytes of the arena: from its start to the 16-byte boundary after the last key byte
+  const uint8_t* lim_lo = arena;
+  const uint8_t* lim_hi = arena + ((__ldg(off + n) + 15) & ~15ull);
+  for (int i = threadIdx.x; i < kRedWords / 4; i += blockDim.x)   // the reduction tables, from their image
+    reinterpret_cast<uint4*>(red)[i] = g_red_img[i];
+  __syncthreads();
+  if (k_lo >= k_hi) return;
   using Cursor = typename std::conditional<AT400, RedCursorAt400, RedCursor>::type;
   Cursor rc;
   if constexpr (AT400) rc = red_cursor_at400(); else rc = red_cursor(red);
 
-  const uint64_t warp = (uint64_t)blockIdx.x * kLKWarps + wib;
-  const uint64_t nwarps = (uint64_t)gridDim.x * kLKWarps;
-  uint64_t k_lo, k_hi;
-  warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
-  if (k_lo >= k_hi) return;
-  // readable bytes of the arena: from its start to the 16-byte boundary after the last key byte
-  const uint8_t* lim_lo = arena;
-  const uint8_t* lim_hi = arena + ((off[n] + 15) & ~15ull);
-
-  lk_prefetch_window(W, off, k_lo, k_hi);
   for (uint64_t wb = k_lo; wb < k_hi;) {
     cp_async_wait_all();                            // the window's offsets
     __syncwarp();
