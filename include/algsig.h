@@ -78,14 +78,6 @@ const char* as_last_error(void);
 /* Name of a status code. */
 const char* as_status_string(as_status st);
 
-/* Health check: the number of bounded waits that gave up on the current
- * device since the library was loaded (the signature kernel's warps hand rounds
- * to each other through waits with an iteration limit; a wait that runs out
- * counts here and its warp stops instead of hanging).  0 in a healthy run.
- * Synchronises the device's legacy stream.  Errors: AS_ERR_INVALID for a null
- * pointer, AS_ERR_CUDA. */
-as_status as_device_faults(uint64_t* h_count);
-
 /* Library version, as 10000*major + 100*minor + patch. */
 int as_version(void);
 

@@ -30,7 +30,7 @@ AS_ERR_TABLE_FULL = 4
 AS_ERR_CUDA = 5
 AS_ERR_UNSUPPORTED = 6
 
-EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_device_faults", "as_sig_compute", "as_sig_compute_n",
+EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_sig_compute_n",
            "as_sig_compute_gf8",
            "as_sig_prefix_ws_bytes", "as_sig_prefix_offsets", "as_sig_prefixes", "as_join_table_bytes",
            "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_probe_sigs", "as_join_probe_mode", "as_join_ws_bytes", "as_join",
@@ -74,8 +74,6 @@ def load(path: str | None = None):
         lib.as_sig_compute.restype = S
         lib.as_sig_compute_n.argtypes = [P, P, U64, S, P, P]
         lib.as_sig_compute_n.restype = S
-        lib.as_device_faults.argtypes = [ctypes.POINTER(ctypes.c_uint64)]
-        lib.as_device_faults.restype = S
         lib.as_sig_compute_gf8.argtypes = [P, P, U64, P, P]
         lib.as_sig_compute_gf8.restype = S
         lib.as_sig_prefix_ws_bytes.argtypes = [U64]
@@ -184,13 +182,6 @@ def sig_compute(rel: DeviceRelation, out: torch.Tensor | None = None, stream=Non
     else:
         _check(lib.as_sig_compute_n(_ptr(rel.arena), _ptr(rel.off), n, n_components, _ptr(out), _stream(stream)))
     return out
-
-
-def device_faults() -> int:
-    """as_device_faults: bounded waits that gave up on the current device (0 when healthy)."""
-    v = ctypes.c_uint64(0)
-    _check(load().as_device_faults(ctypes.byref(v)))
-    return int(v.value)
 
 
 def sig_compute_gf8(rel: DeviceRelation, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:

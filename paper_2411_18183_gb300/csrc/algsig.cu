@@ -1,14 +1,15 @@
 // algsig.cu -- sm_103a kernels and C ABI of the algebraic-signature equi-join.
 //
 // Pipeline of one join T = Join(R, S) (Figure 2 of the paper):
-//   1. signatures of R      sig_kernel     (Section 3.1)
+//   1. signatures of R      sig_key_kernel (Section 3.1; sigkey.cuh)
 //   2. build H_sign on R    build_kernel   (Figure 2, formula 3)
-//   3. probe with S         sig_kernel on S, then verify_kernel: table walk,
-//                           byte-exact verification, output compaction
+//   3. probe with S         sig_key_kernel on S, then verify_kernel: table
+//                           walk, byte-exact verification, output compaction
 //                           (formulas 4-5)
-// The signature work of 1 and 3 is the warp tile walk of rounds.cuh: each
-// warp streams its share of the arena through shared memory with cp.async,
-// two rounds (32 tiles of kTile bytes each) ahead of the arithmetic.
+// sig_key_kernel computes one key per lane (keys grouped by length, a
+// bit-sliced Horner state for three of the four components).  A batch whose
+// joins' rows are not one run of the relation uses sig_kernel, the warp tile
+// walk of rounds.cuh over the joins' row ranges.
 #include <cuda_runtime.h>
 
 #include <cstdarg>
@@ -222,225 +223,6 @@ __device__ __forceinline__ void sig_walk(const uint8_t* __restrict__ arena, cons
     if (lane == 0) sig_out[pd.key + out_shift] = s;
   }
   cp_async_wait_all();
-}
-
-// ----------------------------------------------------------------------------
-// Warp-specialised signature walk: each stream of keys is served by a pair of
-// warps.  The control warp plans the rounds, stages their spans with
-// cp.async, combines the tile values and finishes the keys (the latency-bound
-// part of the walk); the math warp runs only the tile arithmetic.  They hand
-// rounds over through two plan / value slots and four mbarriers, so the math
-// warp computes round r+1 while the control warp combines round r and stages
-// round r+2.  Every wait is bounded: a wait that gives up counts a timeout in
-// g_walk_timeouts and the warp leaves.
-// ----------------------------------------------------------------------------
-
-constexpr int kWSPairs = 8;
-constexpr int kWSThreads = 64 * kWSPairs;
-constexpr uint32_t kWaitTries = 1u << 22;
-__device__ unsigned long long g_walk_timeouts;
-
-// what the tile arithmetic needs of a lane's plan
-struct TileJob {
-  uint32_t rel0;     // padded-free span offset of the tile's first aligned chunk
-  uint32_t bits;     // nc | odd << 5 | lo << 6 | first << 10 | last << 11 | tail_e << 12; kStopJob: no more rounds
-};
-constexpr uint32_t kStopJob = 0xFFFFFFFFu;
-
-struct PairShared {
-  TileJob job[2][32];
-  uint64_t val[2][32];
-  uint64_t bar[4];   // ready[0..1] (control -> math), done[0..1] (math -> control)
-};
-// tables | constants | staging buffers | pair hand-over state (the tables' init
-// scratch lives in the first staging buffer, unused until the walk starts)
-constexpr size_t kSmemWSTables = (size_t)kRedBytes;
-constexpr size_t kSmemWS = kSmemWSTables + kConstBytes + (size_t)kWSPairs * 2 * kBufBytes +
-                           (size_t)kWSPairs * sizeof(PairShared);
-static_assert(kSmemWS <= 232448, "warp-specialised signature walk: shared memory");
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* b, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(b)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* b) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(b)) : "memory");
-}
-// wait for the phase of parity `parity` to complete; false after kWaitTries attempts
-__device__ __forceinline__ bool mbar_wait(uint64_t* b, uint32_t parity) {
-  const uint32_t a = smem_addr(b);
-  for (uint32_t it = 0; it < kWaitTries; ++it) {
-    uint32_t ok;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(ok)
-        : "r"(a), "r"(parity)
-        : "memory");
-    if (ok) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ TileJob job_of(const Plan& p) {
-  TileJob j;
-  j.rel0 = (uint32_t)(p.cbase - p.span_lo);
-  j.bits = p.nc | (p.odd << 5) | (p.lo << 6) | ((p.tile == 0 ? 1u : 0u) << 10) | ((p.last ? 1u : 0u) << 11) |
-           (p.tail_e << 12);
-  return j;
-}
-__device__ __forceinline__ Plan plan_of(const TileJob& j) {
-  Plan p;
-  p.cbase = j.rel0;
-  p.span_lo = 0;
-  p.nc = j.bits & 31u;
-  p.odd = (j.bits >> 5) & 1u;
-  p.lo = (j.bits >> 6) & 15u;
-  p.tile = ((j.bits >> 10) & 1u) ? 0u : 1u;
-  p.last = (j.bits >> 11) & 1u;
-  p.tail_e = (j.bits >> 12) & 31u;
-  return p;
-}
-
-// control warp: hand a round to the math warp (its data has landed)
-__device__ __forceinline__ void publish(PairShared& ps, int slot, const Plan& p) {
-  const int lane = threadIdx.x & 31;
-  TileJob j;
-  if (!p.valid) {
-    j.rel0 = 0;
-    j.bits = kStopJob;
-  } else if (!p.active) {
-    j.rel0 = 0;
-    j.bits = 0;                                      // nc = 0: no tile
-  } else {
-    j = job_of(p);
-  }
-  ps.job[slot][lane] = j;
-  __syncwarp();
-  if (lane == 0) mbar_arrive(&ps.bar[slot]);
-}
-
-template <int NCOMP, class Cursor>
-__device__ void ws_math(PairShared& ps, uint8_t* bufs, const Cursor& rc) {
-  const int lane = threadIdx.x & 31;
-  for (uint32_t r = 0;; ++r) {
-    const int s = (int)(r & 1u);
-    if (!mbar_wait(&ps.bar[s], (r >> 1) & 1u)) {
-      if (lane == 0) atomicAdd(&g_walk_timeouts, 1ull);
-      return;
-    }
-    const TileJob j = ps.job[s][lane];
-    if (__shfl_sync(kFull, j.bits, 0) == kStopJob) return;   // the control warp writes it to every lane
-    uint32_t a1, a2, a3, a4;
-    tile_accumulate<NCOMP>(bufs + s * kBufBytes, 0, plan_of(j), rc, a1, a2, a3, a4);
-    ps.val[s][lane] = pack4(a1, a2, a3, a4);
-    __syncwarp();
-    if (lane == 0) mbar_arrive(&ps.bar[2 + s]);
-  }
-}
-
-template <class Cursor>
-__device__ void ws_control(const uint8_t* __restrict__ arena, const uint64_t* __restrict__ off, uint64_t k_lo,
-                           uint64_t k_hi, uint64_t* __restrict__ sig_out, uint8_t* bufs, PairShared& ps,
-                           const uint16_t* ctab, const Cursor& rc) {
-  const int lane = threadIdx.x & 31;
-  Plan cur = plan_round(plan_load(off, k_lo, k_hi), k_lo, k_hi, 0);
-  issue_span(bufs, arena, cur);
-  Plan nxt = plan_round(plan_load(off, cur.kc_next, k_hi), cur.kc_next, k_hi, cur.tc_next);
-  issue_span(bufs + kBufBytes, arena, nxt);
-  cp_async_wait_prev();                              // round 0 has landed
-  __syncwarp();
-  publish(ps, 0, cur);
-  uint64_t carry = 0;
-  Pending pd;
-  pd.valid = false;
-  for (uint32_t r = 0; cur.valid; ++r) {
-    const int s = (int)(r & 1u);
-    cp_async_wait_all();                             // round r+1 has landed (the only group in flight)
-    __syncwarp();
-    publish(ps, s ^ 1, nxt);
-    const PlanLoad ahead = plan_load(off, nxt.kc_next, k_hi);
-    if (!mbar_wait(&ps.bar[2 + s], (r >> 1) & 1u)) {  // round r's tile values
-      if (lane == 0) atomicAdd(&g_walk_timeouts, 1ull);
-      cp_async_wait_all();
-      return;
-    }
-    const uint64_t tv = ps.val[s][lane];
-    if (pd.valid) pending_alogs(pd);                // its logs were loaded one round ago
-    __syncwarp();
-    const Plan nn = plan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
-    issue_span(bufs + s * kBufBytes, arena, nn);     // round r+2 into the buffer round r used
-    const uint64_t V = scan_round(cur, cur.active ? tv : 0ull, ctab);
-    const bool head = cur.active && (uint32_t)lane == cur.slot0;
-    const bool fresh = cur.q != 0 || cur.tc == 0;
-    const bool hjob = head && fresh && cur.slot0 + cur.rq <= 32u;
-    uint64_t P = 0;
-    bool pjob = false;
-    if (pd.valid) {
-      P = pending_value(pd);
-      if (pd.complete) pjob = true; else carry = P;
-      pd.valid = false;
-    }
-    const uint32_t hm = __ballot_sync(kFull, hjob);
-    const int plane = pjob ? __ffs(~hm) - 1 : -1;
-    if (pjob && plane < 0) {
-      const uint64_t sg = lo_correct(ctab, P, pd.lo, rc);
-      if (lane == 0) sig_out[pd.key] = sg;
-      pjob = false;
-    }
-    const bool mine = pjob && lane == plane;
-    const uint64_t fin = lo_correct(ctab, hjob ? V : P, hjob ? cur.lo : pd.lo, rc);
-    if (hjob) sig_out[cur.kc + (uint64_t)cur.q] = fin;
-    else if (mine) sig_out[pd.key] = fin;
-    if (cur.tc > 0) {
-      pd.valid = true;
-      pd.key = cur.kc;
-      pd.carry = carry;
-      pd.lo = __shfl_sync(kFull, cur.lo, 0);
-      pd.complete = __shfl_sync(kFull, cur.rq, 0) <= 32u;
-      pending_logs(pd, __shfl_sync(kFull, V, 0), cur.tc);
-    }
-    const uint64_t vlast = __shfl_sync(kFull, V, (int)cur.s31);
-    if (cur.carries && !(cur.s31 == 0 && cur.tc > 0)) carry = vlast;
-    cur = nxt;
-    nxt = nn;
-  }
-  if (pd.valid) {
-    pending_alogs(pd);
-    const uint64_t sg = lo_correct(ctab, pending_value(pd), pd.lo, rc);
-    if (lane == 0) sig_out[pd.key] = sg;
-  }
-  cp_async_wait_all();
-}
-
-template <bool AT400, int NCOMP>
-__global__ void __launch_bounds__(kWSThreads, 1) sig_kernel_ws(const uint8_t* __restrict__ arena,
-                                                               const uint64_t* __restrict__ off, uint64_t n,
-                                                               uint64_t* __restrict__ sig_out) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
-  uint16_t* ctab = reinterpret_cast<uint16_t*>(smem + kSmemWSTables);
-  uint8_t* buf0 = smem + kSmemWSTables + kConstBytes;
-  for (int i = threadIdx.x; i < kConstEntries / 2; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(ctab)[i] = reinterpret_cast<const uint32_t*>(g_const)[i];
-  PairShared* pshared = reinterpret_cast<PairShared*>(buf0 + (size_t)kWSPairs * 2 * kBufBytes);
-  if (threadIdx.x < kWSPairs * 4) mbar_init(&pshared[threadIdx.x / 4].bar[threadIdx.x % 4], 1);
-  init_red_tables(red, reinterpret_cast<uint32_t*>(buf0));   // scratch in a staging buffer; ends with __syncthreads()
-  using Cursor = typename std::conditional<AT400, RedCursorAt400, RedCursor>::type;
-  Cursor rc;
-  if constexpr (AT400) rc = red_cursor_at400(); else rc = red_cursor(red);
-  const int w = threadIdx.x >> 5;
-  const int pair = w % kWSPairs;
-  uint8_t* bufs = buf0 + (size_t)pair * 2 * kBufBytes;
-  PairShared& ps = pshared[pair];
-  if (w < kWSPairs) {
-    ws_math<NCOMP>(ps, bufs, rc);
-  } else {
-    const uint64_t stream = (uint64_t)blockIdx.x * kWSPairs + pair;
-    const uint64_t nstreams = (uint64_t)gridDim.x * kWSPairs;
-    uint64_t k_lo, k_hi;
-    warp_key_range(off, n, stream, nstreams, &k_lo, &k_hi);
-    ws_control(arena, off, k_lo, k_hi, sig_out, bufs, ps, ctab, rc);
-  }
 }
 
 }  // namespace algsig
@@ -1277,13 +1059,6 @@ static as_status ensure_device(DeviceState** out) {
       for (const void* f : fns)
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) != cudaSuccess)
           return cuda_fail(e, "kernel attribute");
-      const void* wfns[4] = {reinterpret_cast<const void*>(sig_kernel_ws<false, 4>),
-                             reinterpret_cast<const void*>(sig_kernel_ws<true, 4>),
-                             reinterpret_cast<const void*>(sig_kernel_ws<false, 2>),
-                             reinterpret_cast<const void*>(sig_kernel_ws<true, 2>)};
-      for (const void* f : wfns)
-        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemWS)) != cudaSuccess)
-          return cuda_fail(e, "kernel attribute");
       const void* kfns[4] = {reinterpret_cast<const void*>(sig_key_kernel<false, 4>),
                              reinterpret_cast<const void*>(sig_key_kernel<true, 4>),
                              reinterpret_cast<const void*>(sig_key_kernel<false, 2>),
@@ -1441,19 +1216,6 @@ as_status as_sig_compute_gf8(const uint8_t* d_arena, const uint64_t* d_off, uint
   sig8_kernel<<<blocks, kG8Threads, kSmemSig8, (cudaStream_t)stream>>>(d_arena, d_off, n, d_sig_out);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "byte-symbol signature kernel launch");
-  return AS_OK;
-}
-
-as_status as_device_faults(uint64_t* h_count) {
-  NvtxRange nvtx_range("as_device_faults");
-  if (!h_count) return fail(AS_ERR_INVALID, "as_device_faults: null pointer");
-  DeviceState* d = nullptr;
-  as_status st = ensure_device(&d);
-  if (st != AS_OK) return st;
-  unsigned long long v = 0;
-  cudaError_t e = cudaMemcpyFromSymbol(&v, g_walk_timeouts, sizeof(v));
-  if (e != cudaSuccess) return cuda_fail(e, "fault counter");
-  *h_count = (uint64_t)v;
   return AS_OK;
 }
 
