@@ -197,7 +197,7 @@ def batch_leg(ag, steps: int):
     R = ag.DeviceRelation.from_host(bw.R.arena, bw.R.off, None)
     S = ag.DeviceRelation.from_host(bw.S.arena, bw.S.off, None)
     caps = [max(64, int(e * 1.25) + 64) for e in bw.expected]
-    gb, tried = tune.autotune(R, S, bw.ranges, caps)
+    gb, tried, shape_tried = tune.autotune(R, S, bw.ranges, caps)
     gb.counts.zero_()
     gb.replay()
     torch.cuda.synchronize()
@@ -210,7 +210,8 @@ def batch_leg(ag, steps: int):
                         f"{list(spec.bands)} B, {int(spec.frac_copy * 100)}% S copies (relation sizes of the "
                         f"512-join batch / {BATCH_SCALE})",
             "rows": {"R": bw.R.n, "S": n}, "key_bytes": bw.R.nbytes + bw.S.nbytes,
-            "load_factor": gb.lf, "tuning_ms": tried, "ms_per_batch": ms,
+            "load_factor": gb.lf, "tuning_ms": tried, "sig_shape": ag.sig_shapes()[gb.shape],
+            "shape_tuning_ms": {str(ag.sig_shapes()[k]): v for k, v in shape_tried.items()}, "ms_per_batch": ms,
             "joins_per_s": spec.n_joins / (ms * 1e-3), "tuples_per_s": n / (ms * 1e-3),
             "gpu_launches_per_batch": 5, "cuda_graph": True}
 
@@ -319,6 +320,7 @@ _flush_buf = None
 
 def flush_l2(stream):
     """Evict L2 by writing a buffer four times its size on the stream."""
+    import torch
     global _flush_buf
     if _flush_buf is None:
         _flush_buf = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
@@ -331,6 +333,7 @@ def tune_load_factor(make_run, stream):
     over two joins per round, in TUNE_ROUNDS rounds that interleave the
     candidates (so a drift of the clock or the memory system hits them all);
     a candidate's time is its median round.  Returns (best, {lf: ms})."""
+    import torch
     runs = {}
     for cand in LOAD_FACTORS:
         runs[cand] = make_run(cand)

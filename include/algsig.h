@@ -107,6 +107,23 @@ as_status as_sig_compute_n(const uint8_t* d_arena, const uint64_t* d_off, uint64
                            uint64_t* d_sig_out, as_stream stream);
 
 /*
+ * Launch shapes of the signature kernel of as_sig_compute (Section 3.1 fixes
+ * the result, not the schedule): shape s runs warps[s] warps per block, one
+ * key per lane, with depth[s] 32-byte blocks of each key in flight.  Every
+ * shape gives the same signatures; which is fastest depends on the key-length
+ * mix, so a tuner times them.  Shape 0 is the default of as_sig_compute.
+ *
+ * as_sig_shapes -- writes up to cap (warps, depth) pairs (either array may be
+ *   null) and returns the number of shapes.
+ * as_sig_compute_shape -- as_sig_compute_n with an explicit shape.  Errors: as
+ *   for as_sig_compute_n, and AS_ERR_INVALID for a shape outside
+ *   [0, as_sig_shapes(0, 0, 0)).
+ */
+int as_sig_shapes(int* warps, int* depth, int cap);
+as_status as_sig_compute_shape(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, int n_components,
+                               int shape, uint64_t* d_sig_out, as_stream stream);
+
+/*
  * as_sig_compute_gf8 -- signatures with byte symbols (Section 3.1: a symbol
  * is a byte or a double byte): GF(2^8) with field polynomial
  * x^8 + x^4 + x^3 + x^2 + 1, alpha_k = x^k, p_i = byte i,
@@ -390,6 +407,11 @@ typedef struct as_batch {
      * join order, form one ascending contiguous range (the signatures then run
      * as those of a single relation); AS_ROWS_SCATTERED otherwise. */
     uint64_t r_first, s_first;
+    /* Shape of the signature kernel for a side whose rows form one run (see
+     * as_sig_shapes); as_join_batch_prepare sets 0, a tuner may change it
+     * before as_join_batch_run. */
+    int32_t sig_shape;
+    int32_t reserved0;
 } as_batch;
 #define AS_ROWS_SCATTERED (~(uint64_t)0)
 

@@ -31,7 +31,7 @@ AS_ERR_CUDA = 5
 AS_ERR_UNSUPPORTED = 6
 
 EXPORTS = ("as_last_error", "as_status_string", "as_version", "as_sig_compute", "as_sig_compute_n",
-           "as_sig_compute_gf8",
+           "as_sig_shapes", "as_sig_compute_shape", "as_sig_compute_gf8",
            "as_sig_prefix_ws_bytes", "as_sig_prefix_offsets", "as_sig_prefixes", "as_join_table_bytes",
            "as_join_build", "as_join_probe_ws_bytes", "as_join_probe", "as_join_probe_sigs", "as_join_probe_mode", "as_join_ws_bytes", "as_join",
            "as_join_part_ws_bytes", "as_join_partitioned", "as_join_prefix_ws_bytes", "as_join_prefix", "as_baseline_ws_bytes", "as_baseline_join")
@@ -74,6 +74,10 @@ def load(path: str | None = None):
         lib.as_sig_compute.restype = S
         lib.as_sig_compute_n.argtypes = [P, P, U64, S, P, P]
         lib.as_sig_compute_n.restype = S
+        lib.as_sig_shapes.argtypes = [P, P, S]
+        lib.as_sig_shapes.restype = S
+        lib.as_sig_compute_shape.argtypes = [P, P, U64, S, S, P, P]
+        lib.as_sig_compute_shape.restype = S
         lib.as_sig_compute_gf8.argtypes = [P, P, U64, P, P]
         lib.as_sig_compute_gf8.restype = S
         lib.as_sig_prefix_ws_bytes.argtypes = [U64]
@@ -169,15 +173,29 @@ def version() -> int:
     return int(load().as_version())
 
 
+def sig_shapes() -> list:
+    """as_sig_shapes: the (warps per block, blocks in flight per key) launch shapes
+    of the signature kernel; index 0 is the default."""
+    lib = load()
+    cnt = int(lib.as_sig_shapes(None, None, 0))
+    w, d = (ctypes.c_int * cnt)(), (ctypes.c_int * cnt)()
+    lib.as_sig_shapes(w, d, cnt)
+    return [(int(w[i]), int(d[i])) for i in range(cnt)]
+
+
 def sig_compute(rel: DeviceRelation, out: torch.Tensor | None = None, stream=None,
-                n_components: int = 4) -> torch.Tensor:
+                n_components: int = 4, shape: int | None = None) -> torch.Tensor:
     """as_sig_compute (n_components = 4) or as_sig_compute_n (2: the paper's two-symbol
-    signature, components 3 and 4 zero): uint64 signature of every key (as int64 bits)."""
+    signature, components 3 and 4 zero): uint64 signature of every key (as int64 bits).
+    With `shape`, as_sig_compute_shape with that launch shape (see sig_shapes)."""
     lib = load()
     n = rel.n
     if out is None:
         out = torch.empty(max(n, 0), dtype=torch.int64, device=rel.arena.device)
-    if n_components == 4:
+    if shape is not None:
+        _check(lib.as_sig_compute_shape(_ptr(rel.arena), _ptr(rel.off), n, n_components, shape, _ptr(out),
+                                        _stream(stream)))
+    elif n_components == 4:
         _check(lib.as_sig_compute(_ptr(rel.arena), _ptr(rel.off), n, _ptr(out), _stream(stream)))
     else:
         _check(lib.as_sig_compute_n(_ptr(rel.arena), _ptr(rel.off), n, n_components, _ptr(out), _stream(stream)))
@@ -456,7 +474,8 @@ class Batch(ctypes.Structure):
     _fields_ = [("descs", ctypes.c_void_p), ("slots", ctypes.c_void_p), ("sigR", ctypes.c_void_p),
                 ("sigS", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("n_joins", ctypes.c_uint64),
                 ("slots_total", ctypes.c_uint64), ("mR", ctypes.c_uint64), ("nS", ctypes.c_uint64),
-                ("r_first", ctypes.c_uint64), ("s_first", ctypes.c_uint64)]
+                ("r_first", ctypes.c_uint64), ("s_first", ctypes.c_uint64), ("sig_shape", ctypes.c_int32),
+                ("reserved0", ctypes.c_int32)]
 
 
 def _batch_lib():

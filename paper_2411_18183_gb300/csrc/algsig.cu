@@ -18,6 +18,7 @@
 #include <mutex>
 #include <string>
 #include <type_traits>
+#include <utility>
 #include <vector>
 
 #include "../../include/algsig.h"
@@ -958,6 +959,41 @@ static as_status cuda_fail(cudaError_t e, const char* where) {
   return fail(AS_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+// The instantiations of the signature kernel: table addressing (AT400),
+// components and shape (warps per block, blocks in flight per key).
+static_assert(kLKShapeCount == 3, "one case per shape below");
+template <bool AT400, int NCOMP, int SHAPE>
+static cudaError_t key_kernel_attr() {
+  constexpr LKShape k = kLKShapes[SHAPE];
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(sig_key_kernel<AT400, NCOMP, k.warps, k.depth>),
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lk_smem_bytes(k.warps));
+}
+template <bool AT400, int NCOMP>
+static cudaError_t key_kernel_attrs() {
+  cudaError_t e = key_kernel_attr<AT400, NCOMP, 0>();
+  if (e == cudaSuccess) e = key_kernel_attr<AT400, NCOMP, 1>();
+  if (e == cudaSuccess) e = key_kernel_attr<AT400, NCOMP, 2>();
+  return e;
+}
+template <bool AT400, int NCOMP, int SHAPE>
+static void key_kernel_launch(int sms, const uint8_t* arena, const uint64_t* off, uint64_t n, uint64_t* out,
+                              cudaStream_t s) {
+  constexpr LKShape k = kLKShapes[SHAPE];
+  const uint64_t want = (n + 32ull * k.warps - 1) / (32ull * k.warps);
+  const unsigned blocks = (unsigned)(want < (uint64_t)sms ? (want < 1 ? 1 : want) : (uint64_t)sms);
+  sig_key_kernel<AT400, NCOMP, k.warps, k.depth><<<blocks, 32 * k.warps, lk_smem_bytes(k.warps), s>>>(arena, off, n,
+                                                                                                      out);
+}
+template <bool AT400, int NCOMP>
+static void key_kernel_launch_shape(int shape, int sms, const uint8_t* arena, const uint64_t* off, uint64_t n,
+                                    uint64_t* out, cudaStream_t s) {
+  switch (shape) {
+    case 1: key_kernel_launch<AT400, NCOMP, 1>(sms, arena, off, n, out, s); break;
+    case 2: key_kernel_launch<AT400, NCOMP, 2>(sms, arena, off, n, out, s); break;
+    default: key_kernel_launch<AT400, NCOMP, 0>(sms, arena, off, n, out, s); break;
+  }
+}
+
 struct DeviceState {
   bool ready = false;
   int sms = 0;
@@ -1059,13 +1095,9 @@ static as_status ensure_device(DeviceState** out) {
       for (const void* f : fns)
         if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) != cudaSuccess)
           return cuda_fail(e, "kernel attribute");
-      const void* kfns[4] = {reinterpret_cast<const void*>(sig_key_kernel<false, 4>),
-                             reinterpret_cast<const void*>(sig_key_kernel<true, 4>),
-                             reinterpret_cast<const void*>(sig_key_kernel<false, 2>),
-                             reinterpret_cast<const void*>(sig_key_kernel<true, 2>)};
-      for (const void* f : kfns)
-        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLK)) != cudaSuccess)
-          return cuda_fail(e, "kernel attribute");
+      if ((e = key_kernel_attrs<true, 4>()) != cudaSuccess || (e = key_kernel_attrs<false, 4>()) != cudaSuccess ||
+          (e = key_kernel_attrs<true, 2>()) != cudaSuccess || (e = key_kernel_attrs<false, 2>()) != cudaSuccess)
+        return cuda_fail(e, "kernel attribute");
     }
     // where dynamic shared memory starts (the tables are its first bytes)
     if ((e = cudaFuncSetAttribute(dyn_smem_base_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) !=
@@ -1143,19 +1175,18 @@ static bool table_geometry(uint64_t m, float lf, uint64_t* cap, uint32_t* log2ca
 }
 
 static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t n, uint64_t* out, cudaStream_t s,
-                            int ncomp = 4) {
+                            int ncomp = 4, int shape = 0) {
   DeviceState* d = nullptr;
   as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
   if (n == 0) return AS_OK;
-  const uint64_t want = (n + 32ull * kLKWarps - 1) / (32ull * kLKWarps);
-  const unsigned blocks = (unsigned)(want < (uint64_t)d->sms ? (want < 1 ? 1 : want) : (uint64_t)d->sms);
+  if (shape < 0 || shape >= kLKShapeCount) return fail(AS_ERR_INVALID, "signature kernel shape %d", shape);
   if (ncomp == 2) {
-    if (d->tables_at400) sig_key_kernel<true, 2><<<blocks, kLKThreads, kSmemLK, s>>>(arena, off, n, out);
-    else sig_key_kernel<false, 2><<<blocks, kLKThreads, kSmemLK, s>>>(arena, off, n, out);
+    if (d->tables_at400) key_kernel_launch_shape<true, 2>(shape, d->sms, arena, off, n, out, s);
+    else key_kernel_launch_shape<false, 2>(shape, d->sms, arena, off, n, out, s);
   } else {
-    if (d->tables_at400) sig_key_kernel<true, 4><<<blocks, kLKThreads, kSmemLK, s>>>(arena, off, n, out);
-    else sig_key_kernel<false, 4><<<blocks, kLKThreads, kSmemLK, s>>>(arena, off, n, out);
+    if (d->tables_at400) key_kernel_launch_shape<true, 4>(shape, d->sms, arena, off, n, out, s);
+    else key_kernel_launch_shape<false, 4>(shape, d->sms, arena, off, n, out, s);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "signature kernel launch");
@@ -1289,6 +1320,26 @@ as_status as_sig_compute_n(const uint8_t* d_arena, const uint64_t* d_off, uint64
   if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute_n: null pointer");
   if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute_n: arena not 16-byte aligned");
   return launch_sig(d_arena, d_off, n, d_sig_out, (cudaStream_t)stream, n_components);
+}
+
+int as_sig_shapes(int* warps, int* depth, int cap) {
+  for (int i = 0; i < kLKShapeCount && i < cap; ++i) {
+    if (warps) warps[i] = kLKShapes[i].warps;
+    if (depth) depth[i] = kLKShapes[i].depth;
+  }
+  return kLKShapeCount;
+}
+
+as_status as_sig_compute_shape(const uint8_t* d_arena, const uint64_t* d_off, uint64_t n, int n_components,
+                               int shape, uint64_t* d_sig_out, as_stream stream) {
+  NvtxRange nvtx_range("as_sig_compute_shape");
+  if (n_components != 2 && n_components != 4)
+    return fail(AS_ERR_INVALID, "as_sig_compute_shape: n_components must be 2 or 4 (got %d)", n_components);
+  if (shape < 0 || shape >= kLKShapeCount)
+    return fail(AS_ERR_INVALID, "as_sig_compute_shape: shape %d outside [0, %d)", shape, kLKShapeCount);
+  if (n > 0 && (!d_arena || !d_off || !d_sig_out)) return fail(AS_ERR_INVALID, "as_sig_compute_shape: null pointer");
+  if (n > 0 && misaligned16(d_arena)) return fail(AS_ERR_INVALID, "as_sig_compute_shape: arena not 16-byte aligned");
+  return launch_sig(d_arena, d_off, n, d_sig_out, (cudaStream_t)stream, n_components, shape);
 }
 
 size_t as_join_table_bytes(uint64_t m, float load_factor) {
@@ -1973,6 +2024,8 @@ as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t
   };
   out->r_first = first_of_run(false);
   out->s_first = first_of_run(true);
+  out->sig_shape = 0;
+  out->reserved0 = 0;
   return AS_OK;
 }
 
@@ -2000,7 +2053,7 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
   batch_bytes_kernel<<<1, 1024, 0, s>>>(J, nj, d_offR, d_offS);
   if (b->mR > 0) {
     if (b->r_first != AS_ROWS_SCATTERED) {             // one run of rows: the single-relation kernel
-      if ((st = launch_sig(d_arenaR, d_offR + b->r_first, b->mR, b->sigR, s)) != AS_OK) return st;
+      if ((st = launch_sig(d_arenaR, d_offR + b->r_first, b->mR, b->sigR, s, 4, b->sig_shape)) != AS_OK) return st;
     } else {
       launch_sig_kernel<false>(d, walk_blocks(b->mR, d->sms), s, d_arenaR, d_offR, b->mR, b->sigR, J, nj);
     }
@@ -2011,7 +2064,7 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
   }
   if (b->nS > 0) {
     if (b->s_first != AS_ROWS_SCATTERED) {
-      if ((st = launch_sig(d_arenaS, d_offS + b->s_first, b->nS, b->sigS, s)) != AS_OK) return st;
+      if ((st = launch_sig(d_arenaS, d_offS + b->s_first, b->nS, b->sigS, s, 4, b->sig_shape)) != AS_OK) return st;
     } else {
       launch_sig_kernel<true>(d, walk_blocks(b->nS, d->sms), s, d_arenaS, d_offS, b->nS, b->sigS, J, nj);
     }

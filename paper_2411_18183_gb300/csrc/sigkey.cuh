@@ -40,21 +40,21 @@
 
 namespace algsig {
 
-#ifndef ALGSIG_LK_WARPS
-#define ALGSIG_LK_WARPS 24
-#endif
 #ifndef ALGSIG_LK_FINISH
 #define ALGSIG_LK_FINISH __forceinline__
 #endif
 #ifndef ALGSIG_LK_LDQUAL
 #define ALGSIG_LK_LDQUAL volatile
 #endif
-#ifndef ALGSIG_LK_DEPTH
-#define ALGSIG_LK_DEPTH 2
-#endif
-constexpr int kLKWarps = ALGSIG_LK_WARPS;             // warps per block (one block per SM)
-constexpr int kLKThreads = 32 * kLKWarps;
-constexpr int kLKDepth = ALGSIG_LK_DEPTH;             // 32-byte blocks in flight per key
+// Kernel shapes: warps per block (one block per SM) and 32-byte blocks in
+// flight per key.  More warps hide more latency, more blocks in flight per key
+// need more registers; the batch autotuner picks one per batch.  Shape 0 is
+// the default of single relations.
+struct LKShape {
+  int warps, depth;
+};
+constexpr LKShape kLKShapes[] = {{24, 2}, {16, 2}, {32, 1}};
+constexpr int kLKShapeCount = sizeof(kLKShapes) / sizeof(kLKShapes[0]);
 #ifndef ALGSIG_LK_WIN
 #define ALGSIG_LK_WIN 256
 #endif
@@ -73,8 +73,10 @@ struct LKWarp {
   uint32_t order[kLKWin];          // window entries sorted by (block count << 8 | index)
 };
 constexpr size_t kSmemLKMasks = 1056;                 // 33 rows of 32 bytes
-constexpr size_t kSmemLK = (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)kLKWarps * sizeof(LKWarp);
-static_assert(kSmemLK <= 232448, "lane-per-key signature kernel: shared memory");
+constexpr size_t lk_smem_bytes(int warps) {
+  return (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)warps * sizeof(LKWarp);
+}
+static_assert(lk_smem_bytes(32) <= 232448, "lane-per-key signature kernel: shared memory");
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
@@ -336,7 +338,7 @@ __device__ ALGSIG_LK_FINISH uint64_t lk_finish(const uint32_t (&c)[16], uint32_t
 // The signature of a key with a block outside the arena's readable range
 // (its first 32 bytes or its last): the blocks one by one with checked loads.
 // At most a few keys per relation take this path.
-template <int NCOMP, class Cursor>
+template <int NCOMP, int kLKWarps, class Cursor>
 __device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_lo, const uint8_t* lim_hi,
                                              const uint16_t* inv32, const uint4* mt, const Cursor& rc) {
   const uint32_t sh = 8u * (k.a & 1u);
@@ -361,7 +363,7 @@ __device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_
 // its block 0 in the group's last iteration.  An odd key whose last aligned
 // block ends with a key byte needs the next block's first byte.  Keys with a
 // block outside the arena's readable range are computed apart (lk_edge_key).
-template <int NCOMP, class Cursor>
+template <int NCOMP, int kLKWarps, int kLKDepth, class Cursor>
 __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8_t* lim_lo, const uint8_t* lim_hi,
                                          const uint16_t* inv32, const uint4* mt, uint64_t* __restrict__ sig_out,
                                          const Cursor& rc) {
@@ -417,11 +419,11 @@ __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8
   }
   if (k.valid && !k.edge) sig_out[k.kq] = lk_finish<NCOMP>(c, a3, k.a, inv32, rc);
   if (__any_sync(kFull, k.edge))
-    if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP>(k, lim_lo, lim_hi, inv32, mt, rc);
+    if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP, kLKWarps>(k, lim_lo, lim_hi, inv32, mt, rc);
 }
 
-template <bool AT400, int NCOMP>
-__global__ void __launch_bounds__(kLKThreads, 1) sig_key_kernel(const uint8_t* __restrict__ arena,
+template <bool AT400, int NCOMP, int kLKWarps, int kLKDepth>
+__global__ void __launch_bounds__(32 * kLKWarps, 1) sig_key_kernel(const uint8_t* __restrict__ arena,
                                                                 const uint64_t* __restrict__ off, uint64_t n,
                                                                 uint64_t* __restrict__ sig_out) {
   extern __shared__ __align__(16) uint8_t smem[];
@@ -470,7 +472,7 @@ __global__ void __launch_bounds__(kLKThreads, 1) sig_key_kernel(const uint8_t* _
         __syncwarp();
         lk_prefetch_window(W, off, wb + wn, k_hi);
       }
-      lk_group<NCOMP>(k, G, lim_lo, lim_hi, inv32, mt, sig_out, rc);
+      lk_group<NCOMP, kLKWarps, kLKDepth>(k, G, lim_lo, lim_hi, inv32, mt, sig_out, rc);
     }
     wb += wn;
   }

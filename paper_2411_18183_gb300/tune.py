@@ -1,19 +1,19 @@
-"""Batch runner: picks the hash-table load factor of a batch of joins by
-timing the candidates on the device, then replays the batch's launches from a
-captured CUDA graph.
+"""Batch runner: picks the hash-table load factor of a batch of joins and the
+launch shape of its signature kernel by timing the candidates on the device,
+then replays the batch's launches from a captured CUDA graph.
 
-The tile shape and warps per key of the kernels are compile-time constants of
-the library (one shape serves every key length, since the tile walk is
-byte-balanced); the load factor is the knob that trades table size (and the
-cache footprint of the probe) against bucket-chain length, so it is the one
-tuned per batch.
+The load factor trades table size (and the cache footprint of the probe)
+against bucket-chain length; the signature kernel's shape (warps per block,
+32-byte blocks of a key in flight) trades occupancy against registers, which
+favours different shapes for short and long keys.  The load factor is tuned
+first at the default shape, then the shapes at the best load factor.
 """
 from __future__ import annotations
 
 import torch
 
-from . import (DeviceRelation, alloc_ws, join_batch_prepare, join_batch_run, join_batch_ws_bytes, make_descs,
-               total_pair_cap)
+from . import (ROWS_SCATTERED, DeviceRelation, alloc_ws, join_batch_prepare, join_batch_run,
+               join_batch_ws_bytes, make_descs, sig_shapes, total_pair_cap)
 
 LOAD_FACTORS = (0.35, 0.5, 0.7, 0.9)
 
@@ -23,7 +23,8 @@ class GraphBatch:
     run() launches it directly, capture() records it into a CUDA graph and
     replay() relaunches the graph."""
 
-    def __init__(self, R: DeviceRelation, S: DeviceRelation, ranges, pair_caps, load_factor: float):
+    def __init__(self, R: DeviceRelation, S: DeviceRelation, ranges, pair_caps, load_factor: float,
+                 sig_shape: int = 0):
         self.R, self.S = R, S
         self.descs = make_descs(ranges, pair_caps)
         self.lf = load_factor
@@ -33,6 +34,20 @@ class GraphBatch:
         self.counts = torch.zeros(len(self.descs), dtype=torch.int64, device="cuda")
         self.batch = join_batch_prepare(self.descs, R, S, self.ws, load_factor, stream=self.stream)
         self.graph = None
+        self.set_shape(sig_shape)
+
+    @property
+    def shape(self) -> int:
+        return int(self.batch.sig_shape)
+
+    def set_shape(self, sig_shape: int) -> None:
+        """Signature kernel shape of the next run (drops a captured graph)."""
+        self.batch.sig_shape = int(sig_shape)
+        self.graph = None
+
+    def shape_matters(self) -> bool:
+        """Whether either side's signatures run through the single-relation kernel."""
+        return self.batch.r_first != ROWS_SCATTERED or self.batch.s_first != ROWS_SCATTERED
 
     def run(self):
         join_batch_run(self.batch, self.R, self.S, self.pairs, self.counts, stream=self.stream)
@@ -68,21 +83,23 @@ class GraphBatch:
 
 
 class TuneCache:
-    """Best load factors found by autotune, keyed by (GPU name, key-length
-    class, size class) so that batches of the same shape skip the timing.
-    Optionally persisted as JSON."""
+    """Best (load factor, signature kernel shape) found by autotune, keyed by
+    (GPU name, key-length class, size class) so that batches of the same shape
+    skip the timing.  Optionally persisted as JSON."""
 
     LENGTH_CLASSES = (128, 1024, 8192)          # upper bounds of the key-length bands, then longer
 
     def __init__(self, path: str | None = None):
         self.path = path
-        self.table: dict[str, float] = {}
+        self.table: dict[str, tuple] = {}
         if path:
             import json
             import os
             if os.path.exists(path):
                 with open(path) as f:
-                    self.table = {k: float(v) for k, v in json.load(f).items()}
+                    for k, v in json.load(f).items():
+                        # an entry is [load_factor, shape]; a bare number is a load factor at shape 0
+                        self.table[k] = (float(v[0]), int(v[1])) if isinstance(v, list) else (float(v), 0)
 
     @classmethod
     def key(cls, device_name: str, mean_key_bytes: float, rows: int) -> str:
@@ -91,14 +108,15 @@ class TuneCache:
         return f"{device_name}|len{lc}|rows2^{sc}"
 
     def get(self, key: str):
+        """(load_factor, shape) or None."""
         return self.table.get(key)
 
-    def put(self, key: str, load_factor: float) -> None:
-        self.table[key] = float(load_factor)
+    def put(self, key: str, load_factor: float, shape: int = 0) -> None:
+        self.table[key] = (float(load_factor), int(shape))
         if self.path:
             import json
             with open(self.path, "w") as f:
-                json.dump(self.table, f, indent=1, sort_keys=True)
+                json.dump({k: list(v) for k, v in self.table.items()}, f, indent=1, sort_keys=True)
 
 
 def batch_shape_key(R: DeviceRelation, S: DeviceRelation, ranges) -> str:
@@ -116,14 +134,17 @@ def batch_shape_key(R: DeviceRelation, S: DeviceRelation, ranges) -> str:
 
 
 def autotune(R: DeviceRelation, S: DeviceRelation, ranges, pair_caps, candidates=LOAD_FACTORS, reps: int = 3,
-             cache: TuneCache | None = None):
-    """Time every candidate load factor on this batch; return (best GraphBatch
-    with its graph captured, {load_factor: ms}).  With a cache, a batch of a
-    shape seen before takes the cached load factor without timing (the dict
-    is then empty)."""
+             cache: TuneCache | None = None, shapes=None):
+    """Time every candidate load factor on this batch at the default signature
+    kernel shape, then every shape at the best load factor; return (best
+    GraphBatch with its graph captured, {load_factor: ms}, {shape: ms}).  With
+    a cache, a batch of a shape seen before takes the cached choice without
+    timing (the dicts are then empty).  `shapes`: shape indices to try
+    (default all; skipped when no side runs the single-relation kernel)."""
     key = batch_shape_key(R, S, ranges) if cache is not None else None
     if cache is not None and cache.get(key) is not None:
-        return GraphBatch(R, S, ranges, pair_caps, cache.get(key)).capture(), {}
+        lf, shape = cache.get(key)
+        return GraphBatch(R, S, ranges, pair_caps, lf, shape).capture(), {}, {}
     times, best = {}, None
     for lf in candidates:
         gb = GraphBatch(R, S, ranges, pair_caps, lf)
@@ -132,6 +153,14 @@ def autotune(R: DeviceRelation, S: DeviceRelation, ranges, pair_caps, candidates
             best = gb
         else:
             del gb
+    shape_times = {}
+    if best.shape_matters():
+        if shapes is None:
+            shapes = range(len(sig_shapes()))
+        for sh in shapes:
+            best.set_shape(sh)
+            shape_times[sh] = best.time_ms(reps, graph=False)
+        best.set_shape(min(shape_times, key=shape_times.get))
     if cache is not None:
-        cache.put(key, best.lf)
-    return best.capture(), times
+        cache.put(key, best.lf, best.shape)
+    return best.capture(), times, shape_times

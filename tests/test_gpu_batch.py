@@ -148,8 +148,10 @@ def test_autotuned_graph_batch(cuda, batch):
     R = ag.DeviceRelation(Rd.arena, Rd.off, None)
     S = ag.DeviceRelation(Sd.arena, Sd.off, None)
     caps = [max(64, 2 * e + 64) for e in batch.expected]
-    gb, times = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1)
+    gb, times, shape_times = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1)
     assert set(times) == {0.4, 0.8} and gb.lf in times and gb.graph is not None
+    # the batch's rows are one run per side, so the signature kernel's shapes were timed too
+    assert set(shape_times) == set(range(len(ag.sig_shapes()))) and gb.shape in shape_times
     gb.counts.zero_()
     gb.replay()
     torch.cuda.synchronize()
@@ -158,6 +160,27 @@ def test_autotuned_graph_batch(cuda, batch):
         Rj, Sj = batch.join_relations(j)
         got = oracle.sort_pairs(gb.result(j).cpu().numpy().view(np.uint32))
         assert np.array_equal(got, oracle.join_simple(Rj, Sj))
+
+
+@pytest.mark.parametrize("shape", [1, 2])
+def test_batch_at_every_signature_shape(cuda, batch, shape):
+    """A batch run with each non-default signature kernel shape gives the
+    generator's per-join counts and the oracle's pairs."""
+    from paper_2411_18183_gb300 import tune
+    ag = cuda
+    assert shape < len(ag.sig_shapes())
+    Rd, Sd = dev(ag, batch.R), dev(ag, batch.S)
+    R = ag.DeviceRelation(Rd.arena, Rd.off, None)
+    S = ag.DeviceRelation(Sd.arena, Sd.off, None)
+    caps = [max(64, 2 * e + 64) for e in batch.expected]
+    gb = tune.GraphBatch(R, S, batch.ranges, caps, 0.5, shape)
+    assert gb.shape_matters()
+    gb.run()
+    torch.cuda.synchronize()
+    assert gb.counts.cpu().tolist() == list(batch.expected)
+    j = len(batch.ranges) // 3
+    Rj, Sj = batch.join_relations(j)
+    assert np.array_equal(oracle.sort_pairs(gb.result(j).cpu().numpy().view(np.uint32)), oracle.join_simple(Rj, Sj))
 
 
 def test_autotune_cache_skips_timing_for_a_known_shape(cuda, batch, tmp_path):
@@ -171,10 +194,11 @@ def test_autotune_cache_skips_timing_for_a_known_shape(cuda, batch, tmp_path):
     S = ag.DeviceRelation(Sd.arena, Sd.off, None)
     caps = [max(64, 2 * e + 64) for e in batch.expected]
     cache = tune.TuneCache(str(tmp_path / "tune.json"))
-    gb1, t1 = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1, cache=cache)
-    gb2, t2 = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1, cache=cache)
-    assert set(t1) == {0.4, 0.8} and t2 == {} and gb2.lf == gb1.lf
-    assert tune.TuneCache(str(tmp_path / "tune.json")).get(tune.batch_shape_key(R, S, batch.ranges)) == gb1.lf
+    gb1, t1, _ = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1, cache=cache)
+    gb2, t2, s2 = tune.autotune(R, S, batch.ranges, caps, candidates=(0.4, 0.8), reps=1, cache=cache)
+    assert set(t1) == {0.4, 0.8} and t2 == {} and s2 == {} and (gb2.lf, gb2.shape) == (gb1.lf, gb1.shape)
+    assert (tune.TuneCache(str(tmp_path / "tune.json")).get(tune.batch_shape_key(R, S, batch.ranges))
+            == (gb1.lf, gb1.shape))
     gb2.counts.zero_()
     gb2.replay()
     torch.cuda.synchronize()

@@ -95,6 +95,36 @@ def test_two_component_signatures(cuda):
         ag.sig_compute(ag.DeviceRelation.from_host(rels[0].arena, rels[0].off, rels[0].ids), n_components=3)
 
 
+def test_every_launch_shape(cuda):
+    """as_sig_compute_shape: each launch shape of the signature kernel gives the
+    oracle's signatures, 4 and 2 components, on edge keys at every alignment,
+    on lengths over the block and window boundaries and on a scaled relation of
+    the large workload (one window per warp and several); an unknown shape is
+    rejected."""
+    ag = cuda
+    rng = random.Random(45)
+    keys = edge_keys() + [bytes(rng.randrange(256) for _ in range(n)) for n in
+                          list(range(0, 70)) + [255, 256, 257, 511, 512, 513, 4095, 4097, 9000]]
+    rels = [relation_garbage_tail([b"#" * s] + interleave_gaps(keys, seed=s), seed=s) for s in range(0, 16, 5)]
+    rels.append(workloads.generate(workloads.CONFIGS["large"].scaled(2000, 60_000)).S)
+    mask = np.uint64(oracle.component_mask(2))
+    shapes = ag.sig_shapes()
+    assert len(shapes) >= 2 and all(w > 0 and d > 0 for w, d in shapes)
+    for rel in rels:
+        D = ag.DeviceRelation.from_host(rel.arena, rel.off, rel.ids)
+        want = oracle.sig_batch(rel.arena, rel.off, nthreads=8)
+        for sh in range(len(shapes)):
+            got = ag.sig_compute(D, shape=sh).cpu().numpy().view(np.uint64)
+            bad = np.nonzero(got != want)[0]
+            assert bad.size == 0, (shapes[sh], bad[:5].tolist())
+            got2 = ag.sig_compute(D, shape=sh, n_components=2).cpu().numpy().view(np.uint64)
+            assert np.array_equal(got2, want & mask), shapes[sh]
+    D = ag.DeviceRelation.from_host(rels[0].arena, rels[0].off, rels[0].ids)
+    for bad_shape in (-1, len(shapes)):
+        with pytest.raises(ag.AlgsigError):
+            ag.sig_compute(D, shape=bad_shape)
+
+
 @pytest.mark.parametrize("block_bytes", [16, 32, 48, 256, 4096])
 def test_cumulative_signatures(cuda, block_bytes):
     """as_sig_prefix_offsets / as_sig_prefixes against the oracle's definition:

@@ -197,5 +197,10 @@ def test_tune_cache_keys_and_persistence(tmp_path):
     path = str(tmp_path / "tune.json")
     c = TuneCache(path)
     assert c.get(k("GPU", 700, 10_000)) is None
-    c.put(k("GPU", 700, 10_000), 0.35)
-    assert TuneCache(path).get(k("GPU", 700, 10_000)) == 0.35
+    c.put(k("GPU", 700, 10_000), 0.35, 2)
+    assert TuneCache(path).get(k("GPU", 700, 10_000)) == (0.35, 2)
+    # a file written with bare load factors reads as shape 0
+    import json
+    with open(path, "w") as f:
+        json.dump({k("GPU", 700, 10_000): 0.5}, f)
+    assert TuneCache(path).get(k("GPU", 700, 10_000)) == (0.5, 0)
