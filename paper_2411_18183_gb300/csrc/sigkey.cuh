@@ -21,7 +21,11 @@
 // planes at once.  At the end of the key,
 //     sig^k = sum_m x^(2 k m) (lo16(c_m) + x^k hi16(c_m))   (mod P),
 // since S_b^(2k) = sum_m c_m[b] x^(2 k m).  Component 3 (2k = 6 is not a power
-// of two) keeps the table-driven delayed-reduction Horner step of gf16.cuh.
+// of two) has its own bit-sliced state over theta = x^1536, a Frobenius
+// conjugate of x^3 (so D_b(x^6) is a fixed GF(2)-linear image of D_b(theta)),
+// kept in a basis of GF(2^16) where its Horner step is 13 logic operations per
+// 16 bytes; xs3_net.h (written by gen_xs3.py) holds that step and the map back
+// to polynomial coordinates.
 //
 // Scheduling.  Each warp owns a byte-balanced range of keys and walks it in
 // windows of kLKWin keys.  A window's keys are sorted by length, and the warp
@@ -37,6 +41,8 @@
 // bulk copy per lane is serialised because its operands are warp-uniform.)
 #pragma once
 #include <cstdint>
+
+#include "xs3_net.h"
 
 namespace algsig {
 
@@ -151,19 +157,20 @@ __device__ __forceinline__ uint32_t xs_component(const uint32_t (&c)[16], const 
   return acc;
 }
 
-// Component 3's Horner step over one realigned chunk (delayed reduction; see
-// horner_chunk in gf16.cuh): a3 <- a3 x^24 + sum_j q_j x^(3 j).
+// Component 3 from its bit-sliced state: with p_i = the poly coordinate i of
+// every D_b(x^6) (bit b), sum_i x^i (lo16(p_i) + x^3 hi16(p_i)) mod P, by
+// Horner over i with a 32-bit accumulator reduced once on the way.
 template <class Cursor>
-__device__ __forceinline__ uint32_t c3_chunk(uint32_t a3, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3,
-                                             const Cursor& rc) {
-  const uint32_t h0 = __umulhi(v0, rc.k16), l0 = h0 * rc.nk16 + v0;
-  const uint32_t h1 = __umulhi(v1, rc.k16), l1 = h1 * rc.nk16 + v1;
-  const uint32_t h2 = __umulhi(v2, rc.k16), l2 = h2 * rc.nk16 + v2;
-  const uint32_t h3 = __umulhi(v3, rc.k16), l3 = h3 * rc.nk16 + v3;
-  uint32_t u = (a3 << 12) ^ l2 ^ (h2 << 3) ^ (l3 << 6) ^ (h3 << 9);
-  a3 = red32(u, rc);
-  u = (a3 << 12) ^ l0 ^ (h0 << 3) ^ (l1 << 6) ^ (h1 << 9);
-  return red32(u, rc);
+__device__ __forceinline__ uint32_t xs3_component(const uint32_t (&c3)[16], const Cursor& rc) {
+  uint32_t p[16];
+  xs3_to_poly(c3, p);
+  uint32_t acc = 0;
+#pragma unroll
+  for (int i = 15; i >= 0; --i) {
+    acc = (acc << 1) ^ (p[i] & 0xFFFFu) ^ ((p[i] >> 16) << 3);   // degree <= 18 + (15 - i)
+    if (i == 3) acc = red32(acc, rc);
+  }
+  return red32(acc, rc);
 }
 
 // x^-m * v in GF(2^16) for 0 <= m <= 60; inv32: the multiply table of x^-32
@@ -304,8 +311,8 @@ __device__ __forceinline__ void blk_zero_below(Blk& b, uint32_t a, const uint4* 
 
 // the Horner steps of one 32-byte block (its two chunks, the upper one first)
 template <int NCOMP, class Cursor>
-__device__ __forceinline__ void lk_block(const Blk& w, uint32_t sh, uint32_t& nxt0, uint32_t (&c)[16], uint32_t& a3,
-                                         const Cursor& rc) {
+__device__ __forceinline__ void lk_block(const Blk& w, uint32_t sh, uint32_t& nxt0, uint32_t (&c)[16],
+                                         uint32_t (&c3)[16], const Cursor& rc) {
   uint32_t v[8];
 #pragma unroll
   for (int i = 0; i < 7; i++) v[i] = __funnelshift_r(w.w[i], w.w[i + 1], sh);
@@ -314,23 +321,24 @@ __device__ __forceinline__ void lk_block(const Blk& w, uint32_t sh, uint32_t& nx
   xs_chunk(c, v[4], v[5], v[6], v[7]);
   xs_chunk(c, v[0], v[1], v[2], v[3]);
   if constexpr (NCOMP == 4) {
-    a3 = c3_chunk(a3, v[4], v[5], v[6], v[7], rc);
-    a3 = c3_chunk(a3, v[0], v[1], v[2], v[3], rc);
+    xs3_chunk(c3, v[4], v[5], v[6], v[7]);
+    xs3_chunk(c3, v[0], v[1], v[2], v[3]);
   }
 }
 
 // A key's signature from the Horner state of its blocks (values counted from
 // the first block's start; the key starts s = (a & ~1) / 2 symbols later).
 template <int NCOMP, class Cursor>
-__device__ ALGSIG_LK_FINISH uint64_t lk_finish(const uint32_t (&c)[16], uint32_t a3, uint32_t a, const uint16_t* inv32,
-                                              const Cursor& rc) {
+__device__ ALGSIG_LK_FINISH uint64_t lk_finish(const uint32_t (&c)[16], const uint32_t (&c3)[16], uint32_t a,
+                                              const uint16_t* inv32, const Cursor& rc) {
   const uint32_t v1 = xs_component<1>(c, rc);
   const uint32_t v2 = xs_component<2>(c, rc);
   const uint32_t s = (a & ~1u) >> 1;
   uint64_t sig = (uint64_t)mul_xinv(inv32, v1, s, rc) | ((uint64_t)mul_xinv(inv32, v2, 2 * s, rc) << 16);
   if constexpr (NCOMP == 4) {
+    const uint32_t v3 = xs3_component(c3, rc);
     const uint32_t v4 = xs_component<4>(c, rc);
-    sig |= ((uint64_t)mul_xinv(inv32, a3, 3 * s, rc) << 32) | ((uint64_t)mul_xinv(inv32, v4, 4 * s, rc) << 48);
+    sig |= ((uint64_t)mul_xinv(inv32, v3, 3 * s, rc) << 32) | ((uint64_t)mul_xinv(inv32, v4, 4 * s, rc) << 48);
   }
   return sig;
 }
@@ -347,14 +355,16 @@ __device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_
   uint32_t c[16];
 #pragma unroll
   for (int i = 0; i < 16; i++) c[i] = 0;
-  uint32_t a3 = 0;
+  uint32_t c3[16];                                    // component 3's state (unused with 2 components)
+#pragma unroll
+  for (int i = 0; i < 16; i++) c3[i] = 0;
   for (uint32_t vb = k.nb; vb-- > 0;) {
     Blk w = ld_blk_checked(k.base + 32ull * vb, lim_lo, lim_hi);
     if (vb + 1 == k.nb) blk_keep_below(w, k.tail, mt);
     if (vb == 0) blk_zero_below(w, k.a, mt);
-    lk_block<NCOMP>(w, sh, nxt0, c, a3, rc);
+    lk_block<NCOMP>(w, sh, nxt0, c, c3, rc);
   }
-  return lk_finish<NCOMP>(c, a3, k.a, inv32, rc);
+  return lk_finish<NCOMP>(c, c3, k.a, inv32, rc);
 }
 
 // The signatures of one group of keys: in iteration it of the group's G
@@ -385,7 +395,9 @@ __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8
   uint32_t c[16];
 #pragma unroll
   for (int i = 0; i < 16; i++) c[i] = 0;
-  uint32_t a3 = 0;
+  uint32_t c3[16];                                    // component 3's state (unused with 2 components)
+#pragma unroll
+  for (int i = 0; i < 16; i++) c3[i] = 0;
   // all iterations but the last (block 0, the bytes before the key's start masked)
   const uint32_t M = G - 1;
   for (uint32_t it0 = 0; it0 < M; it0 += kLKDepth) {
@@ -401,7 +413,7 @@ __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8
       }
       if (vb < nb) {
         if (vb + 1 == nb) blk_keep_below(w, k.tail, mt);   // bytes after the key's end
-        lk_block<NCOMP>(w, sh, nxt0, c, a3, rc);
+        lk_block<NCOMP>(w, sh, nxt0, c, c3, rc);
       }
     }
   }
@@ -414,10 +426,10 @@ __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8
     if (nb) {
       if (nb == 1) blk_keep_below(w, k.tail, mt);
       blk_zero_below(w, k.a, mt);
-      lk_block<NCOMP>(w, sh, nxt0, c, a3, rc);
+      lk_block<NCOMP>(w, sh, nxt0, c, c3, rc);
     }
   }
-  if (k.valid && !k.edge) sig_out[k.kq] = lk_finish<NCOMP>(c, a3, k.a, inv32, rc);
+  if (k.valid && !k.edge) sig_out[k.kq] = lk_finish<NCOMP>(c, c3, k.a, inv32, rc);
   if (__any_sync(kFull, k.edge))
     if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP, kLKWarps>(k, lim_lo, lim_hi, inv32, mt, rc);
 }
