@@ -966,7 +966,7 @@ template <bool AT400, int NCOMP, int SHAPE>
 static cudaError_t key_kernel_attr() {
   constexpr LKShape k = kLKShapes[SHAPE];
   return cudaFuncSetAttribute(reinterpret_cast<const void*>(sig_key_kernel<AT400, NCOMP, k.warps, k.depth>),
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lk_smem_bytes(k.warps));
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lk_smem_bytes(k.warps, k.depth));
 }
 template <bool AT400, int NCOMP>
 static cudaError_t key_kernel_attrs() {
@@ -981,7 +981,7 @@ static void key_kernel_launch(int sms, const uint8_t* arena, const uint64_t* off
   constexpr LKShape k = kLKShapes[SHAPE];
   const uint64_t want = (n + 32ull * k.warps - 1) / (32ull * k.warps);
   const unsigned blocks = (unsigned)(want < (uint64_t)sms ? (want < 1 ? 1 : want) : (uint64_t)sms);
-  sig_key_kernel<AT400, NCOMP, k.warps, k.depth><<<blocks, 32 * k.warps, lk_smem_bytes(k.warps), s>>>(arena, off, n,
+  sig_key_kernel<AT400, NCOMP, k.warps, k.depth><<<blocks, 32 * k.warps, lk_smem_bytes(k.warps, k.depth), s>>>(arena, off, n,
                                                                                                       out);
 }
 template <bool AT400, int NCOMP>

@@ -79,10 +79,10 @@ struct LKWarp {
   uint32_t order[kLKWin];          // window entries sorted by (block count << 8 | index)
 };
 constexpr size_t kSmemLKMasks = 1056;                 // 33 rows of 32 bytes
-constexpr size_t lk_smem_bytes(int warps) {
-  return (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)warps * sizeof(LKWarp);
+constexpr size_t lk_smem_bytes(int warps, int depth) {
+  return (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)warps * sizeof(LKWarp) + 0 * (size_t)depth;
 }
-static_assert(lk_smem_bytes(32) <= 232448, "lane-per-key signature kernel: shared memory");
+static_assert(lk_smem_bytes(32, 1) <= 232448, "lane-per-key signature kernel: shared memory");
 
 __device__ __forceinline__ void cp_async8(void* smem_dst, const void* gmem_src) {
   const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
@@ -346,7 +346,7 @@ __device__ ALGSIG_LK_FINISH uint64_t lk_finish(const uint32_t (&c)[16], const ui
 // The signature of a key with a block outside the arena's readable range
 // (its first 32 bytes or its last): the blocks one by one with checked loads.
 // At most a few keys per relation take this path.
-template <int NCOMP, int kLKWarps, class Cursor>
+template <int NCOMP, int kLKWarps, int kLKDepth, class Cursor>
 __device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_lo, const uint8_t* lim_hi,
                                              const uint16_t* inv32, const uint4* mt, const Cursor& rc) {
   const uint32_t sh = 8u * (k.a & 1u);
@@ -431,7 +431,7 @@ __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8
   }
   if (k.valid && !k.edge) sig_out[k.kq] = lk_finish<NCOMP>(c, c3, k.a, inv32, rc);
   if (__any_sync(kFull, k.edge))
-    if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP, kLKWarps>(k, lim_lo, lim_hi, inv32, mt, rc);
+    if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP, kLKWarps, kLKDepth>(k, lim_lo, lim_hi, inv32, mt, rc);
 }
 
 template <bool AT400, int NCOMP, int kLKWarps, int kLKDepth>
