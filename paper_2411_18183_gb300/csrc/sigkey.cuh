@@ -79,8 +79,9 @@ struct LKWarp {
   uint32_t order[kLKWin];          // window entries sorted by (block count << 8 | index)
 };
 constexpr size_t kSmemLKMasks = 1056;                 // 33 rows of 32 bytes
-constexpr size_t lk_smem_bytes(int warps, int depth) {
-  return (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)warps * sizeof(LKWarp) + 0 * (size_t)depth;
+// (the blocks in flight of a shape live in registers: its depth takes no shared memory)
+constexpr size_t lk_smem_bytes(int warps, int /*depth*/) {
+  return (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)warps * sizeof(LKWarp);
 }
 static_assert(lk_smem_bytes(32, 1) <= 232448, "lane-per-key signature kernel: shared memory");
 

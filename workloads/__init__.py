@@ -85,9 +85,14 @@ def _build_lib() -> None:
     os.replace(tmp, _SO)
 
 
-def build() -> str:
+def build(device: bool = True) -> str:
+    """Compile the host generator (gcc) and, with device=True, the device
+    generator (nvcc, sm_103a)."""
     with _lock:
         _build_lib()
+    if device:
+        from . import device as _device
+        _device.build()
     return _SO
 
 
@@ -96,8 +101,8 @@ def _load():
     with _lock:
         if _lib is not None:
             return _lib
-        src = os.path.join(_HERE, "gen.c")
-        if not os.path.exists(_SO) or os.path.getmtime(_SO) < os.path.getmtime(src):
+        srcs = [os.path.join(_HERE, f) for f in ("gen.c", "genrng.h")]
+        if not os.path.exists(_SO) or os.path.getmtime(_SO) < max(os.path.getmtime(f) for f in srcs):
             _build_lib()
         lib = ctypes.CDLL(_SO)
         P = ctypes.c_void_p
@@ -106,8 +111,10 @@ def _load():
         lib.gen_fill_R.argtypes = [ctypes.POINTER(_Spec), P, P, P, ctypes.c_int]
         lib.gen_fill_S.argtypes = [ctypes.POINTER(_Spec), P, P, P, P, P, P, ctypes.c_int]
         lib.gen_key_bytes.argtypes = [ctypes.POINTER(_Spec), ctypes.c_uint64, ctypes.c_uint64, P, ctypes.c_uint64]
-        lib.gen_perm.argtypes = [ctypes.c_uint64] * 4
-        lib.gen_perm.restype = ctypes.c_uint64
+        lib.gen_perm_x.argtypes = [ctypes.c_uint64] * 4
+        lib.gen_perm_x.restype = ctypes.c_uint64
+        lib.gen_n_copy.argtypes = [ctypes.c_double, ctypes.c_uint64]
+        lib.gen_n_copy.restype = ctypes.c_uint64
         _lib = lib
         return lib
 
@@ -237,7 +244,12 @@ def key_bytes(spec: JoinSpec, rel: int, ident: int, length: int) -> bytes:
 
 
 def perm(seed: int, tag: int, n: int, x: int) -> int:
-    return int(_load().gen_perm(seed, tag, n, x))
+    return int(_load().gen_perm_x(seed, tag, n, x))
+
+
+def n_copy(frac_copy: float, n: int) -> int:
+    """S rows that copy an R key in a relation of n S rows (C llround, as the plan counts them)."""
+    return int(_load().gen_n_copy(frac_copy, n))
 
 
 # ----------------------------------------------------------------------------- batches of joins

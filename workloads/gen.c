@@ -32,97 +32,32 @@ typedef struct {
     int32_t dup_lo, dup_hi;        /* total occurrences of such a key */
 } gen_spec;
 
-enum { T_LEN = 1, T_BYTE, T_PERM_R, T_PERM_S, T_PERM_Z, T_PARTNER, T_DUP, T_NEARC, T_NEARP, T_NEARL };
+/* the random choices (SplitMix64-based words, Feistel bijection, letters, XML
+   text, key lengths) are shared with the device generator */
+#include "genrng.h"
 
-static uint64_t mix64(uint64_t z) {
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
-
-/* pure random 64-bit word for (seed, tag, a, b) */
-static uint64_t rnd(uint64_t seed, uint64_t tag, uint64_t a, uint64_t b) {
-    uint64_t h = mix64(seed + 0x9E3779B97F4A7C15ull * (tag + 1));
-    h = mix64(h ^ (a * 0xD1B54A32D192ED03ull + 0x632BE59BD9B4E019ull));
-    h = mix64(h ^ (b * 0x8CB92BA72F3D8DD7ull + 0x2545F4914F6CDD1Dull));
-    return h;
-}
-
-static uint64_t uniform(uint64_t r, uint64_t lo, uint64_t hi) { /* inclusive */
-    return lo + r % (hi - lo + 1);
-}
+#define mix64 gen_mix64
+#define rnd gen_rnd
+#define uniform gen_uniform
+#define perm gen_perm
+#define letter gen_letter
 
 static double unit(uint64_t r) { return (double)(r >> 11) * (1.0 / 9007199254740992.0); }
 
-/* bijection on [0, n): 4-round Feistel on the smallest even bit width that
-   covers n, with cycle walking */
-static uint64_t perm(uint64_t seed, uint64_t tag, uint64_t n, uint64_t x) {
-    if (n <= 1) return 0;
-    int bits = 2;
-    while (bits < 64 && (1ull << bits) < n) bits += 2;
-    int half = bits / 2;
-    uint64_t mask = (1ull << half) - 1;
-    do {
-        uint64_t L = x >> half, R = x & mask;
-        for (int r = 0; r < 4; r++) {
-            uint64_t F = rnd(seed, tag, (uint64_t)r, R) & mask;
-            uint64_t nL = R, nR = L ^ F;
-            L = nL; R = nR;
-        }
-        x = (L << half) | R;
-    } while (x >= n);
-    return x;
-}
-
 static const char ACGT[4] = {'A', 'C', 'G', 'T'};
-static const char ALNUM[] = "0123456789ABCDEFGHIJKLMNOPQRSTUVWXYZabcdefghijklmnopqrstuvwxyz";
-
-static uint8_t letter(int alphabet, uint16_t u) {
-    switch (alphabet) {
-        case 1: return (uint8_t)ACGT[u & 3];
-        case 2: return (uint8_t)ALNUM[((uint32_t)u * 62u) >> 16];
-        case 3: return (uint8_t)(u & 0xFF);
-        default: return (uint8_t)(0x20 + (((uint32_t)u * 95u) >> 16));
-    }
-}
-
-/* XML-like text: elements <t>text</t> with a tag t of 3..12 letters a..z and
-   alphanumeric text of 1..64 characters, concatenated while they fit, then
-   alphanumeric characters up to exactly len bytes */
-static void xml_bytes(const gen_spec* sp, uint64_t tagbase, uint64_t ident, uint8_t* dst, uint64_t len) {
-    uint64_t pos = 0, ctr = 0;
-    for (;;) {
-        uint64_t r = rnd(sp->seed, tagbase, ident, ctr++);
-        uint64_t tl = 3 + r % 10, cl = 1 + (r >> 8) % 64;
-        uint64_t need = 2 * tl + cl + 5;   /* <t> text </t> */
-        if (pos + need > len) break;
-        uint8_t tagname[12];
-        for (uint64_t i = 0; i < tl; i++) tagname[i] = (uint8_t)('a' + rnd(sp->seed, tagbase, ident, ctr++) % 26);
-        dst[pos++] = '<';
-        for (uint64_t i = 0; i < tl; i++) dst[pos++] = tagname[i];
-        dst[pos++] = '>';
-        for (uint64_t i = 0; i < cl; i++) dst[pos++] = letter(2, (uint16_t)rnd(sp->seed, tagbase, ident, ctr++));
-        dst[pos++] = '<';
-        dst[pos++] = '/';
-        for (uint64_t i = 0; i < tl; i++) dst[pos++] = tagname[i];
-        dst[pos++] = '>';
-    }
-    while (pos < len) dst[pos++] = letter(2, (uint16_t)rnd(sp->seed, tagbase, ident, ctr++));
-}
 
 /* bytes of the key with identity (rel, ident), written to dst[0..len) */
 static void key_bytes(const gen_spec* sp, uint64_t rel, uint64_t ident, uint8_t* dst, uint64_t len) {
-    uint64_t tag = T_BYTE + 16 * rel;
-    if (sp->alphabet == 4) { xml_bytes(sp, tag, ident, dst, len); return; }
+    if (sp->alphabet == 4) { gen_xml_bytes(sp->seed, T_BYTE + 16 * rel, ident, dst, len); return; }
     for (uint64_t j = 0; j < len; j += 4) {
-        uint64_t r = rnd(sp->seed, tag, ident, j >> 2);
+        uint64_t r = gen_group_word(sp->seed, rel, ident, j >> 2);
         for (int q = 0; q < 4 && j + q < len; q++) dst[j + q] = letter(sp->alphabet, (uint16_t)(r >> (16 * q)));
     }
 }
 
 static uint32_t key_len(const gen_spec* sp, uint64_t rel, uint64_t ident) {
-    uint64_t lo = rel ? sp->s_len_lo : sp->r_len_lo, hi = rel ? sp->s_len_hi : sp->r_len_hi;
-    return (uint32_t)uniform(rnd(sp->seed, T_LEN + 16 * rel, ident, 0), lo, hi);
+    return rel ? gen_key_len(sp->seed, rel, ident, sp->s_len_lo, sp->s_len_hi)
+               : gen_key_len(sp->seed, rel, ident, sp->r_len_lo, sp->r_len_hi);
 }
 
 /*
@@ -291,4 +226,7 @@ void gen_key_bytes(const gen_spec* sp, uint64_t rel, uint64_t ident, uint8_t* ds
     key_bytes(sp, rel, ident, dst, len);
 }
 
-uint64_t gen_perm(uint64_t seed, uint64_t tag, uint64_t n, uint64_t x) { return perm(seed, tag, n, x); }
+uint64_t gen_perm_x(uint64_t seed, uint64_t tag, uint64_t n, uint64_t x) { return perm(seed, tag, n, x); }
+
+/* S rows that copy an R key: llround(frac_copy * n), as gen_plan counts them */
+uint64_t gen_n_copy(double frac_copy, uint64_t n) { return (uint64_t)llround(frac_copy * (double)n); }
