@@ -181,66 +181,145 @@ def run_reference(args):
 
 # --------------------------------------------------------------------------- batch and serving legs
 
-BATCH_SCALE = 100        # batch leg: the 512-join batch with relation sizes / 100
-SERVE_SCALE = 50         # serving leg: request relation sizes / 50
 SERVE_SECONDS = 2.0
 LOAD_FACTORS = (0.5, 0.35, 0.25)   # candidates of the single join's load-factor tuning
 
 
+BATCH_WAVE_BYTES = 110 * 10 ** 9      # key bytes per wave of the full batch (with offsets and workspace < 120 GB)
+BATCH_SAMPLE_BYTES = 300 * 10 ** 6    # largest join (R + S key bytes) of a wave checked against the oracle
+
+
 def batch_leg(ag, steps: int):
-    """512 independent joins (sizes log-normal, three key-length bands) in one
-    graph-captured launch sequence, load factor autotuned; S tuples/s."""
+    """The 512-join batch at full size (|R| log-normal median 20,000 in
+    [1,000, 1,000,000], |S| = 10 |R|, three key-length bands; about 430 GB of
+    keys) in waves of consecutive joins of at most BATCH_WAVE_BYTES key bytes.
+    Each wave is generated on the device (untimed), its load factor and
+    signature kernel shape autotuned, its per-join pair counts checked against
+    the generator's and two of its joins (the smallest and a seeded random one
+    under BATCH_SAMPLE_BYTES) checked byte for byte against the host generator
+    and pair for pair against the oracle; then its graph-captured batch run is
+    timed (inputs far larger than L2).  S tuples/s over the timed runs."""
+    import random
+    import time
     import torch
+    import oracle
     from paper_2411_18183_gb300 import tune
-    spec = workloads.BatchSpec().scaled(BATCH_SCALE)
-    bw = workloads.generate_batch(spec)
-    R = ag.DeviceRelation.from_host(bw.R.arena, bw.R.off, None)
-    S = ag.DeviceRelation.from_host(bw.S.arena, bw.S.off, None)
-    caps = [max(64, int(e * 1.25) + 64) for e in bw.expected]
-    gb, tried, shape_tried = tune.autotune(R, S, bw.ranges, caps)
-    gb.counts.zero_()
-    gb.replay()
-    torch.cuda.synchronize()
-    if gb.counts.cpu().tolist() != list(bw.expected):
-        raise SystemExit("batch leg: per-join pair counts differ from the generator's")
-    ms = gb.time_ms(reps=max(3, steps))
-    n = bw.S.n
-    return {"workload": f"{spec.n_joins} joins, |R| log-normal median {spec.r_median:g} in "
+    from workloads import device as gdev
+    spec = workloads.BatchSpec()
+    specs = spec.joins()
+    t0 = time.time()
+    plan = gdev.plan_batch(specs)
+    groups = gdev.waves(plan, BATCH_WAVE_BYTES)
+    rng = random.Random(spec.seed)
+    shapes = ag.sig_shapes()
+    cores = os.cpu_count() or 1
+    out_waves, total_ms, total_s, total_bytes, sampled = [], 0.0, 0, 0, 0
+    for j0, j1 in groups:
+        tg = time.time()
+        w = gdev.fill_wave(plan, j0, j1)
+        gen_s = time.time() - tg
+        R = ag.DeviceRelation(w.arenaR, w.offR, None)
+        S = ag.DeviceRelation(w.arenaS, w.offS, None)
+        caps = [max(64, int(e * 1.25) + 64) for e in w.expected]
+        gb, tried, shape_tried = tune.autotune(R, S, w.ranges, caps)
+        gb.counts.zero_()
+        gb.replay()
+        torch.cuda.synchronize()
+        if gb.counts.cpu().tolist() != list(w.expected):
+            raise SystemExit(f"batch leg: wave {j0}-{j1}: per-join pair counts differ from the generator's")
+        # two joins of the wave against the host generator and the oracle
+        sizes = {j: plan.key_bytes(j, j + 1) for j in range(j0, j1)}
+        small = [j for j in range(j0, j1) if sizes[j] <= BATCH_SAMPLE_BYTES]
+        picks = sorted({min(sizes, key=sizes.get)} | ({rng.choice(small)} if small else set()))
+        checked = []
+        for j in picks:
+            wl = workloads.generate(specs[j])
+            rb, re_, sb, se = w.ranges[j - j0]
+            for dev_arena, dev_off, rel, a, b in ((w.arenaR, w.offR, wl.R, rb, re_), (w.arenaS, w.offS, wl.S, sb, se)):
+                lo, hi = int(dev_off[a]), int(dev_off[b])
+                if not np.array_equal(dev_arena[lo:hi].cpu().numpy(), rel.arena[: rel.nbytes]):
+                    raise SystemExit(f"batch leg: join {j}: device-generated bytes differ from the host generator's")
+            want = oracle.join_grace(wl.R, wl.S, nthreads=cores)
+            got = oracle.sort_pairs(gb.result(j - j0).cpu().numpy().view(np.uint32))
+            if not np.array_equal(got, want):
+                raise SystemExit(f"batch leg: join {j}: pairs differ from the oracle's")
+            checked.append({"join": j, "R": specs[j].m, "S": specs[j].n, "key_bytes": sizes[j], "pairs": len(want)})
+        sampled += len(checked)
+        ms = gb.time_ms(reps=max(3, steps))
+        total_ms += ms
+        total_s += w.nS
+        total_bytes += w.key_bytes
+        out_waves.append({"joins": [j0, j1], "rows": {"R": w.mR, "S": w.nS}, "key_bytes": w.key_bytes,
+                          "generate_s": round(gen_s, 2), "load_factor": gb.lf, "sig_shape": shapes[gb.shape],
+                          "tuning_ms": tried, "shape_tuning_ms": {str(shapes[k]): v for k, v in shape_tried.items()},
+                          "ms": ms, "tuples_per_s": w.nS / (ms * 1e-3), "oracle_checked": checked})
+        del gb, R, S, w
+        torch.cuda.empty_cache()
+    del plan
+    torch.cuda.empty_cache()
+    return {"workload": f"{spec.n_joins} joins, |R| log-normal median {spec.r_median:g} (sigma {spec.sigma:g}) in "
                         f"[{spec.r_range[0]}, {spec.r_range[1]}], |S| = {spec.s_factor} |R|, key bands "
-                        f"{list(spec.bands)} B, {int(spec.frac_copy * 100)}% S copies (relation sizes of the "
-                        f"512-join batch / {BATCH_SCALE})",
-            "rows": {"R": bw.R.n, "S": n}, "key_bytes": bw.R.nbytes + bw.S.nbytes,
-            "load_factor": gb.lf, "tuning_ms": tried, "sig_shape": ag.sig_shapes()[gb.shape],
-            "shape_tuning_ms": {str(ag.sig_shapes()[k]): v for k, v in shape_tried.items()}, "ms_per_batch": ms,
-            "joins_per_s": spec.n_joins / (ms * 1e-3), "tuples_per_s": n / (ms * 1e-3),
-            "gpu_launches_per_batch": 5, "cuda_graph": True}
+                        f"{list(spec.bands)} B, {int(spec.frac_copy * 100)}% S copies; full size, in waves of "
+                        f"<= {BATCH_WAVE_BYTES / 1e9:g} GB of keys generated on the device",
+            "joins": spec.n_joins, "rows": {"R": plan_rows(specs, "m"), "S": plan_rows(specs, "n")},
+            "key_bytes": total_bytes, "waves": out_waves, "ms_total": total_ms,
+            "tuples_per_s": total_s / (total_ms * 1e-3), "key_GBps": total_bytes / (total_ms * 1e-3) / 1e9,
+            "joins_per_s": spec.n_joins / (total_ms * 1e-3), "oracle_checked_joins": sampled,
+            "pair_counts": "every join equals the generator's count", "wall_s": round(time.time() - t0, 1),
+            "l2": "inputs of each wave far larger than L2", "gpu_launches_per_batch": 5, "cuda_graph": True}
+
+
+def plan_rows(specs, field):
+    return sum(getattr(sp, field) for sp in specs)
+
+
+SERVE_OVERLOAD = 4.0     # arrival-rate multiple of the serving leg's second run, in which the budget binds
 
 
 def serve_leg(ag):
-    """Poisson arrivals of join requests over a resident pool, admitted under
-    the device-memory bound, continuously batched on 4 streams."""
+    """Poisson arrivals (2,000 joins/s) of join requests over a resident pool
+    of 64 joins at the stated request size (about 64 GB of XML-like keys,
+    generated on the device), admitted under the 120 GB device-memory bound
+    and continuously batched on 4 streams.  A second run offers
+    SERVE_OVERLOAD times the rate, so that admission waits on the budget.
+    Every request's pair count equals the generator's."""
+    import torch
     from paper_2411_18183_gb300 import serve
-    spec = workloads.SERVE_SPEC.scaled(SERVE_SCALE)
-    bw = workloads.generate_batch(spec)
-    pool = serve.DevicePool.from_batch(bw, lambda rel: ag.DeviceRelation.from_host(rel.arena, rel.off, None))
+    from workloads import device as gdev
+    spec = workloads.SERVE_SPEC
+    plan = gdev.plan_batch(spec.joins())
+    w = gdev.fill_wave(plan, 0, spec.n_joins)
+    del plan
+    torch.cuda.empty_cache()
+    pool = serve.DevicePool.from_device(ag.DeviceRelation(w.arenaR, w.offR, None),
+                                        ag.DeviceRelation(w.arenaS, w.offS, None), w.ranges, w.expected)
     ex = serve.GpuExecutor(pool, n_slots=4, max_batch=64)
-    arrivals = serve.poisson_arrivals(workloads.SERVE_RATE, SERVE_SECONDS, pool.n, seed=spec.seed)
-    srv = serve.Server(ex, budget_bytes=workloads.SERVE_BUDGET_BYTES, max_batch=64)
-    srv.run(serve.poisson_arrivals(workloads.SERVE_RATE, 0.2, pool.n, seed=1))      # warm-up
-    reqs = srv.run(arrivals, timeout=120.0)
-    bad = [r.rid for r in reqs if r.count != pool.expected[r.pool_index]]
-    if bad:
-        raise SystemExit(f"serving leg: {len(bad)} requests got a wrong pair count")
-    s = serve.summarize(reqs)
-    tuples = sum(pool.ranges[r.pool_index][3] - pool.ranges[r.pool_index][2] for r in reqs)
+
+    def one(rate, seconds, seed):
+        srv = serve.Server(ex, budget_bytes=workloads.SERVE_BUDGET_BYTES, max_batch=64)
+        reqs = srv.run(serve.poisson_arrivals(rate, seconds, pool.n, seed=seed), timeout=300.0)
+        bad = [r.rid for r in reqs if r.count != pool.expected[r.pool_index]]
+        if bad:
+            raise SystemExit(f"serving leg: {len(bad)} requests got a wrong pair count")
+        s = serve.summarize(reqs)
+        tuples = sum(pool.ranges[r.pool_index][3] - pool.ranges[r.pool_index][2] for r in reqs)
+        s.update({"rate_per_s": rate, "seconds": seconds, "peak_admitted_bytes": srv.ledger.peak,
+                  "budget_bytes": workloads.SERVE_BUDGET_BYTES, "batches": srv.batches,
+                  "tuples_per_s": tuples / s["span_s"] if s["span_s"] else None})
+        return s
+
+    serve.Server(ex, budget_bytes=workloads.SERVE_BUDGET_BYTES, max_batch=64).run(
+        serve.poisson_arrivals(workloads.SERVE_RATE, 0.2, pool.n, seed=1))             # warm-up
+    s = one(workloads.SERVE_RATE, SERVE_SECONDS, spec.seed)
+    s["overload"] = one(workloads.SERVE_RATE * SERVE_OVERLOAD, SERVE_SECONDS / 2, spec.seed + 1)
     s.update({"workload": f"Poisson {workloads.SERVE_RATE:g} joins/s for {SERVE_SECONDS:g} s over a pool of "
-                          f"{pool.n} joins: |R| log-normal median {spec.r_median:g}, |S| = "
-                          f"{spec.s_factor_range[0]}-{spec.s_factor_range[1]} |R|, XML-like keys "
-                          f"{spec.bands[0][0]}-{spec.bands[0][1]} B, {int(spec.frac_copy * 100)}% S copies "
-                          f"(request sizes / {SERVE_SCALE})",
-              "budget_bytes": workloads.SERVE_BUDGET_BYTES, "peak_admitted_bytes": srv.ledger.peak,
-              "batches": srv.batches, "streams": 4,
-              "tuples_per_s": tuples / s["span_s"] if s["span_s"] else None})
+                          f"{pool.n} joins at full request size: |R| log-normal median {spec.r_median:g} in "
+                          f"[{spec.r_range[0]}, {spec.r_range[1]}], |S| = {spec.s_factor_range[0]}-"
+                          f"{spec.s_factor_range[1]} |R|, XML-like keys {spec.bands[0][0]}-{spec.bands[0][1]} B, "
+                          f"{int(spec.frac_copy * 100)}% S copies; pool generated on the device",
+              "pool_key_bytes": w.key_bytes, "pool_rows": {"R": w.mR, "S": w.nS}, "streams": 4})
+    del ex, pool, w
+    torch.cuda.empty_cache()
     return s
 
 

@@ -334,17 +334,37 @@ class DevicePool:
 
     @staticmethod
     def from_batch(bw, device_relation, load_factor: float = 0.5) -> "DevicePool":
+        """A pool over a host batch (workloads.generate_batch), copied to the device."""
         R = device_relation(bw.R)
         S = device_relation(bw.S)
-        ranges = list(bw.ranges)
+        key_bytes = [int(bw.R.off[r1] - bw.R.off[r0]) + int(bw.S.off[s1] - bw.S.off[s0])
+                     for (r0, r1, s0, s1) in bw.ranges]
+        return DevicePool._sized(R, S, list(bw.ranges), key_bytes, list(bw.expected), load_factor)
+
+    @staticmethod
+    def from_device(R, S, ranges, expected, load_factor: float = 0.5) -> "DevicePool":
+        """A pool over relations already in device memory (for example a batch
+        the device generator wrote); ranges: (r_begin, r_end, s_begin, s_end)."""
+        import torch
+        ranges = list(ranges)
+        ir = torch.tensor([x for (r0, r1, _, _) in ranges for x in (r0, r1)], dtype=torch.int64, device=R.off.device)
+        is_ = torch.tensor([x for (_, _, s0, s1) in ranges for x in (s0, s1)], dtype=torch.int64, device=S.off.device)
+        br = R.off[ir].view(-1, 2).diff(dim=1).view(-1).cpu().tolist()
+        bs = S.off[is_].view(-1, 2).diff(dim=1).view(-1).cpu().tolist()
+        return DevicePool._sized(R, S, ranges, [a + b for a, b in zip(br, bs)], list(expected), load_factor)
+
+    @staticmethod
+    def _sized(R, S, ranges, key_bytes, expected, load_factor) -> "DevicePool":
+        """Per join: pair capacity, workspace need and the bytes a request holds
+        while admitted (its inputs with offsets and ids, workspace, pairs)."""
         caps, rb, need = [], [], []
-        for (r0, r1, s0, s1), e in zip(ranges, bw.expected):
+        for (r0, r1, s0, s1), kb, e in zip(ranges, key_bytes, expected):
             m, n = r1 - r0, s1 - s0
             cap = max(64, int(e * 1.25) + 64)
             cap_slots = 1 << max(6, math.ceil(math.log2(max(1, m) / load_factor)))
-            inputs = int(bw.R.off[r1] - bw.R.off[r0]) + int(bw.S.off[s1] - bw.S.off[s0]) + 8 * (m + n) + 4 * (m + n)
+            inputs = kb + 8 * (m + n) + 4 * (m + n)
             ws = 16 * cap_slots + 8 * (m + n) + 64
             caps.append(cap)
             need.append(ws)
             rb.append(inputs + ws + 8 * cap)
-        return DevicePool(R, S, ranges, caps, rb, need, list(bw.expected))
+        return DevicePool(R, S, ranges, caps, rb, need, expected)
