@@ -749,14 +749,16 @@ def run_gpu(args):
     dprobe = torch.empty(hprobe.numel(), dtype=torch.uint8, device="cuda")
     dprobe.copy_(hprobe, non_blocking=True)
     torch.cuda.synchronize()
-    h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    h0.record(stream)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
+    rates = []
+    for _ in range(5):                                  # the best of five single copies
+        h0, h1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        h0.record(stream)
+        with torch.cuda.stream(stream):
             dprobe.copy_(hprobe, non_blocking=True)
-    h1.record(stream)
-    torch.cuda.synchronize()
-    h2d_gbs = 3 * hprobe.numel() / (h0.elapsed_time(h1) * 1e-3) / 1e9
+        h1.record(stream)
+        torch.cuda.synchronize()
+        rates.append(hprobe.numel() / (h0.elapsed_time(h1) * 1e-3) / 1e9)
+    h2d_gbs = max(rates)
     del dprobe
     e2e_steps = max(2, min(args.steps, 5))
     if sj.run(hR, hS, cuts, out_host) != expected:
