@@ -428,9 +428,10 @@ as_status as_join_batch_prepare(const as_join_desc* descs, int n_joins, uint64_t
  * keys, build of every join's table, signatures of all S keys, probe and
  * verification of every S key against its join's table.  The signatures of a
  * side whose rows form one run (r_first / s_first set) come from the
- * single-relation kernel of as_sig_compute over that run; scattered rows take
- * the batch walk over the joins' row ranges.  Asynchronous; a join's count may
- * exceed its pair_cap (the excess pairs are not written). */
+ * signature kernel of as_sig_compute over that run; scattered rows take the
+ * same kernel over the joins' row ranges back to back (its windows of keys
+ * end with each join's rows); both at the shape b->sig_shape.  Asynchronous;
+ * a join's count may exceed its pair_cap (the excess pairs are not written). */
 as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR,
                             const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint32_t* d_pairs,
                             uint64_t* d_counts, as_stream stream);

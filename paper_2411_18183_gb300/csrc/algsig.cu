@@ -153,85 +153,6 @@ __global__ void batch_bytes_kernel(BatchJoin* J, int nj, const uint64_t* __restr
 // Signature kernel
 // ----------------------------------------------------------------------------
 
-// Signatures of actual keys [k_lo, k_hi) of one relation; key k's signature
-// goes to sig_out[k + out_shift] (out_shift = virtual minus actual row).
-template <int NCOMP, class Cursor>
-__device__ __forceinline__ void sig_walk(const uint8_t* __restrict__ arena, const uint64_t* __restrict__ off,
-                                         uint64_t k_lo, uint64_t k_hi, uint64_t out_shift,
-                                         uint64_t* __restrict__ sig_out, uint8_t* bufs, const uint16_t* ctab,
-                                         const Cursor& rc) {
-  const int lane = threadIdx.x & 31;
-  // rounds r and r+1 are in flight before round r is computed
-  Plan cur = plan_round(plan_load(off, k_lo, k_hi), k_lo, k_hi, 0);
-  issue_span(bufs, arena, cur);
-  Plan nxt = plan_round(plan_load(off, cur.kc_next, k_hi), cur.kc_next, k_hi, cur.tc_next);
-  issue_span(bufs + kBufBytes, arena, nxt);
-  uint64_t carry = 0;                               // partial signature of the key continuing into `cur`
-  Pending pd;
-  pd.valid = false;
-  for (int r = 0; cur.valid; ++r) {
-    const PlanLoad ahead = plan_load(off, nxt.kc_next, k_hi);
-    cp_async_wait_prev();
-    __syncwarp();
-    uint8_t* buf = bufs + (r & 1) * kBufBytes;
-    uint32_t a1, a2, a3, a4;
-    tile_accumulate<NCOMP>(buf, cur.span_lo, cur, rc, a1, a2, a3, a4);
-    if (pd.valid) pending_alogs(pd);                // its logs were loaded one round ago
-    __syncwarp();                                   // buf is free: refill it with round r+2
-    const Plan nn = plan_round(ahead, nxt.kc_next, k_hi, nxt.tc_next);
-    issue_span(buf, arena, nn);
-    const uint64_t V = scan_round(cur, cur.active ? pack4(a1, a2, a3, a4) : 0ull, ctab);
-    // Keys that finish here: the head lane of every key whose tiles all lie in
-    // this round, and the previous round's deferred key if it is complete (taken
-    // by a lane without a head job); one lo_correct for all of them.
-    const bool head = cur.active && (uint32_t)lane == cur.slot0;
-    const bool fresh = cur.q != 0 || cur.tc == 0;   // the key's first tile is in this round
-    const bool hjob = head && fresh && cur.slot0 + cur.rq <= 32u;
-    uint64_t P = 0;
-    bool pjob = false;
-    if (pd.valid) {                                 // finish the previous round's deferred product
-      P = pending_value(pd);
-      if (pd.complete) pjob = true; else carry = P;
-      pd.valid = false;
-    }
-    const uint32_t hm = __ballot_sync(kFull, hjob);
-    const int plane = pjob ? __ffs(~hm) - 1 : -1;
-    if (pjob && plane < 0) {                        // every lane has a head job (rare)
-      const uint64_t s = lo_correct(ctab, P, pd.lo, rc);
-      if (lane == 0) sig_out[pd.key + out_shift] = s;
-      pjob = false;
-    }
-    const bool mine = pjob && lane == plane;
-    const uint64_t fin = lo_correct(ctab, hjob ? V : P, hjob ? cur.lo : pd.lo, rc);
-    if (hjob) sig_out[cur.kc + (uint64_t)cur.q + out_shift] = fin;
-    else if (mine) sig_out[pd.key + out_shift] = fin;
-    if (cur.tc > 0) {                               // group 0 continues a key: x^(k e) B, finished next round
-      pd.valid = true;
-      pd.key = cur.kc;
-      pd.carry = carry;
-      pd.lo = __shfl_sync(kFull, cur.lo, 0);
-      pd.complete = __shfl_sync(kFull, cur.rq, 0) <= 32u;
-      pending_logs(pd, __shfl_sync(kFull, V, 0), cur.tc);
-    }
-    const uint64_t vlast = __shfl_sync(kFull, V, (int)cur.s31);
-    if (cur.carries && !(cur.s31 == 0 && cur.tc > 0)) carry = vlast;   // a key that starts here continues
-    cur = nxt;
-    nxt = nn;
-  }
-  if (pd.valid) {                                   // the range's last key, if it was deferred
-    pending_alogs(pd);
-    const uint64_t s = lo_correct(ctab, pending_value(pd), pd.lo, rc);
-    if (lane == 0) sig_out[pd.key + out_shift] = s;
-  }
-  cp_async_wait_all();
-}
-
-}  // namespace algsig
-
-#include "sigkey.cuh"
-
-namespace algsig {
-
 // first actual key of join j whose start lies at or after virtual byte t
 // (t inside join j's byte range), as a virtual row
 template <bool S_SIDE>
@@ -244,65 +165,18 @@ __device__ __forceinline__ uint64_t vcut_in_join(const BatchJoin* J, const uint6
   return v0 + (k - b);
 }
 
+}  // namespace algsig
+
+#include "sigkey.cuh"
+
+namespace algsig {
+
 // Shared-memory address of the start of dynamic shared memory (one probe per
 // device decides whether the tables can be addressed at the fixed 0x400).
 __device__ uint32_t g_dyn_smem_base;
 __global__ void dyn_smem_base_kernel() {
   extern __shared__ __align__(16) uint8_t smem[];
   if (threadIdx.x == 0) g_dyn_smem_base = (uint32_t)__cvta_generic_to_shared(smem);
-}
-
-// Signatures of all keys of a relation (J == nullptr), or of the rows of a
-// batch's joins (S_SIDE picks the relation), byte-balanced over the warps.
-// AT400: the reduction tables sit at shared address 0x400 (RedCursorAt400).
-// NCOMP: components computed (4, or 2 for the two-symbol signature; the
-// others are 0); batches always use 4.
-template <bool S_SIDE, bool AT400, int NCOMP = 4>
-__global__ void __launch_bounds__(kThreads, 1) sig_kernel(const uint8_t* __restrict__ arena,
-                                                          const uint64_t* __restrict__ off, uint64_t n,
-                                                          uint64_t* __restrict__ sig_out,
-                                                          const BatchJoin* __restrict__ J, int nj) {
-  extern __shared__ __align__(16) uint8_t smem[];
-  uint32_t* red = reinterpret_cast<uint32_t*>(smem);
-  uint16_t* ctab = reinterpret_cast<uint16_t*>(smem + kSmemTables);
-  for (int i = threadIdx.x; i < kConstEntries / 2; i += blockDim.x)
-    reinterpret_cast<uint32_t*>(ctab)[i] = reinterpret_cast<const uint32_t*>(g_const)[i];
-  init_red_tables(red, red + kRedWords);            // ends with __syncthreads()
-  const int wib = threadIdx.x >> 5;
-  using Cursor = typename std::conditional<AT400, RedCursorAt400, RedCursor>::type;
-  Cursor rc;
-  if constexpr (AT400) rc = red_cursor_at400(); else rc = red_cursor(red);
-  uint8_t* bufs = smem + kSmemTables + kConstBytes + (size_t)wib * 2 * kBufBytes;
-  const uint64_t warp = (uint64_t)blockIdx.x * kWarpsPerBlock + wib;
-  const uint64_t nwarps = (uint64_t)gridDim.x * kWarpsPerBlock;
-  if (!J) {
-    uint64_t k_lo, k_hi;
-    warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
-    sig_walk<NCOMP>(arena, off, k_lo, k_hi, 0, sig_out, bufs, ctab, rc);
-    return;
-  }
-  // batch: this warp's share of the virtual bytes, as virtual rows [v_lo, v_hi)
-  const uint64_t vrows = S_SIDE ? __ldg(&J[nj].vs) : __ldg(&J[nj].vr);
-  const uint64_t vbytes = S_SIDE ? __ldg(&J[nj].vbs) : __ldg(&J[nj].vbr);
-  auto vcut = [&](uint64_t w) -> uint64_t {
-    if (w == 0) return 0;
-    if (w >= nwarps) return vrows;
-    const uint64_t t = (uint64_t)((unsigned __int128)vbytes * w / nwarps);
-    if (t >= vbytes) return vrows;
-    return vcut_in_join<S_SIDE>(J, off, join_of_vbyte<S_SIDE>(J, nj, t), t);
-  };
-  const uint64_t v_lo = vcut(warp), v_hi = warp + 1 >= nwarps ? vrows : vcut(warp + 1);
-  // walk the pieces of [v_lo, v_hi) that fall in each join
-  uint64_t v = v_lo;
-  while (v < v_hi) {
-    const int j = join_of_virtual<S_SIDE>(J, nj, v);
-    const uint64_t b = S_SIDE ? __ldg(&J[j].s_begin) : __ldg(&J[j].r_begin);
-    const uint64_t e = S_SIDE ? __ldg(&J[j].s_end) : __ldg(&J[j].r_end);
-    const uint64_t v0 = S_SIDE ? __ldg(&J[j].vs) : __ldg(&J[j].vr);
-    const uint64_t vend = v0 + (e - b) < v_hi ? v0 + (e - b) : v_hi;
-    sig_walk<NCOMP>(arena, off, b + (v - v0), b + (vend - v0), v0 - b, sig_out, bufs, ctab, rc);
-    v = vend;
-  }
 }
 
 // ----------------------------------------------------------------------------
@@ -960,37 +834,38 @@ static as_status cuda_fail(cudaError_t e, const char* where) {
 }
 
 // The instantiations of the signature kernel: table addressing (AT400),
-// components and shape (warps per block, blocks in flight per key).
+// components, shape (warps per block, blocks in flight per key) and whether
+// it runs over the virtual rows of a batch (4 components only).
 static_assert(kLKShapeCount == 3, "one case per shape below");
-template <bool AT400, int NCOMP, int SHAPE>
+template <bool AT400, int NCOMP, int SHAPE, bool BATCH>
 static cudaError_t key_kernel_attr() {
   constexpr LKShape k = kLKShapes[SHAPE];
-  return cudaFuncSetAttribute(reinterpret_cast<const void*>(sig_key_kernel<AT400, NCOMP, k.warps, k.depth>),
+  return cudaFuncSetAttribute(reinterpret_cast<const void*>(sig_key_kernel<AT400, NCOMP, k.warps, k.depth, BATCH>),
                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lk_smem_bytes(k.warps, k.depth));
 }
-template <bool AT400, int NCOMP>
+template <bool AT400, int NCOMP, bool BATCH>
 static cudaError_t key_kernel_attrs() {
-  cudaError_t e = key_kernel_attr<AT400, NCOMP, 0>();
-  if (e == cudaSuccess) e = key_kernel_attr<AT400, NCOMP, 1>();
-  if (e == cudaSuccess) e = key_kernel_attr<AT400, NCOMP, 2>();
+  cudaError_t e = key_kernel_attr<AT400, NCOMP, 0, BATCH>();
+  if (e == cudaSuccess) e = key_kernel_attr<AT400, NCOMP, 1, BATCH>();
+  if (e == cudaSuccess) e = key_kernel_attr<AT400, NCOMP, 2, BATCH>();
   return e;
 }
-template <bool AT400, int NCOMP, int SHAPE>
+template <bool AT400, int NCOMP, int SHAPE, bool BATCH>
 static void key_kernel_launch(int sms, const uint8_t* arena, const uint64_t* off, uint64_t n, uint64_t* out,
-                              cudaStream_t s) {
+                              const BatchJoin* J, int nj, int s_side, cudaStream_t s) {
   constexpr LKShape k = kLKShapes[SHAPE];
   const uint64_t want = (n + 32ull * k.warps - 1) / (32ull * k.warps);
   const unsigned blocks = (unsigned)(want < (uint64_t)sms ? (want < 1 ? 1 : want) : (uint64_t)sms);
-  sig_key_kernel<AT400, NCOMP, k.warps, k.depth><<<blocks, 32 * k.warps, lk_smem_bytes(k.warps, k.depth), s>>>(arena, off, n,
-                                                                                                      out);
+  sig_key_kernel<AT400, NCOMP, k.warps, k.depth, BATCH>
+      <<<blocks, 32 * k.warps, lk_smem_bytes(k.warps, k.depth), s>>>(arena, off, n, out, J, nj, s_side);
 }
-template <bool AT400, int NCOMP>
+template <bool AT400, int NCOMP, bool BATCH>
 static void key_kernel_launch_shape(int shape, int sms, const uint8_t* arena, const uint64_t* off, uint64_t n,
-                                    uint64_t* out, cudaStream_t s) {
+                                    uint64_t* out, const BatchJoin* J, int nj, int s_side, cudaStream_t s) {
   switch (shape) {
-    case 1: key_kernel_launch<AT400, NCOMP, 1>(sms, arena, off, n, out, s); break;
-    case 2: key_kernel_launch<AT400, NCOMP, 2>(sms, arena, off, n, out, s); break;
-    default: key_kernel_launch<AT400, NCOMP, 0>(sms, arena, off, n, out, s); break;
+    case 1: key_kernel_launch<AT400, NCOMP, 1, BATCH>(sms, arena, off, n, out, J, nj, s_side, s); break;
+    case 2: key_kernel_launch<AT400, NCOMP, 2, BATCH>(sms, arena, off, n, out, J, nj, s_side, s); break;
+    default: key_kernel_launch<AT400, NCOMP, 0, BATCH>(sms, arena, off, n, out, J, nj, s_side, s); break;
   }
 }
 
@@ -1005,14 +880,6 @@ struct DeviceState {
 };
 
 // launch the signature kernel instantiation that matches the device
-template <bool S_SIDE, int NCOMP = 4>
-static void launch_sig_kernel(const DeviceState* d, unsigned blocks, cudaStream_t s, const uint8_t* arena,
-                              const uint64_t* off, uint64_t n, uint64_t* out, const BatchJoin* J, int nj) {
-  if (d->tables_at400)
-    sig_kernel<S_SIDE, true, NCOMP><<<blocks, kThreads, kSmemSig, s>>>(arena, off, n, out, J, nj);
-  else
-    sig_kernel<S_SIDE, false, NCOMP><<<blocks, kThreads, kSmemSig, s>>>(arena, off, n, out, J, nj);
-}
 
 static std::mutex g_dev_mu;
 static DeviceState g_dev[kMaxDevices];
@@ -1086,17 +953,12 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaDeviceGetAttribute(&d.sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess)
       return cuda_fail(e, "device query");
     {
-      const void* fns[6] = {reinterpret_cast<const void*>(sig_kernel<false, false>),
-                            reinterpret_cast<const void*>(sig_kernel<false, true>),
-                            reinterpret_cast<const void*>(sig_kernel<true, false>),
-                            reinterpret_cast<const void*>(sig_kernel<true, true>),
-                            reinterpret_cast<const void*>(sig_kernel<false, false, 2>),
-                            reinterpret_cast<const void*>(sig_kernel<false, true, 2>)};
-      for (const void* f : fns)
-        if ((e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemSig)) != cudaSuccess)
-          return cuda_fail(e, "kernel attribute");
-      if ((e = key_kernel_attrs<true, 4>()) != cudaSuccess || (e = key_kernel_attrs<false, 4>()) != cudaSuccess ||
-          (e = key_kernel_attrs<true, 2>()) != cudaSuccess || (e = key_kernel_attrs<false, 2>()) != cudaSuccess)
+      if ((e = key_kernel_attrs<true, 4, false>()) != cudaSuccess ||
+          (e = key_kernel_attrs<false, 4, false>()) != cudaSuccess ||
+          (e = key_kernel_attrs<true, 2, false>()) != cudaSuccess ||
+          (e = key_kernel_attrs<false, 2, false>()) != cudaSuccess ||
+          (e = key_kernel_attrs<true, 4, true>()) != cudaSuccess ||
+          (e = key_kernel_attrs<false, 4, true>()) != cudaSuccess)
         return cuda_fail(e, "kernel attribute");
     }
     // where dynamic shared memory starts (the tables are its first bytes)
@@ -1182,14 +1044,27 @@ static as_status launch_sig(const uint8_t* arena, const uint64_t* off, uint64_t 
   if (n == 0) return AS_OK;
   if (shape < 0 || shape >= kLKShapeCount) return fail(AS_ERR_INVALID, "signature kernel shape %d", shape);
   if (ncomp == 2) {
-    if (d->tables_at400) key_kernel_launch_shape<true, 2>(shape, d->sms, arena, off, n, out, s);
-    else key_kernel_launch_shape<false, 2>(shape, d->sms, arena, off, n, out, s);
+    if (d->tables_at400) key_kernel_launch_shape<true, 2, false>(shape, d->sms, arena, off, n, out, nullptr, 0, 0, s);
+    else key_kernel_launch_shape<false, 2, false>(shape, d->sms, arena, off, n, out, nullptr, 0, 0, s);
   } else {
-    if (d->tables_at400) key_kernel_launch_shape<true, 4>(shape, d->sms, arena, off, n, out, s);
-    else key_kernel_launch_shape<false, 4>(shape, d->sms, arena, off, n, out, s);
+    if (d->tables_at400) key_kernel_launch_shape<true, 4, false>(shape, d->sms, arena, off, n, out, nullptr, 0, 0, s);
+    else key_kernel_launch_shape<false, 4, false>(shape, d->sms, arena, off, n, out, nullptr, 0, 0, s);
   }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "signature kernel launch");
+  return AS_OK;
+}
+
+// The signatures of one side of a batch over its joins' row ranges (n virtual
+// rows; out indexed by virtual row), with the one-key-per-lane kernel.
+static as_status launch_sig_batch(const DeviceState* d, const uint8_t* arena, const uint64_t* off, uint64_t n,
+                                  uint64_t* out, const BatchJoin* J, int nj, int s_side, int shape, cudaStream_t s) {
+  if (n == 0) return AS_OK;
+  if (shape < 0 || shape >= kLKShapeCount) return fail(AS_ERR_INVALID, "signature kernel shape %d", shape);
+  if (d->tables_at400) key_kernel_launch_shape<true, 4, true>(shape, d->sms, arena, off, n, out, J, nj, s_side, s);
+  else key_kernel_launch_shape<false, 4, true>(shape, d->sms, arena, off, n, out, J, nj, s_side, s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "batch signature kernel launch");
   return AS_OK;
 }
 
@@ -2055,7 +1930,7 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
     if (b->r_first != AS_ROWS_SCATTERED) {             // one run of rows: the single-relation kernel
       if ((st = launch_sig(d_arenaR, d_offR + b->r_first, b->mR, b->sigR, s, 4, b->sig_shape)) != AS_OK) return st;
     } else {
-      launch_sig_kernel<false>(d, walk_blocks(b->mR, d->sms), s, d_arenaR, d_offR, b->mR, b->sigR, J, nj);
+      if ((st = launch_sig_batch(d, d_arenaR, d_offR, b->mR, b->sigR, J, nj, 0, b->sig_shape, s)) != AS_OK) return st;
     }
     uint64_t blocks = (b->mR + 255) / 256;
     const uint64_t lim = (uint64_t)d->sms * 16;
@@ -2066,7 +1941,7 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
     if (b->s_first != AS_ROWS_SCATTERED) {
       if ((st = launch_sig(d_arenaS, d_offS + b->s_first, b->nS, b->sigS, s, 4, b->sig_shape)) != AS_OK) return st;
     } else {
-      launch_sig_kernel<true>(d, walk_blocks(b->nS, d->sms), s, d_arenaS, d_offS, b->nS, b->sigS, J, nj);
+      if ((st = launch_sig_batch(d, d_arenaS, d_offS, b->nS, b->sigS, J, nj, 1, b->sig_shape, s)) != AS_OK) return st;
     }
     VerifyParams P;
     P.slots = slots;

@@ -39,6 +39,9 @@
 // signatures together.  (Staging the keys through shared memory was measured
 // slower: per-lane 16-byte copies fetch each 32-byte sector twice, and a TMA
 // bulk copy per lane is serialised because its operands are warp-uniform.)
+// In a batch the keys are the joins' row ranges back to back ("virtual
+// rows"): the warps split them by key bytes across the joins, and a window
+// ends with its join's rows so that its keys are consecutive in the relation.
 #pragma once
 #include <cstdint>
 
@@ -347,7 +350,9 @@ __device__ ALGSIG_LK_FINISH uint64_t lk_finish(const uint32_t (&c)[16], const ui
 // The signature of a key with a block outside the arena's readable range
 // (its first 32 bytes or its last): the blocks one by one with checked loads.
 // At most a few keys per relation take this path.
-template <int NCOMP, int kLKWarps, int kLKDepth, class Cursor>
+// (one copy per kernel instantiation: ptxas fails on a non-inlined function
+// shared by kernels of different shapes)
+template <int NCOMP, int kLKWarps, int kLKDepth, bool BATCH, class Cursor>
 __device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_lo, const uint8_t* lim_hi,
                                              const uint16_t* inv32, const uint4* mt, const Cursor& rc) {
   const uint32_t sh = 8u * (k.a & 1u);
@@ -374,7 +379,7 @@ __device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_
 // its block 0 in the group's last iteration.  An odd key whose last aligned
 // block ends with a key byte needs the next block's first byte.  Keys with a
 // block outside the arena's readable range are computed apart (lk_edge_key).
-template <int NCOMP, int kLKWarps, int kLKDepth, class Cursor>
+template <int NCOMP, int kLKWarps, int kLKDepth, bool BATCH, class Cursor>
 __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8_t* lim_lo, const uint8_t* lim_hi,
                                          const uint16_t* inv32, const uint4* mt, uint64_t* __restrict__ sig_out,
                                          const Cursor& rc) {
@@ -432,13 +437,67 @@ __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8
   }
   if (k.valid && !k.edge) sig_out[k.kq] = lk_finish<NCOMP>(c, c3, k.a, inv32, rc);
   if (__any_sync(kFull, k.edge))
-    if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP, kLKWarps, kLKDepth>(k, lim_lo, lim_hi, inv32, mt, rc);
+    if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP, kLKWarps, kLKDepth, BATCH>(k, lim_lo, lim_hi, inv32, mt, rc);
 }
 
-template <bool AT400, int NCOMP, int kLKWarps, int kLKDepth>
+// The window of keys starting at key wb (keys below k_hi): returns its key
+// count and sets *wa to its first row in the relation.  In a batch the keys are
+// virtual rows (the joins' row ranges back to back) and a window ends with its
+// join's rows, so that its keys are consecutive rows of the relation.
+template <bool BATCH>
+__device__ __forceinline__ uint32_t lk_window(const BatchJoin* __restrict__ J, int nj, int s_side, uint64_t wb,
+                                              uint64_t k_hi, uint64_t* wa) {
+  uint64_t lim = k_hi;
+  *wa = wb;
+  if constexpr (BATCH) {
+    const int j = s_side ? join_of_virtual<true>(J, nj, wb) : join_of_virtual<false>(J, nj, wb);
+    const uint64_t b = s_side ? __ldg(&J[j].s_begin) : __ldg(&J[j].r_begin);
+    const uint64_t e = s_side ? __ldg(&J[j].s_end) : __ldg(&J[j].r_end);
+    const uint64_t v0 = s_side ? __ldg(&J[j].vs) : __ldg(&J[j].vr);
+    *wa = b + (wb - v0);
+    if (v0 + (e - b) < lim) lim = v0 + (e - b);
+  }
+  const uint64_t left = lim - wb;
+  return left < (uint64_t)kLKWin ? (uint32_t)left : (uint32_t)kLKWin;
+}
+
+// A warp's keys [lo, hi) of n (virtual rows of a batch side, or rows of a
+// relation): equal counts below kLKSearchFrom keys, else a byte-balanced cut
+// (in a batch, over the joins' key bytes back to back).  Whole warp.
+template <bool BATCH>
+__device__ __forceinline__ void lk_warp_range(const BatchJoin* __restrict__ J, int nj, int s_side,
+                                              const uint64_t* __restrict__ off, uint64_t n, uint64_t warp,
+                                              uint64_t nwarps, uint64_t* lo, uint64_t* hi) {
+  if (n < kLKSearchFrom) {
+    *lo = (uint64_t)((unsigned __int128)n * warp / nwarps);
+    *hi = (uint64_t)((unsigned __int128)n * (warp + 1) / nwarps);
+    return;
+  }
+  if constexpr (!BATCH) {
+    warp_key_range(off, n, warp, nwarps, lo, hi);
+  } else {
+    const uint64_t vbytes = s_side ? __ldg(&J[nj].vbs) : __ldg(&J[nj].vbr);
+    auto cut = [&](uint64_t w) -> uint64_t {
+      if (w == 0) return 0;
+      if (w >= nwarps) return n;
+      const uint64_t t = (uint64_t)((unsigned __int128)vbytes * w / nwarps);
+      if (t >= vbytes) return n;
+      return s_side ? vcut_in_join<true>(J, off, join_of_vbyte<true>(J, nj, t), t)
+                    : vcut_in_join<false>(J, off, join_of_vbyte<false>(J, nj, t), t);
+    };
+    *lo = cut(warp);
+    *hi = cut(warp + 1);
+  }
+}
+
+// The signatures of n keys: the rows of a relation (BATCH false), or the
+// virtual rows of one side of a batch (BATCH true; s_side picks S, J and nj
+// describe the joins, and sig_out is indexed by virtual row).
+template <bool AT400, int NCOMP, int kLKWarps, int kLKDepth, bool BATCH>
 __global__ void __launch_bounds__(32 * kLKWarps, 1) sig_key_kernel(const uint8_t* __restrict__ arena,
                                                                 const uint64_t* __restrict__ off, uint64_t n,
-                                                                uint64_t* __restrict__ sig_out) {
+                                                                uint64_t* __restrict__ sig_out,
+                                                                const BatchJoin* __restrict__ J, int nj, int s_side) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* red = reinterpret_cast<uint32_t*>(smem);
   uint16_t* inv32 = reinterpret_cast<uint16_t*>(smem + kRedBytes);
@@ -453,16 +512,15 @@ __global__ void __launch_bounds__(32 * kLKWarps, 1) sig_key_kernel(const uint8_t
   const uint64_t warp = (uint64_t)blockIdx.x * kLKWarps + wib;
   const uint64_t nwarps = (uint64_t)gridDim.x * kLKWarps;
   uint64_t k_lo, k_hi;
-  if (n < kLKSearchFrom) {                          // small relation: equal key counts, no search
-    k_lo = (uint64_t)((unsigned __int128)n * warp / nwarps);
-    k_hi = (uint64_t)((unsigned __int128)n * (warp + 1) / nwarps);
-  } else {
-    warp_key_range(off, n, warp, nwarps, &k_lo, &k_hi);
-  }
-  if (k_lo < k_hi) lk_prefetch_window(W, off, k_lo, k_hi);
-  // readable bytes of the arena: from its start to the 16-byte boundary after the last key byte
+  lk_warp_range<BATCH>(J, nj, s_side, off, n, warp, nwarps, &k_lo, &k_hi);
+  uint64_t wa = 0;                                  // the current window: first row and key count
+  uint32_t wn = k_lo < k_hi ? lk_window<BATCH>(J, nj, s_side, k_lo, k_hi, &wa) : 0u;
+  if (wn) lk_prefetch_window(W, off, wa, wa + wn);
+  // readable bytes of the arena: from its start to the 16-byte boundary after the relation's last key byte
+  uint64_t rows_all = n;
+  if constexpr (BATCH) rows_all = s_side ? __ldg(&J[nj].s_end) : __ldg(&J[nj].r_end);
   const uint8_t* lim_lo = arena;
-  const uint8_t* lim_hi = arena + ((__ldg(off + n) + 15) & ~15ull);
+  const uint8_t* lim_hi = arena + ((__ldg(off + rows_all) + 15) & ~15ull);
   for (int i = threadIdx.x; i < kRedWords / 4; i += blockDim.x)   // the reduction tables, from their image
     reinterpret_cast<uint4*>(red)[i] = g_red_img[i];
   __syncthreads();
@@ -474,20 +532,24 @@ __global__ void __launch_bounds__(32 * kLKWarps, 1) sig_key_kernel(const uint8_t
   for (uint64_t wb = k_lo; wb < k_hi;) {
     cp_async_wait_all();                            // the window's offsets
     __syncwarp();
-    const uint64_t left = k_hi - wb;
-    const uint32_t wn = left < (uint64_t)kLKWin ? (uint32_t)left : (uint32_t)kLKWin;
     lk_sort_window(W, wn, reinterpret_cast<uintptr_t>(arena));
     const uint32_t ng = (wn + 31) / 32;
+    uint64_t na = 0;
+    uint32_t nn = 0;
     for (uint32_t g = 0; g < ng; ++g) {
       LKKey k;
       const uint32_t G = lk_load_group(k, W, wb, g, arena, lim_lo, lim_hi);
       if (g + 1 == ng) {                            // the window's offsets are free: fetch the next ones
         __syncwarp();
-        lk_prefetch_window(W, off, wb + wn, k_hi);
+        if (wb + wn < k_hi) {
+          nn = lk_window<BATCH>(J, nj, s_side, wb + wn, k_hi, &na);
+          lk_prefetch_window(W, off, na, na + nn);
+        }
       }
-      lk_group<NCOMP, kLKWarps, kLKDepth>(k, G, lim_lo, lim_hi, inv32, mt, sig_out, rc);
+      lk_group<NCOMP, kLKWarps, kLKDepth, BATCH>(k, G, lim_lo, lim_hi, inv32, mt, sig_out, rc);
     }
     wb += wn;
+    wn = nn;
   }
   cp_async_wait_all();
 }

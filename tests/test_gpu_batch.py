@@ -98,9 +98,9 @@ def test_batch_subset_of_pool(cuda, batch):
 
 def test_batch_contiguous_run_and_gapped_run(cuda, batch):
     """Joins whose rows form one run of the relations (starting mid-pool) take the
-    single-relation signature kernel; the same joins with one left out (a gap in
-    the rows) take the batch walk; with a gap in S's rows only, R takes the
-    single-relation kernel and S the walk.  Every join gets the oracle's pairs."""
+    signature kernel over that run; the same joins with one left out (a gap in
+    the rows) take it over the joins' row ranges; with a gap in S's rows only,
+    R takes the run and S the row ranges.  Every join gets the oracle's pairs."""
     ag = cuda
     Rd, Sd = dev(ag, batch.R), dev(ag, batch.S)
     R = ag.DeviceRelation(Rd.arena, Rd.off, None)
@@ -203,3 +203,35 @@ def test_autotune_cache_skips_timing_for_a_known_shape(cuda, batch, tmp_path):
     gb2.replay()
     torch.cuda.synchronize()
     assert gb2.counts.cpu().tolist() == list(batch.expected)
+
+
+@pytest.mark.parametrize("shape", [0, 2])
+def test_gapped_batch_signatures_at_scale(cuda, shape):
+    """A batch whose joins' rows have gaps, with more than 2^19 S rows (so the
+    signature kernel splits the joins' rows over its warps by key bytes) and
+    runs that end inside a window: every virtual row's signature equals the
+    oracle's signature of its relation row, at two kernel shapes."""
+    ag = cuda
+    wl = workloads.generate(workloads.CONFIGS["large"].scaled(60_000, 1_200_000))
+    R = ag.DeviceRelation.from_host(wl.R.arena, wl.R.off, None)
+    S = ag.DeviceRelation.from_host(wl.S.arena, wl.S.off, None)
+    s_runs = [(0, 150_000), (200_000, 400_017), (400_017, 400_017), (450_003, 800_000), (800_010, 1_100_000),
+              (1_150_000, 1_200_000)]
+    r_runs = [(0, 9_000), (10_000, 20_000), (20_000, 20_000), (25_000, 40_001), (40_100, 55_000), (55_500, 60_000)]
+    ranges = [(rb, re_, sb, se) for (rb, re_), (sb, se) in zip(r_runs, s_runs)]
+    descs = ag.make_descs(ranges, [1 << 16] * len(ranges))
+    ws = ag.alloc_ws(ag.join_batch_ws_bytes(descs, R.n, S.n, 0.5))
+    b = ag.join_batch_prepare(descs, R, S, ws, 0.5)
+    assert b.r_first == ag.ROWS_SCATTERED and b.s_first == ag.ROWS_SCATTERED and b.nS > (1 << 19)
+    b.sig_shape = shape
+    pairs = torch.empty(2 * (1 << 16) * len(ranges), dtype=torch.int32, device="cuda")
+    counts = torch.zeros(len(ranges), dtype=torch.int64, device="cuda")
+    ag.join_batch_run(b, R, S, pairs, counts)
+    torch.cuda.synchronize()
+    base = ws.data_ptr()
+    for ptr, n, rel, runs in ((b.sigR, b.mR, wl.R, r_runs), (b.sigS, b.nS, wl.S, s_runs)):
+        got = ws[ptr - base: ptr - base + 8 * n].view(torch.int64).cpu().numpy().view(np.uint64)
+        want = oracle.sig_batch(rel.arena, rel.off, nthreads=8)
+        want = np.concatenate([want[a:e] for a, e in runs])
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, (shape, bad.size, bad[:5].tolist())
