@@ -832,6 +832,11 @@ def run_gpu(args):
         "paper_variants": paper_variants,
         "cumulative_signatures": cumulative_sigs,
         "pairs": total_pairs,
+        "device_bytes": {"table": ag.join_table_bytes(m, lf), "signatures": 8 * (m + n),
+                         "join_workspace": ag.join_ws_bytes(m, n, lf), "pairs_buffer": 8 * cap,
+                         "inputs": key_bytes + 12 * (m + n + 2),
+                         "note": "per join: the hash table (slots, R signatures, flags, matched-R bitmap), R's and "
+                                 "S's signatures, the pair buffer and the resident relations (keys, offsets, ids)"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "ms_per_step": e2e_s * 1e3, "chunks": len(cuts) - 1, "h2d_pinned_gbs": h2d_gbs,

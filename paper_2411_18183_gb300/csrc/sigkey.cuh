@@ -530,26 +530,25 @@ __global__ void __launch_bounds__(32 * kLKWarps, 1) sig_key_kernel(const uint8_t
   if constexpr (AT400) rc = red_cursor_at400(); else rc = red_cursor(red);
 
   for (uint64_t wb = k_lo; wb < k_hi;) {
+    wn = lk_window<BATCH>(J, nj, s_side, wb, k_hi, &wa);   // as prefetched
     cp_async_wait_all();                            // the window's offsets
     __syncwarp();
     lk_sort_window(W, wn, reinterpret_cast<uintptr_t>(arena));
     const uint32_t ng = (wn + 31) / 32;
-    uint64_t na = 0;
-    uint32_t nn = 0;
     for (uint32_t g = 0; g < ng; ++g) {
       LKKey k;
       const uint32_t G = lk_load_group(k, W, wb, g, arena, lim_lo, lim_hi);
       if (g + 1 == ng) {                            // the window's offsets are free: fetch the next ones
         __syncwarp();
         if (wb + wn < k_hi) {
-          nn = lk_window<BATCH>(J, nj, s_side, wb + wn, k_hi, &na);
+          uint64_t na;
+          const uint32_t nn = lk_window<BATCH>(J, nj, s_side, wb + wn, k_hi, &na);
           lk_prefetch_window(W, off, na, na + nn);
         }
       }
       lk_group<NCOMP, kLKWarps, kLKDepth, BATCH>(k, G, lim_lo, lim_hi, inv32, mt, sig_out, rc);
     }
     wb += wn;
-    wn = nn;
   }
   cp_async_wait_all();
 }
