@@ -79,8 +79,10 @@ constexpr uint32_t kLKNbCap = (1u << (31 - kLKIdxBits)) - 1u;   // block counts 
 
 struct LKWarp {
   uint64_t woff[kLKWin + 2];       // offsets of the window's keys (woff[i] = off[wb + i]), i <= wn
-  uint32_t order[kLKWin];          // window entries sorted by (block count << 8 | index)
+  uint32_t order[kLKWin];          // window entries by block count: (block count << 8 | index)
+  uint32_t hist[256];              // the counting sort's bins (block counts, 255 and up in the last)
 };
+static_assert(kLKWin == 256, "the window sort: 8 entries and 8 bins per lane");
 constexpr size_t kSmemLKMasks = 1056;                 // 33 rows of 32 bytes
 // (the blocks in flight of a shape live in registers: its depth takes no shared memory)
 constexpr size_t lk_smem_bytes(int warps, int /*depth*/) {
@@ -221,35 +223,62 @@ __device__ __forceinline__ uint32_t lk_blocks(uintptr_t abs, uint64_t len) {
   return nb < 0xFFFFFFFFull ? (uint32_t)nb : 0xFFFFFFFFu;
 }
 
-// sort the window's entries by block count (bitonic network over kLKWin entries)
+// order the window's entries by block count: a counting sort over the block
+// counts (255 and more share the last bin; the order within a bin is
+// arbitrary), so that each group of 32 consecutive entries has keys of
+// nearly equal length
 __device__ __forceinline__ void lk_sort_window(LKWarp& W, uint32_t wn, uintptr_t arena) {
   const uint32_t lane = threadIdx.x & 31u;
-  for (uint32_t i = lane; i < (uint32_t)kLKWin; i += 32) {
-    uint32_t e = kLKNoKey;
+  if (wn <= 32) {                                    // one group: nothing to balance
+    for (uint32_t i = lane; i < (uint32_t)kLKWin; i += 32) W.order[i] = i < wn ? i : kLKNoKey;
+    __syncwarp();
+    return;
+  }
+#pragma unroll
+  for (int t = 0; t < 8; ++t) W.hist[8 * lane + t] = 0u;
+  __syncwarp();
+  uint32_t e[8], bin[8], rank[8];
+#pragma unroll
+  for (int j = 0; j < 8; ++j) {
+    const uint32_t i = lane + 32u * (uint32_t)j;
+    e[j] = kLKNoKey;
+    bin[j] = 0;
+    rank[j] = 0;
     if (i < wn) {
       const uint64_t ks = W.woff[i], len = W.woff[i + 1] - ks;
       const uint32_t nb = lk_blocks(arena + ks, len);
-      e = ((nb < kLKNbCap ? nb : kLKNbCap) << kLKIdxBits) | i;
+      e[j] = ((nb < kLKNbCap ? nb : kLKNbCap) << kLKIdxBits) | i;
+      bin[j] = nb < 255u ? nb : 255u;
+      rank[j] = atomicAdd(&W.hist[bin[j]], 1u);
     }
-    W.order[i] = e;
   }
   __syncwarp();
-  if (wn <= 32) return;                              // one group: nothing to balance
-  for (uint32_t k = 2; k <= (uint32_t)kLKWin; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t t = lane; t < (uint32_t)kLKWin / 2; t += 32) {
-        const uint32_t i = ((t & ~(j - 1)) << 1) | (t & (j - 1));
-        const uint32_t p = i + j;
-        const uint32_t a = W.order[i], b = W.order[p];
-        const bool up = (i & k) == 0;
-        if ((a > b) == up) {
-          W.order[i] = b;
-          W.order[p] = a;
-        }
-      }
-      __syncwarp();
-    }
+  // exclusive prefix sum over the bins, 8 consecutive bins per lane
+  uint32_t h[8], sum = 0;
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    h[t] = W.hist[8 * lane + t];
+    sum += h[t];
   }
+  uint32_t incl = sum;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t o = __shfl_up_sync(kFull, incl, d);
+    if (lane >= (uint32_t)d) incl += o;
+  }
+  uint32_t base = incl - sum;
+  __syncwarp();
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    W.hist[8 * lane + t] = base;
+    base += h[t];
+  }
+  __syncwarp();
+#pragma unroll
+  for (int j = 0; j < 8; ++j)
+    if (e[j] != kLKNoKey) W.order[W.hist[bin[j]] + rank[j]] = e[j];
+  for (uint32_t i = wn + lane; i < (uint32_t)kLKWin; i += 32) W.order[i] = kLKNoKey;
+  __syncwarp();
 }
 
 // group g of the window (wb: its first key) into the lanes; returns the
