@@ -765,8 +765,11 @@ def run_gpu(args):
         raise SystemExit("end-to-end join: wrong pair count")
     barrier()
     te = time.perf_counter()
+    e2e_runs = []
     for _ in range(e2e_steps):
+        t_run = time.perf_counter()
         cnt = sj.run(hR, hS, cuts, out_host)
+        e2e_runs.append((time.perf_counter() - t_run) * 1e3)
     barrier()
     e2e_s = ranks_max((time.perf_counter() - te) / e2e_steps)
     e2e_value = replica_value(n, world, e2e_s * 1e3)
@@ -839,7 +842,8 @@ def run_gpu(args):
                                  "S's signatures, the pair buffer and the resident relations (keys, offsets, ids)"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_s * 1e3, "chunks": len(cuts) - 1, "h2d_pinned_gbs": h2d_gbs,
+                "ms_per_step": e2e_s * 1e3, "runs_ms": [round(x, 2) for x in e2e_runs], "chunks": len(cuts) - 1,
+                "h2d_pinned_gbs": h2d_gbs,
                 "copy_bound_ms": (h2d + d2h) / (h2d_gbs * 1e9) * 1e3,
                 "path": "stream.HostStreamJoin: pinned host R and S, S copied in chunks under the kernels"},
         "gpu_launches": 4 * args.steps,

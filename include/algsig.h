@@ -44,6 +44,11 @@
  * Streams: every call is asynchronous on the given stream (a cudaStream_t
  * passed as void*, NULL = legacy default stream) unless it is given a host
  * pointer to return a count, in which case it synchronises that stream.
+ * as_join, as_join_batch_run and as_baseline_join run S's signatures (or
+ * hashes) on a side stream of the library (four per device, created with the
+ * tables) forked from the given stream and joined back into it before the
+ * probe, so that they overlap R's signatures and the build; the calls stay
+ * asynchronous on the given stream and can be captured in a CUDA graph.
  *
  * Errors: every call returns an as_status; AS_OK is 0.  as_last_error()
  * gives a human-readable message for the calling thread's last failure.  No

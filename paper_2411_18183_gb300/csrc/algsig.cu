@@ -12,6 +12,7 @@
 // walk of rounds.cuh over the joins' row ranges.
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -869,6 +870,7 @@ static void key_kernel_launch_shape(int shape, int sms, const uint8_t* arena, co
   }
 }
 
+constexpr int kSideStreams = 4;
 struct DeviceState {
   bool ready = false;
   int sms = 0;
@@ -877,6 +879,8 @@ struct DeviceState {
   int capsig_blocks_per_sm = 1;
   int prefix_thread_blocks_per_sm = 1;
   bool tables_at400 = false;   // dynamic shared memory starts at shared address 0x400
+  cudaStream_t side[kSideStreams] = {};   // side streams (SideStream), created with the state
+  std::atomic<unsigned> side_next{0};
 };
 
 // launch the signature kernel instantiation that matches the device
@@ -971,6 +975,9 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaMemcpyFromSymbol(&base, g_dyn_smem_base, sizeof(base))) != cudaSuccess)
       return cuda_fail(e, "shared memory probe");
     d.tables_at400 = base == kTablesAt400;
+    for (int i = 0; i < kSideStreams; ++i)
+      if ((e = cudaStreamCreateWithFlags(&d.side[i], cudaStreamNonBlocking)) != cudaSuccess)
+        return cuda_fail(e, "side stream");
     if ((e = cudaFuncSetAttribute(prefix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemPrefix)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
@@ -1067,6 +1074,40 @@ static as_status launch_sig_batch(const DeviceState* d, const uint8_t* arena, co
   if (e != cudaSuccess) return cuda_fail(e, "batch signature kernel launch");
   return AS_OK;
 }
+
+// Work that may overlap the caller's stream s: fork() makes a side stream
+// (from a small per-device pool) wait for everything enqueued on s so far;
+// join() makes s wait for everything enqueued on the side stream since.  The
+// events are per call, so concurrent callers never wait on each other's
+// records; inside CUDA graph capture the fork and the join become edges of
+// the graph.
+struct SideStream {
+  cudaStream_t main = nullptr, side = nullptr;
+  bool forked = false;
+  as_status fork(DeviceState* d, cudaStream_t s) {
+    main = s;
+    side = d->side[d->side_next.fetch_add(1u) % kSideStreams];
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "side stream event");
+    if ((e = cudaEventRecord(ev, main)) == cudaSuccess) e = cudaStreamWaitEvent(side, ev, 0);
+    cudaEventDestroy(ev);                            // released once the device has passed it
+    if (e != cudaSuccess) return cuda_fail(e, "side stream fork");
+    forked = true;
+    return AS_OK;
+  }
+  as_status join() {
+    if (!forked) return AS_OK;
+    forked = false;
+    cudaEvent_t ev;
+    cudaError_t e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_fail(e, "side stream event");
+    if ((e = cudaEventRecord(ev, side)) == cudaSuccess) e = cudaStreamWaitEvent(main, ev, 0);
+    cudaEventDestroy(ev);
+    if (e != cudaSuccess) return cuda_fail(e, "side stream join");
+    return AS_OK;
+  }
+};
 
 }  // namespace algsig
 
@@ -1455,13 +1496,30 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
   if (!tb) return fail(AS_ERR_INVALID, "as_join: need 0 < load_factor <= 1 and m < 2^32-1");
   const size_t need = as_join_ws_bytes(m, n, load_factor);
   if (!d_ws || ws_bytes < need) return fail(AS_ERR_NOMEM, "as_join: workspace of %zu bytes, need %zu", ws_bytes, need);
-  as_table t;
-  as_status st = as_join_build(d_ws, tb, d_arenaR, d_offR, d_idR, m, nullptr, load_factor, &t, stream);
+  if (n > 0 && (!d_arenaS || !d_offS)) return fail(AS_ERR_INVALID, "as_join: null relation");
+  if (n > 0 && misaligned16(d_arenaS)) return fail(AS_ERR_INVALID, "as_join: arena not 16-byte aligned");
+  if (reinterpret_cast<uintptr_t>(d_ws) & 255u) return fail(AS_ERR_INVALID, "as_join: workspace not 256-byte aligned");
+  DeviceState* d = nullptr;
+  as_status st = ensure_device(&d);
   if (st != AS_OK) return st;
   uint8_t* rest = (uint8_t*)d_ws + tb;
+  uint64_t* sigS = reinterpret_cast<uint64_t*>(rest + 256);
+  // S's signatures on a side stream, concurrently with R's signatures and the build
+  SideStream side;
+  if (n > 0) {
+    if ((st = side.fork(d, (cudaStream_t)stream)) != AS_OK) return st;
+    if ((st = launch_sig(d_arenaS, d_offS, n, sigS, side.side)) != AS_OK) {
+      side.join();
+      return st;
+    }
+  }
+  as_table t;
+  st = as_join_build(d_ws, tb, d_arenaR, d_offR, d_idR, m, nullptr, load_factor, &t, stream);
+  const as_status js = side.join();
+  if (st != AS_OK) return st;
+  if (js != AS_OK) return js;
   uint64_t* cnt = d_count ? d_count : (uint64_t*)rest;
-  return as_join_probe(&t, d_arenaS, d_offS, d_idS, n, nullptr, rest + 256, need - tb - 256, d_pairs, cap_pairs, cnt,
-                       h_count, stream);
+  return as_join_probe_sigs(&t, d_arenaS, d_offS, d_idS, n, sigS, d_pairs, cap_pairs, cnt, h_count, stream);
 }
 
 // ----------------------------------------------------------------------------
@@ -1769,16 +1827,23 @@ as_status as_baseline_join(const uint8_t* d_arenaR, const uint64_t* d_offR, cons
   if ((e = cudaMemsetAsync(slots, 0xFF, cap * 8, s)) != cudaSuccess) return cuda_fail(e, "table clear");
   if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
   if ((e = cudaMemsetAsync(cnt, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
+  // S's hashes on a side stream, concurrently with R's hashes and the build (as in as_join)
+  SideStream side;
+  if (n > 0) {
+    if ((st = side.fork(d, s)) != AS_OK) return st;
+    bl_hash_kernel<<<walk_blocks(n, d->sms), kThreads, kSmemBHash, side.side>>>(d_arenaS, d_offS, n, hS);
+  }
   if (m > 0) {
     bl_hash_kernel<<<walk_blocks(m, d->sms), kThreads, kSmemBHash, s>>>(d_arenaR, d_offR, m, hR);
     uint64_t blocks = (m + 255) / 256;
     const uint64_t lim = (uint64_t)d->sms * 16;
     if (blocks > lim) blocks = lim;
     bl_build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, cap - 1, hR, m, tagged, flags);
-    if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "baseline build launch");
   }
+  const as_status js = side.join();
+  if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(e, "baseline hash / build launch");
+  if (js != AS_OK) return js;
   if (n > 0) {
-    bl_hash_kernel<<<walk_blocks(n, d->sms), kThreads, kSmemBHash, s>>>(d_arenaS, d_offS, n, hS);
     BVerifyParams P;
     P.slots = slots;
     P.mask = cap - 1;
@@ -1926,23 +1991,35 @@ as_status as_join_batch_run(const as_batch* b, const uint8_t* d_arenaR, const ui
   if ((e = cudaMemsetAsync(b->flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
   if ((e = cudaMemsetAsync(d_counts, 0, 8 * b->n_joins, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
   batch_bytes_kernel<<<1, 1024, 0, s>>>(J, nj, d_offR, d_offS);
+  // S's signatures on a side stream, concurrently with R's signatures and the builds
+  SideStream side;
+  if (b->nS > 0) {
+    if ((st = side.fork(d, s)) != AS_OK) return st;
+    if (b->s_first != AS_ROWS_SCATTERED)
+      st = launch_sig(d_arenaS, d_offS + b->s_first, b->nS, b->sigS, side.side, 4, b->sig_shape);
+    else
+      st = launch_sig_batch(d, d_arenaS, d_offS, b->nS, b->sigS, J, nj, 1, b->sig_shape, side.side);
+    if (st != AS_OK) {
+      side.join();
+      return st;
+    }
+  }
   if (b->mR > 0) {
-    if (b->r_first != AS_ROWS_SCATTERED) {             // one run of rows: the single-relation kernel
-      if ((st = launch_sig(d_arenaR, d_offR + b->r_first, b->mR, b->sigR, s, 4, b->sig_shape)) != AS_OK) return st;
-    } else {
-      if ((st = launch_sig_batch(d, d_arenaR, d_offR, b->mR, b->sigR, J, nj, 0, b->sig_shape, s)) != AS_OK) return st;
+    if (b->r_first != AS_ROWS_SCATTERED)             // one run of rows: the single-relation kernel
+      st = launch_sig(d_arenaR, d_offR + b->r_first, b->mR, b->sigR, s, 4, b->sig_shape);
+    else
+      st = launch_sig_batch(d, d_arenaR, d_offR, b->mR, b->sigR, J, nj, 0, b->sig_shape, s);
+    if (st != AS_OK) {
+      side.join();
+      return st;
     }
     uint64_t blocks = (b->mR + 255) / 256;
     const uint64_t lim = (uint64_t)d->sms * 16;
     if (blocks > lim) blocks = lim;
     build_kernel<<<(unsigned)blocks, 256, 0, s>>>(slots, 0, b->sigR, d_offR, b->mR, b->flags, J, nj);
   }
+  if ((st = side.join()) != AS_OK) return st;
   if (b->nS > 0) {
-    if (b->s_first != AS_ROWS_SCATTERED) {
-      if ((st = launch_sig(d_arenaS, d_offS + b->s_first, b->nS, b->sigS, s, 4, b->sig_shape)) != AS_OK) return st;
-    } else {
-      if ((st = launch_sig_batch(d, d_arenaS, d_offS, b->nS, b->sigS, J, nj, 1, b->sig_shape, s)) != AS_OK) return st;
-    }
     VerifyParams P;
     P.slots = slots;
     P.mask = 0;
