@@ -459,7 +459,9 @@ __device__ __forceinline__ void flush_stage_join(const Stage& st, uint32_t np, c
   __syncwarp();
 }
 
-template <bool BATCH>
+// BATCH: the S rows of a batch's joins; INNER: the plain inner join of one
+// table (no output mode to test per pair)
+template <bool BATCH, bool INNER = false>
 __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
   __shared__ Stage stage_all[kVWarps];
   __shared__ uint4 emask[17];
@@ -470,6 +472,7 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
   uint32_t np = 0;                                   // staged pairs (warp-uniform)
   int sj = -1;                                       // batch: join of the staged pairs
   constexpr bool batch = BATCH;
+  const int mode = INNER ? (int)AS_JOIN_INNER : P.mode;
   const uint64_t ngroups = (P.n + 31) / 32;
   const uint64_t nwarps = (uint64_t)gridDim.x * kVWarps;
   for (uint64_t grp = (uint64_t)blockIdx.x * kVWarps + (threadIdx.x >> 5); grp < ngroups; grp += nwarps) {
@@ -546,7 +549,7 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
           if (lane == 0) asm volatile("prefetch.global.L1 [%0];" ::"l"(P.offR + r2));
         }
         const uint64_t rs = __ldg(P.offR + rj);
-        const bool verify = batch || P.mode != AS_JOIN_SIG_ONLY;   // signature-only: no byte comparison
+        const bool verify = batch || mode != AS_JOIN_SIG_ONLY;   // signature-only: no byte comparison
         bool eq;
         if (lj < kNarrowLen) {
           eq = !verify || warp_equal(P.arenaR + rs, P.arenaS + stj, lj, emask);
@@ -559,11 +562,11 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         if (eq) {
           const uint64_t srow = __shfl_sync(kFull, i, j);
           if (lane == j) matched = true;
-          if (!batch && P.mode >= AS_JOIN_OUTER_R) {  // R-side modes: mark the R row
+          if (!batch && mode >= AS_JOIN_OUTER_R) {  // R-side modes: mark the R row
             if (lane == 0) atomicOr(P.matched + (rj >> 5), 1u << (rj & 31u));
-            if (P.mode != AS_JOIN_OUTER_R) continue;   // rows, not pairs
+            if (mode != AS_JOIN_OUTER_R) continue;   // rows, not pairs
           }
-          if (!batch && (P.mode == AS_JOIN_SEMI || P.mode == AS_JOIN_ANTI)) continue;   // rows, not pairs
+          if (!batch && (mode == AS_JOIN_SEMI || mode == AS_JOIN_ANTI)) continue;   // rows, not pairs
           const int jj = __shfl_sync(kFull, jn, j);
           if (batch && np && jj != sj) {              // the stage holds one join's pairs
             flush_stage_join(stage, np, P, sj);
@@ -582,9 +585,9 @@ __global__ void __launch_bounds__(kVThreads, 4) verify_kernel(VerifyParams P) {
         }
       }
     }
-    if (!batch && (P.mode == AS_JOIN_SEMI || P.mode == AS_JOIN_ANTI || P.mode == AS_JOIN_OUTER_S)) {
+    if (!batch && (mode == AS_JOIN_SEMI || mode == AS_JOIN_ANTI || mode == AS_JOIN_OUTER_S)) {
       // one (AS_NO_ROW, s_id) per selected S row
-      const bool emit = row_live && (P.mode == AS_JOIN_SEMI ? matched : !matched);
+      const bool emit = row_live && (mode == AS_JOIN_SEMI ? matched : !matched);
       const uint32_t em = __ballot_sync(kFull, emit);
       if (em) {
         if (np + (uint32_t)__popc(em) > (uint32_t)kVStage) {
@@ -1005,7 +1008,7 @@ static as_status ensure_device(DeviceState** out) {
     if ((e = cudaFuncSetAttribute(bl_hash_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemBHash)) !=
         cudaSuccess)
       return cuda_fail(e, "kernel attribute");
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.verify_blocks_per_sm, verify_kernel<false>, kVThreads, 0)) !=
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&d.verify_blocks_per_sm, verify_kernel<false, true>, kVThreads, 0)) !=
         cudaSuccess)
       return cuda_fail(e, "occupancy query");
     if (d.verify_blocks_per_sm < 1) d.verify_blocks_per_sm = 1;
@@ -1365,7 +1368,8 @@ static as_status launch_verify(DeviceState* d, const as_table* t, const uint8_t*
   uint64_t blocks = (n + kVThreads - 1) / kVThreads;
   const uint64_t lim = (uint64_t)d->sms * (uint64_t)d->verify_blocks_per_sm;
   if (blocks > lim) blocks = lim;
-  verify_kernel<false><<<(unsigned)blocks, kVThreads, 0, s>>>(P);
+  if (mode == AS_JOIN_INNER) verify_kernel<false, true><<<(unsigned)blocks, kVThreads, 0, s>>>(P);
+  else verify_kernel<false, false><<<(unsigned)blocks, kVThreads, 0, s>>>(P);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "probe kernel launch");
   return AS_OK;
