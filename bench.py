@@ -875,7 +875,7 @@ def run_gpu(args):
 
 
 # revision of each kernel's code; profiles/traffic.json holds counters per revision
-KERNEL_REVS = {"sig_key_kernel": "v2", "build_kernel": "v8", "verify_kernel": "v16"}
+KERNEL_REVS = {"sig_key_kernel": "v3", "build_kernel": "v8", "verify_kernel": "v17"}
 KERNEL_NAMES = {"sig_R": "sig_key_kernel", "sig_S": "sig_key_kernel", "build": "build_kernel",
                 "verify": "verify_kernel"}
 
