@@ -531,26 +531,43 @@ def run_gpu(args):
     if total_pairs != expected:
         raise SystemExit(f"pair count {total_pairs} != expected {expected}")
 
+    # the whole join as one library call (as_join: S's signatures on a side stream overlap R's
+    # signatures and the build), the timed step of the headline value
+    jws = ag.alloc_ws(ag.join_ws_bytes(m, n, lf))
+    jcount = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def whole_join():
+        ag.join_into(dR, dS, jws, pairs, jcount, lf, sync=False, stream=stream)
+    whole_join()
+    torch.cuda.synchronize()
+    if int(jcount.item()) != expected:
+        raise SystemExit(f"whole join: pair count {int(jcount.item())} != expected {expected}")
+
     for _ in range(args.warmup):
         step()
+        whole_join()
     barrier()
     clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
-    t0 = torch.cuda.Event(enable_timing=True)
-    t1 = torch.cuda.Event(enable_timing=True)
     barrier()
-    t0.record(stream)
+    # K whole joins (the headline), each bracketed by CUDA events, L2 flushed between them ...
+    wev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    for k in range(args.steps):
+        wev[k][0].record(stream)
+        whole_join()
+        wev[k][1].record(stream)
+        flush_l2(stream)                                # between steps, outside the steps' events
+    # ... then K joins as the four calls, with events between the kernels (the per-kernel split)
     for k in range(args.steps):
         step(ev[k])
-        flush_l2(stream)                                # between steps, outside the steps' events
-    t1.record(stream)
+        flush_l2(stream)
     barrier()
+    torch.cuda.synchronize()
     clk = clocks.stop()
-    total_ms = t0.elapsed_time(t1)
     phase_ms = {ph: [e[i].elapsed_time(e[i + 1]) for e in ev] for i, ph in enumerate(PH)}
-    step_ms = [e[0].elapsed_time(e[len(PH)]) for e in ev]
-    total_ms = ranks_max(total_ms)
+    split_ms = [e[0].elapsed_time(e[len(PH)]) for e in ev]
+    step_ms = [a.elapsed_time(b) for a, b in wev]
     ms_per_step = ranks_max(sum(step_ms)) / args.steps   # the K steps' own event time, flushes excluded
     value = replica_value(n, world, ms_per_step)
 
@@ -826,6 +843,7 @@ def run_gpu(args):
                          f"steps' own CUDA-event time, flushes excluded; inputs {key_bytes / 1e9:.2f} GB of keys",
                    "parallelism": f"replicas{world}"},
         "p50_ms": pct(step_ms, 50), "p99_ms": pct(step_ms, 99),
+        "split_step_ms": statistics.mean(split_ms),
         "probe_tuples_per_s_probe_phase": n / ((kernels["sig_S"]["ms"] + kernels["verify"]["ms"]) * 1e-3),
         "key_gbps": key_bytes / (ms_per_step * 1e-3) / 1e9,
         "kernels": kernels,

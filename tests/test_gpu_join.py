@@ -332,3 +332,44 @@ def test_output_buffers_never_written_past_their_capacity(cuda):
 def _pack(keys):
     rel = workloads.relation_from_keys(keys)
     return rel.arena, rel.off, rel.ids
+
+
+@pytest.mark.parametrize("which", ["signature", "fullstring"])
+def test_whole_join_on_a_stream_and_in_a_cuda_graph(cuda, which):
+    """as_join and as_baseline_join fork S's signatures (hashes) onto a side
+    stream and join it back: on a non-default stream, back to back without a
+    synchronisation, and captured in a CUDA graph and replayed, every run
+    gives the oracle's pairs."""
+    ag = cuda
+    wl = workloads.generate(workloads.CONFIGS["large"].scaled(3_000, 30_000))
+    R = ag.DeviceRelation.from_host(wl.R.arena, wl.R.off, wl.R.ids)
+    S = ag.DeviceRelation.from_host(wl.S.arena, wl.S.off, wl.S.ids)
+    want = oracle.join_simple(wl.R, wl.S)
+    cap = len(want) + 1024
+    stream = torch.cuda.Stream()
+    if which == "signature":
+        ws = ag.alloc_ws(ag.join_ws_bytes(R.n, S.n, 0.5))
+        run = lambda pairs, count: ag.join_into(R, S, ws, pairs, count, 0.5, sync=False, stream=stream)
+    else:
+        ws = ag.alloc_ws(ag.baseline_ws_bytes(R.n, S.n, 0.5))
+        run = lambda pairs, count: ag.baseline_join_into(R, S, ws, pairs, count, 0.5, tagged=True, sync=False,
+                                                         stream=stream)
+    pairs = torch.empty(2 * cap, dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            run(pairs, count)
+    stream.synchronize()
+    n = int(count.item())
+    assert np.array_equal(oracle.sort_pairs(pairs[: 2 * n].cpu().numpy().view(np.uint32)), want)
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        run(pairs, count)
+    for _ in range(2):
+        pairs.zero_()
+        count.zero_()
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        n = int(count.item())
+        assert np.array_equal(oracle.sort_pairs(pairs[: 2 * n].cpu().numpy().view(np.uint32)), want)
