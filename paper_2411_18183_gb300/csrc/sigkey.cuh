@@ -73,8 +73,8 @@ constexpr uint32_t kLKNoKey = 0xFFFFFFFFu;            // empty sorting entry
 // search in the offsets); smaller ones by key count, which saves the search's
 // dependent loads where they would be a large share of the kernel's time
 constexpr uint64_t kLKSearchFrom = 1ull << 19;
-constexpr int kLKIdxBits = kLKWin == 256 ? 8 : (kLKWin == 512 ? 9 : (kLKWin == 128 ? 7 : 10));
-static_assert((1 << kLKIdxBits) == kLKWin, "window sizes 128, 256, 512, 1024");
+constexpr int kLKIdxBits = kLKWin == 256 ? 8 : (kLKWin == 128 ? 7 : (kLKWin == 64 ? 6 : 10));
+static_assert((1 << kLKIdxBits) == kLKWin, "window sizes 64, 128, 256");
 constexpr uint32_t kLKNbCap = (1u << (31 - kLKIdxBits)) - 1u;   // block counts above sort together
 
 struct LKWarp {
@@ -82,7 +82,7 @@ struct LKWarp {
   uint32_t order[kLKWin];          // window entries by block count: (block count << 8 | index)
   uint32_t hist[256];              // the counting sort's bins (block counts, 255 and up in the last)
 };
-static_assert(kLKWin == 256, "the window sort: 8 entries and 8 bins per lane");
+static_assert(kLKWin >= 64 && kLKWin <= 256, "the window sort: up to 8 entries and 8 bins per lane");
 constexpr size_t kSmemLKMasks = 1056;                 // 33 rows of 32 bytes
 // (the blocks in flight of a shape live in registers: its depth takes no shared memory)
 constexpr size_t lk_smem_bytes(int warps, int /*depth*/) {
@@ -237,9 +237,10 @@ __device__ __forceinline__ void lk_sort_window(LKWarp& W, uint32_t wn, uintptr_t
 #pragma unroll
   for (int t = 0; t < 8; ++t) W.hist[8 * lane + t] = 0u;
   __syncwarp();
-  uint32_t e[8], bin[8], rank[8];
+  constexpr int kPer = kLKWin / 32;                   // entries per lane
+  uint32_t e[kPer], bin[kPer], rank[kPer];
 #pragma unroll
-  for (int j = 0; j < 8; ++j) {
+  for (int j = 0; j < kPer; ++j) {
     const uint32_t i = lane + 32u * (uint32_t)j;
     e[j] = kLKNoKey;
     bin[j] = 0;
@@ -275,7 +276,7 @@ __device__ __forceinline__ void lk_sort_window(LKWarp& W, uint32_t wn, uintptr_t
   }
   __syncwarp();
 #pragma unroll
-  for (int j = 0; j < 8; ++j)
+  for (int j = 0; j < kPer; ++j)
     if (e[j] != kLKNoKey) W.order[W.hist[bin[j]] + rank[j]] = e[j];
   for (uint32_t i = wn + lane; i < (uint32_t)kLKWin; i += 32) W.order[i] = kLKNoKey;
   __syncwarp();
