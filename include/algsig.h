@@ -44,11 +44,12 @@
  * Streams: every call is asynchronous on the given stream (a cudaStream_t
  * passed as void*, NULL = legacy default stream) unless it is given a host
  * pointer to return a count, in which case it synchronises that stream.
- * as_join, as_join_batch_run and as_baseline_join run S's signatures (or
- * hashes) on a side stream of the library (four per device, created with the
- * tables) forked from the given stream and joined back into it before the
- * probe, so that they overlap R's signatures and the build; the calls stay
- * asynchronous on the given stream and can be captured in a CUDA graph.
+ * as_join (below 2^20 S keys), as_join_batch_run and as_baseline_join run
+ * S's signatures (or hashes) on a side stream of the library (four per
+ * device, created with the tables) forked from the given stream and joined
+ * back into it before the probe, so that they overlap R's signatures and the
+ * build; the calls stay asynchronous on the given stream and can be captured
+ * in a CUDA graph.
  *
  * Errors: every call returns an as_status; AS_OK is 0.  as_last_error()
  * gives a human-readable message for the calling thread's last failure.  No
@@ -326,7 +327,10 @@ size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor);
  * signatures of R, build, probe with S (signatures, verification, compaction).
  * Arguments as for as_join_build and as_join_probe; d_ws must hold
  * as_join_ws_bytes(m, load_factor) bytes.  d_count may be NULL (the counter
- * then lives in the workspace).
+ * then lives in the workspace).  From 2^20 S keys, S's signatures and the
+ * probe run as one kernel (each group of keys is probed and verified right
+ * after its signatures); below that, S's signatures overlap R's on a side
+ * stream.  The result is the same either way.
  */
 as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
                   const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,

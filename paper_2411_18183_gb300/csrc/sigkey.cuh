@@ -85,8 +85,8 @@ struct LKWarp {
 static_assert(kLKWin >= 64 && kLKWin <= 256, "the window sort: up to 8 entries and 8 bins per lane");
 constexpr size_t kSmemLKMasks = 1056;                 // 33 rows of 32 bytes
 // (the blocks in flight of a shape live in registers: its depth takes no shared memory)
-constexpr size_t lk_smem_bytes(int warps, int /*depth*/) {
-  return (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)warps * sizeof(LKWarp);
+constexpr size_t lk_smem_bytes(int warps, int /*depth*/, size_t scratch_per_warp = 0) {
+  return (size_t)kRedBytes + 1024 + kSmemLKMasks + (size_t)warps * (sizeof(LKWarp) + scratch_per_warp);
 }
 static_assert(lk_smem_bytes(32, 1) <= 232448, "lane-per-key signature kernel: shared memory");
 
@@ -382,7 +382,7 @@ __device__ ALGSIG_LK_FINISH uint64_t lk_finish(const uint32_t (&c)[16], const ui
 // At most a few keys per relation take this path.
 // (one copy per kernel instantiation: ptxas fails on a non-inlined function
 // shared by kernels of different shapes)
-template <int NCOMP, int kLKWarps, int kLKDepth, bool BATCH, class Cursor>
+template <int NCOMP, int kLKWarps, int kLKDepth, bool BATCH, class Unique, class Cursor>
 __device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_lo, const uint8_t* lim_hi,
                                              const uint16_t* inv32, const uint4* mt, const Cursor& rc) {
   const uint32_t sh = 8u * (k.a & 1u);
@@ -409,8 +409,8 @@ __device__ __noinline__ uint64_t lk_edge_key(const LKKey& k, const uint8_t* lim_
 // its block 0 in the group's last iteration.  An odd key whose last aligned
 // block ends with a key byte needs the next block's first byte.  Keys with a
 // block outside the arena's readable range are computed apart (lk_edge_key).
-template <int NCOMP, int kLKWarps, int kLKDepth, bool BATCH, class Cursor>
-__device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8_t* lim_lo, const uint8_t* lim_hi,
+template <int NCOMP, int kLKWarps, int kLKDepth, bool BATCH, class Unique, class Cursor>
+__device__ __forceinline__ uint64_t lk_group(const LKKey& k, uint32_t G, const uint8_t* lim_lo, const uint8_t* lim_hi,
                                          const uint16_t* inv32, const uint4* mt, uint64_t* __restrict__ sig_out,
                                          const Cursor& rc) {
   const uint32_t nb = k.edge ? 0u : k.nb;
@@ -465,10 +465,22 @@ __device__ __forceinline__ void lk_group(const LKKey& k, uint32_t G, const uint8
       lk_block<NCOMP>(w, sh, nxt0, c, c3, rc);
     }
   }
-  if (k.valid && !k.edge) sig_out[k.kq] = lk_finish<NCOMP>(c, c3, k.a, inv32, rc);
+  uint64_t sig = 0;
+  if (k.valid && !k.edge) sig_out[k.kq] = sig = lk_finish<NCOMP>(c, c3, k.a, inv32, rc);
   if (__any_sync(kFull, k.edge))
-    if (k.edge) sig_out[k.kq] = lk_edge_key<NCOMP, kLKWarps, kLKDepth, BATCH>(k, lim_lo, lim_hi, inv32, mt, rc);
+    if (k.edge) sig_out[k.kq] = sig = lk_edge_key<NCOMP, kLKWarps, kLKDepth, BATCH, Unique>(k, lim_lo, lim_hi, inv32, mt, rc);
+  return sig;
 }
+
+// What a kernel does with each group's signatures besides writing them out:
+// nothing (LKNoPost), or a probe of a hash table (the whole join's fused
+// pass).  kScratch: shared-memory bytes a warp needs for it.
+struct LKNoPost {
+  static constexpr size_t kScratch = 0;
+  __device__ __forceinline__ void init(uint8_t*, const uint4*) {}
+  __device__ __forceinline__ void group(uint64_t, uint64_t, bool) {}
+  __device__ __forceinline__ void finish() {}
+};
 
 // The window of keys starting at key wb (keys below k_hi): returns its key
 // count and sets *wa to its first row in the relation.  In a batch the keys are
@@ -523,16 +535,19 @@ __device__ __forceinline__ void lk_warp_range(const BatchJoin* __restrict__ J, i
 // The signatures of n keys: the rows of a relation (BATCH false), or the
 // virtual rows of one side of a batch (BATCH true; s_side picks S, J and nj
 // describe the joins, and sig_out is indexed by virtual row).
-template <bool AT400, int NCOMP, int kLKWarps, int kLKDepth, bool BATCH>
+template <bool AT400, int NCOMP, int kLKWarps, int kLKDepth, bool BATCH, class Post = LKNoPost>
 __global__ void __launch_bounds__(32 * kLKWarps, 1) sig_key_kernel(const uint8_t* __restrict__ arena,
                                                                 const uint64_t* __restrict__ off, uint64_t n,
                                                                 uint64_t* __restrict__ sig_out,
-                                                                const BatchJoin* __restrict__ J, int nj, int s_side) {
+                                                                const BatchJoin* __restrict__ J, int nj, int s_side,
+                                                                Post post = Post()) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* red = reinterpret_cast<uint32_t*>(smem);
   uint16_t* inv32 = reinterpret_cast<uint16_t*>(smem + kRedBytes);
   uint4* mt = reinterpret_cast<uint4*>(smem + kRedBytes + 1024);
   LKWarp* warps = reinterpret_cast<LKWarp*>(smem + kRedBytes + 1024 + kSmemLKMasks);
+  post.init(smem + kRedBytes + 1024 + kSmemLKMasks + kLKWarps * sizeof(LKWarp) + (threadIdx.x >> 5) * Post::kScratch,
+            reinterpret_cast<const uint4*>(smem + kRedBytes + 1024));
   lk_fill_masks(mt);
   for (int i = threadIdx.x; i < 256; i += blockDim.x)   // the x^-32 multiply table (512 entries)
     reinterpret_cast<uint32_t*>(inv32)[i] = reinterpret_cast<const uint32_t*>(g_const + 16 * 512)[i];
@@ -576,10 +591,12 @@ __global__ void __launch_bounds__(32 * kLKWarps, 1) sig_key_kernel(const uint8_t
           lk_prefetch_window(W, off, na, na + nn);
         }
       }
-      lk_group<NCOMP, kLKWarps, kLKDepth, BATCH>(k, G, lim_lo, lim_hi, inv32, mt, sig_out, rc);
+      const uint64_t sig = lk_group<NCOMP, kLKWarps, kLKDepth, BATCH, Post>(k, G, lim_lo, lim_hi, inv32, mt, sig_out, rc);
+      post.group(k.kq, sig, k.valid);
     }
     wb += wn;
   }
+  post.finish();
   cp_async_wait_all();
 }
 

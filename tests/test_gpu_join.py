@@ -1,5 +1,6 @@
 """GPU signature join (as_join / as_join_build / as_join_probe through the C
 ABI) against the CPU oracle: sorted (r_id, s_id) pairs, bit-exact."""
+import dataclasses
 import random
 
 import numpy as np
@@ -373,3 +374,27 @@ def test_whole_join_on_a_stream_and_in_a_cuda_graph(cuda, which):
         torch.cuda.synchronize()
         n = int(count.item())
         assert np.array_equal(oracle.sort_pairs(pairs[: 2 * n].cpu().numpy().view(np.uint32)), want)
+
+
+def test_whole_join_fused_pass_matches_oracle(cuda):
+    """From 2^20 S keys as_join probes each group of S keys inside the signature
+    kernel; with edge keys at both ends of the arena, duplicates and ids, its
+    pairs and signatures equal the oracle's (and those of the separate calls)."""
+    ag = cuda
+    spec = dataclasses.replace(workloads.CONFIGS["large"], m=20_000, n=(1 << 20) + 777, r_len=(1, 300),
+                               s_len=(1, 300))
+    wl = workloads.generate(spec)
+    ids_r = (np.arange(wl.R.n, dtype=np.uint32) * 7 + 3).astype(np.uint32)
+    ids_s = (np.arange(wl.S.n, dtype=np.uint32) * 5 + 1).astype(np.uint32)
+    R = ag.DeviceRelation.from_host(wl.R.arena, wl.R.off, ids_r)
+    S = ag.DeviceRelation.from_host(wl.S.arena, wl.S.off, ids_s)
+    from workloads import Relation
+    # (keys of one or two bytes also join by chance, so the oracle, not the generator, gives the count)
+    want = oracle.join_grace(Relation(wl.R.arena, wl.R.off, ids_r), Relation(wl.S.arena, wl.S.off, ids_s), nthreads=8)
+    ws = ag.alloc_ws(ag.join_ws_bytes(R.n, S.n, 0.5))
+    pairs = torch.empty(2 * (len(want) + 4096), dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    st, cnt = ag.join_into(R, S, ws, pairs, count, 0.5, sync=True)
+    assert cnt == len(want)
+    got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
+    assert np.array_equal(got, want)
