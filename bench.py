@@ -512,6 +512,7 @@ def run_gpu(args):
             ag.join_probe_sigs(t, dS, sigS, pairs, count, sync=False, stream=stream)
             if evs:
                 evs[4].record(stream)
+            return t
         return step, ws, tb, count
 
     # the table's load factor: given, or the fastest of a few, each timed over two
@@ -558,9 +559,17 @@ def run_gpu(args):
         whole_join()
         wev[k][1].record(stream)
         flush_l2(stream)                                # between steps, outside the steps' events
-    # ... then K joins as the four calls, with events between the kernels (the per-kernel split)
+    # ... then K joins as the four calls, with events between the kernels (the per-kernel split),
+    # each followed (after an L2 flush) by the probe of the same table as one call, whose kernel
+    # computes S's signatures and probes in one pass (the whole join's pass over S)
+    fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    fcount = torch.zeros(1, dtype=torch.int64, device="cuda")
     for k in range(args.steps):
-        step(ev[k])
+        t_k = step(ev[k])
+        flush_l2(stream)
+        fev[k][0].record(stream)
+        ag.join_probe(t_k, dS, pairs, fcount, sigS_out=sigS, sync=False, stream=stream)
+        fev[k][1].record(stream)
         flush_l2(stream)
     barrier()
     torch.cuda.synchronize()
@@ -807,12 +816,19 @@ def run_gpu(args):
                    + total_pairs * (16 + 4 + 8)                        # offR pair, idR, output pair
                    + 2 * verified_bytes),                              # R and S key bytes compared
     }
+    fused = n >= FUSED_PROBE_FROM                       # the whole join's S pass is one kernel
+    phases = PH
+    if fused:                                          # its time from the probe calls after the split steps
+        phase_ms["sig_probe_S"] = [a.elapsed_time(b) for a, b in fev]
+        alg["sig_probe_S"] = alg["sig_S"] + alg["verify"]
+        phases = PH + ("sig_probe_S",)
     kernels = {}
-    for ph in PH:
+    for ph in phases:
         avg = statistics.mean(phase_ms[ph])
         kernels[ph] = {"ms": avg, "algorithmic_bytes": alg[ph], "gbps": alg[ph] / (avg * 1e-3) / 1e9,
                        "frac_hbm": alg[ph] / (avg * 1e-3) / 1e9 / hbm}
-    dom = max(("sig_S", "verify"), key=lambda ph: kernels[ph]["ms"])
+    # the dominant kernel of the timed step: the fused S pass, or the larger of the S signatures and the probe
+    dom = "sig_probe_S" if fused else max(("sig_S", "verify"), key=lambda ph: kernels[ph]["ms"])
     traffic = None
     tp = os.path.join(ROOT, "profiles", "traffic.json")
     if os.path.exists(tp):
@@ -820,7 +836,7 @@ def run_gpu(args):
             d = json.load(f)
         ent = d.get(KERNEL_NAMES[dom], {})
         if ent.get("kernel_rev") == KERNEL_REVS[KERNEL_NAMES[dom]] and ent.get("per_byte_of_keys"):
-            keyb = wl.S.nbytes if dom == "sig_S" else 2 * verified_bytes
+            keyb = wl.S.nbytes if dom in ("sig_S", "sig_probe_S") else 2 * verified_bytes
             traffic = ent["per_byte_of_keys"] * keyb
 
     extra = {}
@@ -865,21 +881,21 @@ def run_gpu(args):
                 "h2d_pinned_gbs": h2d_gbs,
                 "copy_bound_ms": (h2d + d2h) / (h2d_gbs * 1e9) * 1e3,
                 "path": "stream.HostStreamJoin: pinned host R and S, S copied in chunks under the kernels"},
-        "gpu_launches": 4 * args.steps,
+        "gpu_launches": (3 if fused else 4) * args.steps,
         "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": kernels[dom]["gbps"], "peak": hbm,
                      "peak_kind": f"{peak_kind} (copy bandwidth, burst)", "unit": "GB/s",
                      "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
                      "algorithmic_bytes": alg[dom],
                      "kernels": {ph: {"kernel": KERNEL_NAMES[ph], "ms": round(kernels[ph]["ms"], 4),
                                       "achieved": round(kernels[ph]["gbps"], 1),
-                                      "frac": round(kernels[ph]["frac_hbm"], 4)} for ph in PH}},
+                                      "frac": round(kernels[ph]["frac_hbm"], 4)} for ph in phases}},
         "cpu_baseline": cpu,
         "gen_s": t_gen,
         **extra,
     }
     # a compact summary at the end of the line (where a truncated tail still shows it)
     summ = {"step_ms": round(ms_per_step, 4),
-            "kernel_frac_hbm": {ph: round(kernels[ph]["frac_hbm"], 3) for ph in PH},
+            "kernel_frac_hbm": {ph: round(kernels[ph]["frac_hbm"], 3) for ph in phases},
             "speedup_vs_fullstring": {k: round(v, 3) for k, v in line["speedup_vs_fullstring"].items()},
             "e2e_ms": round(e2e_s * 1e3, 2), "h2d_pinned_gbs": round(h2d_gbs, 1)}
     if "length_sweep" in extra:
@@ -894,9 +910,10 @@ def run_gpu(args):
 
 
 # revision of each kernel's code; profiles/traffic.json holds counters per revision
-KERNEL_REVS = {"sig_key_kernel": "v3", "build_kernel": "v8", "verify_kernel": "v17"}
+KERNEL_REVS = {"sig_key_kernel": "v3", "build_kernel": "v8", "verify_kernel": "v17", "sig_key_kernel+probe": "v1"}
 KERNEL_NAMES = {"sig_R": "sig_key_kernel", "sig_S": "sig_key_kernel", "build": "build_kernel",
-                "verify": "verify_kernel"}
+                "verify": "verify_kernel", "sig_probe_S": "sig_key_kernel+probe"}
+FUSED_PROBE_FROM = 1 << 20    # S keys from which the library's probe computes signatures and probes in one kernel
 
 
 def main():

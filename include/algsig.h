@@ -231,7 +231,9 @@ size_t as_join_probe_ws_bytes(uint64_t n);
  * S's signatures are computed first (as by as_sig_compute); then every S key
  * walks its bucket sequence until an empty slot; a slot is a candidate when
  * its signature and key length equal the S key's, and a candidate is emitted
- * only if the R key's bytes equal the S key's bytes.
+ * only if the R key's bytes equal the S key's bytes.  From 2^20 S keys the
+ * two steps run as one kernel (each group of 32 keys is probed and verified
+ * right after its signatures), with the same result.
  *   t              : table from as_join_build (host struct)
  *   d_arenaS, d_offS, d_idS, n : relation S
  *   d_sigS_out     : uint64[n] device buffer to receive S's signatures, or NULL
@@ -327,10 +329,10 @@ size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor);
  * signatures of R, build, probe with S (signatures, verification, compaction).
  * Arguments as for as_join_build and as_join_probe; d_ws must hold
  * as_join_ws_bytes(m, load_factor) bytes.  d_count may be NULL (the counter
- * then lives in the workspace).  From 2^20 S keys, S's signatures and the
- * probe run as one kernel (each group of keys is probed and verified right
- * after its signatures); below that, S's signatures overlap R's on a side
- * stream.  The result is the same either way.
+ * then lives in the workspace).  From 2^20 S keys it is as_join_build then
+ * as_join_probe (whose signatures and probe then run as one kernel); below
+ * that, S's signatures overlap R's on a side stream.  The result is the same
+ * either way.
  */
 as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
                   const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,

@@ -1582,7 +1582,10 @@ static as_status probe_impl(const char* fn, const as_table* t, const uint8_t* d_
   cudaStream_t s = (cudaStream_t)stream;
   cudaError_t e;
   if ((e = cudaMemsetAsync(d_count, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
-  if (n > 0) {
+  if (n >= kFusedProbeFrom) {                      // signatures and probe in one kernel
+    st = launch_sig_probe(d, t, d_arenaS, d_offS, d_idS, n, sigS, d_pairs, cap_pairs, d_count, s);
+    if (st != AS_OK) return st;
+  } else if (n > 0) {
     st = launch_sig(d_arenaS, d_offS, n, sigS, s);
     if (st != AS_OK) return st;
     st = launch_verify(d, t, d_arenaS, d_offS, d_idS, n, sigS, d_pairs, cap_pairs, d_count, s);
@@ -1680,12 +1683,8 @@ as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_
     // reads the S keys while they may still sit in L2)
     if ((st = as_join_build(d_ws, tb, d_arenaR, d_offR, d_idR, m, nullptr, load_factor, &t, stream)) != AS_OK)
       return st;
-    if ((st = probe_args("as_join", &t, d_arenaS, d_offS, n, d_pairs, cap_pairs, cnt)) != AS_OK) return st;
-    cudaError_t e;
-    if ((e = cudaMemsetAsync(cnt, 0, 8, s)) != cudaSuccess) return cuda_fail(e, "counter clear");
-    if ((st = launch_sig_probe(d, &t, d_arenaS, d_offS, d_idS, n, sigS, d_pairs, cap_pairs, cnt, s)) != AS_OK)
-      return st;
-    return finish_probe("as_join", &t, cap_pairs, cnt, h_count, s);
+    return probe_impl("as_join", &t, d_arenaS, d_offS, d_idS, n, sigS, nullptr, 0, d_pairs, cap_pairs, cnt, h_count,
+                      stream);
   }
   // smaller S: its signatures on a side stream, concurrently with R's signatures and the build
   // (kernels of small relations leave SMs idle), then the probe
