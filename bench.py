@@ -913,7 +913,7 @@ def run_gpu(args):
 KERNEL_REVS = {"sig_key_kernel": "v3", "build_kernel": "v8", "verify_kernel": "v17", "sig_key_kernel+probe": "v1"}
 KERNEL_NAMES = {"sig_R": "sig_key_kernel", "sig_S": "sig_key_kernel", "build": "build_kernel",
                 "verify": "verify_kernel", "sig_probe_S": "sig_key_kernel+probe"}
-FUSED_PROBE_FROM = 1 << 20    # S keys from which the library's probe computes signatures and probes in one kernel
+FUSED_PROBE_FROM = 1 << 19    # S keys from which the library's probe computes signatures and probes in one kernel
 
 
 def main():

@@ -44,7 +44,7 @@
  * Streams: every call is asynchronous on the given stream (a cudaStream_t
  * passed as void*, NULL = legacy default stream) unless it is given a host
  * pointer to return a count, in which case it synchronises that stream.
- * as_join (below 2^20 S keys), as_join_batch_run and as_baseline_join run
+ * as_join (below 2^19 S keys), as_join_batch_run and as_baseline_join run
  * S's signatures (or hashes) on a side stream of the library (four per
  * device, created with the tables) forked from the given stream and joined
  * back into it before the probe, so that they overlap R's signatures and the
@@ -231,7 +231,7 @@ size_t as_join_probe_ws_bytes(uint64_t n);
  * S's signatures are computed first (as by as_sig_compute); then every S key
  * walks its bucket sequence until an empty slot; a slot is a candidate when
  * its signature and key length equal the S key's, and a candidate is emitted
- * only if the R key's bytes equal the S key's bytes.  From 2^20 S keys the
+ * only if the R key's bytes equal the S key's bytes.  From 2^19 S keys the
  * two steps run as one kernel (each group of 32 keys is probed and verified
  * right after its signatures), with the same result.
  *   t              : table from as_join_build (host struct)
@@ -329,7 +329,7 @@ size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor);
  * signatures of R, build, probe with S (signatures, verification, compaction).
  * Arguments as for as_join_build and as_join_probe; d_ws must hold
  * as_join_ws_bytes(m, load_factor) bytes.  d_count may be NULL (the counter
- * then lives in the workspace).  From 2^20 S keys it is as_join_build then
+ * then lives in the workspace).  From 2^19 S keys it is as_join_build then
  * as_join_probe (whose signatures and probe then run as one kernel); below
  * that, S's signatures overlap R's on a side stream.  The result is the same
  * either way.

@@ -1193,9 +1193,10 @@ static as_status launch_sig_batch(const DeviceState* d, const uint8_t* arena, co
   return AS_OK;
 }
 
-// S relations from this many keys take the fused pass in as_join (measured: 1-4 %
-// faster from 1M keys, slower for 100k keys, where the side-stream overlap wins)
-constexpr uint64_t kFusedProbeFrom = 1ull << 20;
+// S relations from this many keys take the fused pass in as_join_probe and as_join
+// (measured: 1.5-4 % faster at 1M to 10M keys; for 100k keys as_join's side-stream
+// overlap wins)
+constexpr uint64_t kFusedProbeFrom = 1ull << 19;
 
 // The whole join's pass over S: the signature kernel (shape 0) with the probe
 // of table t fused in (ProbePost; plain inner join).

@@ -377,7 +377,7 @@ def test_whole_join_on_a_stream_and_in_a_cuda_graph(cuda, which):
 
 
 def test_whole_join_fused_pass_matches_oracle(cuda):
-    """From 2^20 S keys as_join probes each group of S keys inside the signature
+    """From 2^19 S keys as_join probes each group of S keys inside the signature
     kernel; with edge keys at both ends of the arena, duplicates and ids, its
     pairs and signatures equal the oracle's (and those of the separate calls)."""
     ag = cuda
