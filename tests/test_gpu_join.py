@@ -398,3 +398,55 @@ def test_whole_join_fused_pass_matches_oracle(cuda):
     assert cnt == len(want)
     got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
     assert np.array_equal(got, want)
+
+
+def _pair_keys(p):
+    p = np.asarray(p, dtype=np.uint32).reshape(-1, 2)
+    return (p[:, 0].astype(np.uint64) << np.uint64(32)) | p[:, 1].astype(np.uint64)
+
+
+def test_fused_pass_capacity_and_split_probe(cuda):
+    """The fused signature-and-probe pass (from 2^19 S keys) when the pair
+    buffer is too small, through as_join and through as_join_build +
+    as_join_probe: the exact count with AS_ERR_CAPACITY below it, canary words
+    after the buffer untouched, every pair written distinct and one of the
+    oracle's (all of them at the exact capacity), and the S signatures that
+    as_join_probe returns equal to the oracle's."""
+    ag = cuda
+    CANARY = 0x5A5A5A5A
+    wl = workloads.generate(workloads.CONFIGS["plain"].scaled(20_000, (1 << 19) + 100))
+    R, S = dev(ag, wl.R), dev(ag, wl.S)
+    want = oracle.join_grace(wl.R, wl.S, nthreads=8)
+    exact = len(want)
+    assert exact == wl.expected_pairs()
+    wantk = _pair_keys(want)
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+
+    def check_buffer(buf, cap, st, cnt):
+        assert cnt == exact and st == (ag.AS_OK if cap >= exact else ag.AS_ERR_CAPACITY), cap
+        assert bool((buf[2 * cap:] == CANARY).all()), cap
+        got = _pair_keys(buf[: 2 * min(cap, exact)].cpu().numpy().view(np.uint32))
+        assert np.unique(got).size == got.size and np.isin(got, wantk).all(), cap
+        if cap >= exact:
+            assert np.array_equal(np.sort(got), np.sort(wantk))
+
+    ws = ag.alloc_ws(ag.join_ws_bytes(R.n, S.n, 0.5))
+    for cap in (0, 1, 4099, exact - 1, exact):
+        buf = torch.full((2 * cap + 64,), CANARY, dtype=torch.int32, device="cuda")
+        st, cnt = ag.join_into(R, S, ws, buf[: 2 * cap], count, 0.5, sync=True, allow_capacity=True)
+        check_buffer(buf, cap, st, cnt)
+
+    tws = ag.alloc_ws(ag.join_table_bytes(R.n, 0.5))
+    t = ag.join_build(R, tws, 0.5)
+    sigS = torch.zeros(S.n, dtype=torch.int64, device="cuda")
+    for cap in (4099, exact):
+        buf = torch.full((2 * cap + 64,), CANARY, dtype=torch.int32, device="cuda")
+        try:
+            st, cnt = ag.AS_OK, ag.join_probe(t, S, buf[: 2 * cap], count, sigS_out=sigS)
+        except ag.AlgsigError as e:
+            st, cnt = e.status, int(count.item())
+        check_buffer(buf, cap, st, cnt)
+    assert np.array_equal(sigS.cpu().numpy().view(np.uint64), oracle.sig_batch(wl.S.arena, wl.S.off, nthreads=8))
+    buf = torch.full((2 * exact + 64,), CANARY, dtype=torch.int32, device="cuda")   # S's signatures in a workspace
+    cnt = ag.join_probe(t, S, buf[: 2 * exact], count, ws=ag.alloc_ws(ag.join_probe_ws_bytes(S.n)))
+    check_buffer(buf, exact, ag.AS_OK, cnt)
