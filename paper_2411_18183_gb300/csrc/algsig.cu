@@ -94,14 +94,19 @@ __device__ __forceinline__ int join_of_virtual(const BatchJoin* __restrict__ J, 
   return ans;
 }
 
-// join whose virtual byte range holds byte `t` (last j with vb_j <= t)
+// Work of a side's virtual rows up to join j's first: its key bytes + c per row
 template <bool S_SIDE>
-__device__ __forceinline__ int join_of_vbyte(const BatchJoin* __restrict__ J, int nj, uint64_t t) {
+__device__ __forceinline__ uint64_t vcost_of_join(const BatchJoin* __restrict__ J, int j, uint64_t c) {
+  return S_SIDE ? __ldg(&J[j].vbs) + c * __ldg(&J[j].vs) : __ldg(&J[j].vbr) + c * __ldg(&J[j].vr);
+}
+
+// join whose share of the work holds the point `t` (last j with vcost_j <= t)
+template <bool S_SIDE>
+__device__ __forceinline__ int join_of_vcost(const BatchJoin* __restrict__ J, int nj, uint64_t t, uint64_t c) {
   int lo = 0, hi = nj - 1, ans = 0;
   while (lo <= hi) {
     const int mid = (lo + hi) >> 1;
-    const uint64_t b = S_SIDE ? __ldg(&J[mid].vbs) : __ldg(&J[mid].vbr);
-    if (b <= t) { ans = mid; lo = mid + 1; } else { hi = mid - 1; }
+    if (vcost_of_join<S_SIDE>(J, mid, c) <= t) { ans = mid; lo = mid + 1; } else { hi = mid - 1; }
   }
   return ans;
 }
@@ -154,15 +159,15 @@ __global__ void batch_bytes_kernel(BatchJoin* J, int nj, const uint64_t* __restr
 // Signature kernel
 // ----------------------------------------------------------------------------
 
-// first actual key of join j whose start lies at or after virtual byte t
-// (t inside join j's byte range), as a virtual row
+// first actual key of join j whose share of the work (key bytes + c per key)
+// starts at or after the point t (t inside join j's share), as a virtual row
 template <bool S_SIDE>
-__device__ __forceinline__ uint64_t vcut_in_join(const BatchJoin* J, const uint64_t* off, int j, uint64_t t) {
+__device__ __forceinline__ uint64_t vcut_in_join(const BatchJoin* J, const uint64_t* off, int j, uint64_t t,
+                                                 uint64_t c) {
   const uint64_t b = S_SIDE ? __ldg(&J[j].s_begin) : __ldg(&J[j].r_begin);
   const uint64_t e = S_SIDE ? __ldg(&J[j].s_end) : __ldg(&J[j].r_end);
-  const uint64_t vb = S_SIDE ? __ldg(&J[j].vbs) : __ldg(&J[j].vbr);
   const uint64_t v0 = S_SIDE ? __ldg(&J[j].vs) : __ldg(&J[j].vr);
-  const uint64_t k = b + warp_lower_bound(off + b, e - b, off[b] + (t - vb));
+  const uint64_t k = b + warp_lower_bound(off + b, e - b, off[b] + (t - vcost_of_join<S_SIDE>(J, j, c)), c);
   return v0 + (k - b);
 }
 

@@ -51,14 +51,16 @@ __device__ __forceinline__ uint32_t padded(uint32_t rel) { return rel + (rel / (
 // arena bytes (byte-balanced static partition)
 // ---------------------------------------------------------------------------
 
-// first i in [0, n] with off[i] >= target (off non-decreasing); 32-ary search by one warp
-__device__ __forceinline__ uint64_t warp_lower_bound(const uint64_t* __restrict__ off, uint64_t n, uint64_t target) {
+// first i in [0, n] with off[i] + c i >= target (off non-decreasing; c, a
+// weight per key, 0 for a plain search in the offsets); 32-ary search by one warp
+__device__ __forceinline__ uint64_t warp_lower_bound(const uint64_t* __restrict__ off, uint64_t n, uint64_t target,
+                                                     uint64_t c = 0) {
   const int lane = threadIdx.x & 31;
   uint64_t lo = 0, hi = n;          // answer in [lo, hi]
   while (hi - lo > 32) {
     const uint64_t step = (hi - lo + 31) / 32;
     const uint64_t idx = lo + (uint64_t)lane * step;
-    const bool below = idx <= hi && off[idx] < target;
+    const bool below = idx <= hi && off[idx] + c * idx < target;
     const int cnt = __popc(__ballot_sync(kFull, below));   // lanes 0..cnt-1 are below
     if (cnt == 0) { hi = lo; break; }
     const uint64_t nlo = lo + (uint64_t)(cnt - 1) * step;
@@ -68,19 +70,21 @@ __device__ __forceinline__ uint64_t warp_lower_bound(const uint64_t* __restrict_
     if (lo > hi) lo = hi;
   }
   const uint64_t idx = lo + (uint64_t)lane;
-  const bool below = idx < hi && off[idx] < target;
+  const bool below = idx < hi && off[idx] + c * idx < target;
   const int cnt = __popc(__ballot_sync(kFull, below));
   return lo + (uint64_t)cnt;
 }
 
+// The keys [k_lo, k_hi) of warp `warp` of nwarps: equal shares of the work
+// bytes + c per key (c = 0: of the key bytes).
 __device__ __forceinline__ void warp_key_range(const uint64_t* __restrict__ off, uint64_t n, uint64_t warp,
-                                               uint64_t nwarps, uint64_t* k_lo, uint64_t* k_hi) {
-  const uint64_t base = off[0], total = off[n] - off[0];
+                                               uint64_t nwarps, uint64_t* k_lo, uint64_t* k_hi, uint64_t c = 0) {
+  const uint64_t base = off[0], total = off[n] - off[0] + c * n;
   auto cut = [&](uint64_t w) -> uint64_t {
     if (w == 0) return 0;
     if (w >= nwarps) return n;
     const unsigned __int128 t = (unsigned __int128)total * w / nwarps;
-    return warp_lower_bound(off, n, base + (uint64_t)t);
+    return warp_lower_bound(off, n, base + (uint64_t)t, c);
   };
   *k_lo = cut(warp);
   *k_hi = cut(warp + 1);

@@ -73,6 +73,12 @@ constexpr uint32_t kLKNoKey = 0xFFFFFFFFu;            // empty sorting entry
 // search in the offsets); smaller ones by key count, which saves the search's
 // dependent loads where they would be a large share of the kernel's time
 constexpr uint64_t kLKSearchFrom = 1ull << 19;
+// A key's work in key-byte equivalents is its length + kLKKeyCost (the window
+// sort, masks and finishing): fitted to the kernel's rates on keys of 32-128
+// and 2048-8192 bytes, it gives the rate on 256-1024 bytes within 1 %.  The
+// warps' shares are cut on it, so that a relation (or batch) that mixes short
+// and long keys leaves no warp with far more keys than the others.
+constexpr uint64_t kLKKeyCost = 140;
 constexpr int kLKIdxBits = kLKWin == 256 ? 8 : (kLKWin == 128 ? 7 : (kLKWin == 64 ? 6 : 10));
 static_assert((1 << kLKIdxBits) == kLKWin, "window sizes 64, 128, 256");
 constexpr uint32_t kLKNbCap = (1u << (31 - kLKIdxBits)) - 1u;   // block counts above sort together
@@ -504,8 +510,9 @@ __device__ __forceinline__ uint32_t lk_window(const BatchJoin* __restrict__ J, i
 }
 
 // A warp's keys [lo, hi) of n (virtual rows of a batch side, or rows of a
-// relation): equal counts below kLKSearchFrom keys, else a byte-balanced cut
-// (in a batch, over the joins' key bytes back to back).  Whole warp.
+// relation): equal counts below kLKSearchFrom keys, else equal shares of the
+// work, key bytes + kLKKeyCost per key (in a batch, over the joins' keys back
+// to back).  Whole warp.
 template <bool BATCH>
 __device__ __forceinline__ void lk_warp_range(const BatchJoin* __restrict__ J, int nj, int s_side,
                                               const uint64_t* __restrict__ off, uint64_t n, uint64_t warp,
@@ -516,16 +523,16 @@ __device__ __forceinline__ void lk_warp_range(const BatchJoin* __restrict__ J, i
     return;
   }
   if constexpr (!BATCH) {
-    warp_key_range(off, n, warp, nwarps, lo, hi);
+    warp_key_range(off, n, warp, nwarps, lo, hi, kLKKeyCost);
   } else {
-    const uint64_t vbytes = s_side ? __ldg(&J[nj].vbs) : __ldg(&J[nj].vbr);
+    const uint64_t total = s_side ? vcost_of_join<true>(J, nj, kLKKeyCost) : vcost_of_join<false>(J, nj, kLKKeyCost);
     auto cut = [&](uint64_t w) -> uint64_t {
       if (w == 0) return 0;
       if (w >= nwarps) return n;
-      const uint64_t t = (uint64_t)((unsigned __int128)vbytes * w / nwarps);
-      if (t >= vbytes) return n;
-      return s_side ? vcut_in_join<true>(J, off, join_of_vbyte<true>(J, nj, t), t)
-                    : vcut_in_join<false>(J, off, join_of_vbyte<false>(J, nj, t), t);
+      const uint64_t t = (uint64_t)((unsigned __int128)total * w / nwarps);
+      if (t >= total) return n;
+      return s_side ? vcut_in_join<true>(J, off, join_of_vcost<true>(J, nj, t, kLKKeyCost), t, kLKKeyCost)
+                    : vcut_in_join<false>(J, off, join_of_vcost<false>(J, nj, t, kLKKeyCost), t, kLKKeyCost);
     };
     *lo = cut(warp);
     *hi = cut(warp + 1);
