@@ -910,7 +910,7 @@ def run_gpu(args):
 
 
 # revision of each kernel's code; profiles/traffic.json holds counters per revision
-KERNEL_REVS = {"sig_key_kernel": "v3", "build_kernel": "v8", "verify_kernel": "v17", "sig_key_kernel+probe": "v1"}
+KERNEL_REVS = {"sig_key_kernel": "v4", "build_kernel": "v8", "verify_kernel": "v17", "sig_key_kernel+probe": "v2"}
 KERNEL_NAMES = {"sig_R": "sig_key_kernel", "sig_S": "sig_key_kernel", "build": "build_kernel",
                 "verify": "verify_kernel", "sig_probe_S": "sig_key_kernel+probe"}
 FUSED_PROBE_FROM = 1 << 19    # S keys from which the library's probe computes signatures and probes in one kernel
