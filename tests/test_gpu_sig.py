@@ -125,6 +125,31 @@ def test_every_launch_shape(cuda):
             ag.sig_compute(D, shape=bad_shape)
 
 
+def test_mixed_length_runs_at_every_shape(cuda):
+    """A relation above the size from which the warps' shares are cut by work
+    (2^19 keys; a key counts its bytes + a fixed cost) whose key lengths change
+    in runs (tens of thousands of 0-16-byte keys, two thousand of 4-8 KB,
+    tens of thousands of 256-1024 bytes), so that the cuts fall inside and
+    between runs of very different work per byte, garbage after the last key:
+    every launch shape gives the oracle's signatures."""
+    ag = cuda
+    rng = np.random.default_rng(46)
+    runs = [(80_000, 0, 16), (2_000, 4096, 8192), (80_000, 0, 16), (60_000, 256, 1024), (80_000, 1, 8),
+            (2_000, 4096, 8192), (80_000, 0, 16), (60_000, 256, 1024), (80_000, 0, 16), (2_000, 4096, 8192)]
+    lens = np.concatenate([rng.integers(lo, hi + 1, n) for n, lo, hi in runs]).astype(np.uint64)
+    assert lens.size >= 1 << 19
+    off = np.zeros(lens.size + 1, np.uint64)
+    off[1:] = np.cumsum(lens)
+    arena = rng.integers(0, 256, int(off[-1]) + 64, dtype=np.uint8)
+    rel = workloads.Relation(arena, off, np.arange(lens.size, dtype=np.uint32))
+    D = ag.DeviceRelation.from_host(rel.arena, rel.off, rel.ids)
+    want = oracle.sig_batch(rel.arena, rel.off, nthreads=8)
+    for sh in range(len(ag.sig_shapes())):
+        got = ag.sig_compute(D, shape=sh).cpu().numpy().view(np.uint64)
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, (sh, bad[:5].tolist())
+
+
 @pytest.mark.parametrize("block_bytes", [16, 32, 48, 256, 4096])
 def test_cumulative_signatures(cuda, block_bytes):
     """as_sig_prefix_offsets / as_sig_prefixes against the oracle's definition:
