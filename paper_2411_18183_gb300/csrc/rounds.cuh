@@ -1,6 +1,6 @@
 // rounds.cuh -- warp-level helpers shared by the kernels: async copies,
-// the byte-balanced split of a relation's keys over warps (a 32-ary search in
-// the offsets by one warp), the offsets a warp loads for a round of 32 keys,
+// the split of a relation's keys over warps in equal shares of key bytes
+// (+ an optional cost per key; a 32-ary search in the offsets by one warp), the offsets a warp loads for a round of 32 keys,
 // the constant-multiply tables, and the geometry of the 16-byte chunk grid
 // that the comparison join's string hash (baseline.cuh) walks in tiles of
 // kTile bytes (a key starting at an odd byte is read funnel-shifted by one
@@ -48,7 +48,7 @@ __device__ __forceinline__ uint32_t padded(uint32_t rel) { return rel + (rel / (
 
 // ---------------------------------------------------------------------------
 // warp range: keys [k_lo, k_hi) whose starts fall in this warp's share of the
-// arena bytes (byte-balanced static partition)
+// key bytes, each key counting c more (static partition)
 // ---------------------------------------------------------------------------
 
 // first i in [0, n] with off[i] + c i >= target (off non-decreasing; c, a

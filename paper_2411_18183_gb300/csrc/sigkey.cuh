@@ -27,8 +27,8 @@
 // 16 bytes; xs3_net.h (written by gen_xs3.py) holds that step and the map back
 // to polynomial coordinates.
 //
-// Scheduling.  Each warp owns a byte-balanced range of keys and walks it in
-// windows of kLKWin keys.  A window's keys are sorted by length, and the warp
+// Scheduling.  Each warp owns a range of keys with an equal share of the work
+// (key bytes + a fixed cost per key) and walks it in windows of kLKWin keys.  A window's keys are sorted by length, and the warp
 // computes them in groups of 32 consecutive sorted keys, one key per lane, so
 // the lanes of a group have (nearly) the same amount of work.  A lane streams
 // its key from global memory in 32-byte blocks (one 256-bit load per block,
@@ -40,7 +40,7 @@
 // slower: per-lane 16-byte copies fetch each 32-byte sector twice, and a TMA
 // bulk copy per lane is serialised because its operands are warp-uniform.)
 // In a batch the keys are the joins' row ranges back to back ("virtual
-// rows"): the warps split them by key bytes across the joins, and a window
+// rows"): the warps split them by work across the joins, and a window
 // ends with its join's rows so that its keys are consecutive in the relation.
 #pragma once
 #include <cstdint>
@@ -69,7 +69,7 @@ constexpr int kLKShapeCount = sizeof(kLKShapes) / sizeof(kLKShapes[0]);
 #endif
 constexpr int kLKWin = ALGSIG_LK_WIN;                 // keys per sorting window (a power of two)
 constexpr uint32_t kLKNoKey = 0xFFFFFFFFu;            // empty sorting entry
-// relations of this many keys and more are split over the warps by key bytes (a
+// relations of this many keys and more are split over the warps by work (a
 // search in the offsets); smaller ones by key count, which saves the search's
 // dependent loads where they would be a large share of the kernel's time
 constexpr uint64_t kLKSearchFrom = 1ull << 19;

@@ -208,7 +208,7 @@ def test_autotune_cache_skips_timing_for_a_known_shape(cuda, batch, tmp_path):
 @pytest.mark.parametrize("shape", [0, 2])
 def test_gapped_batch_signatures_at_scale(cuda, shape):
     """A batch whose joins' rows have gaps, with more than 2^19 S rows (so the
-    signature kernel splits the joins' rows over its warps by key bytes) and
+    signature kernel splits the joins' rows over its warps by work) and
     runs that end inside a window: every virtual row's signature equals the
     oracle's signature of its relation row, at two kernel shapes."""
     ag = cuda
