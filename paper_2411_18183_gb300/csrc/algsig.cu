@@ -202,6 +202,28 @@ __device__ __forceinline__ uint32_t len32(uint64_t len) {
   return len < 0xFFFFFFFEull ? (uint32_t)len : 0xFFFFFFFEu;
 }
 
+// Insert R row `row` (signature sig, key length len) into the table tab[0..msk]:
+// the first empty slot from its bucket on, claimed by atomicCAS on word 1; a
+// walk over the whole table that finds none sets the table-full flag.
+__device__ __forceinline__ void table_insert(Slot* tab, uint64_t msk, uint64_t sig, uint64_t len, uint64_t row,
+                                             uint32_t* flags) {
+  const uint64_t word = ((uint64_t)len32(len) << 32) | row;
+  uint64_t b = sig_hash(sig, len) & msk;
+  for (uint64_t step = 0; step <= msk; ++step) {
+    const uint64_t cur = *(volatile const uint64_t*)(&tab[b].key);
+    if (cur == kEmpty) {
+      const unsigned long long prev = atomicCAS(reinterpret_cast<unsigned long long*>(&tab[b].key),
+                                                (unsigned long long)kEmpty, (unsigned long long)word);
+      if (prev == kEmpty) {
+        tab[b].sig = sig;
+        return;
+      }
+    }
+    b = (b + 1) & msk;
+  }
+  atomicOr(flags, kFlagTableFull);
+}
+
 // Insert R rows (batch: the m virtual rows of the joins).  Single join:
 // J == nullptr, the table is slots[0..mask].
 __global__ void build_kernel(Slot* __restrict__ slots, uint64_t mask, const uint64_t* __restrict__ sigR,
@@ -220,27 +242,26 @@ __global__ void build_kernel(Slot* __restrict__ slots, uint64_t mask, const uint
     }
     const uint64_t full = offR[row + 1] - offR[row];
     const uint64_t len = full < cap_len ? full : cap_len;   // the prefix join reads keys' first cap_len bytes
-    const uint64_t sig = sigR[v];
-    const uint64_t word = ((uint64_t)len32(len) << 32) | row;
-    uint64_t b = sig_hash(sig, len) & msk;
-    bool placed = false;
-    for (uint64_t step = 0; step <= msk; ++step) {
-      const uint64_t cur = *(volatile const uint64_t*)(&tab[b].key);
-      if (cur == kEmpty) {
-        const unsigned long long prev =
-            atomicCAS(reinterpret_cast<unsigned long long*>(&tab[b].key), (unsigned long long)kEmpty,
-                      (unsigned long long)word);
-        if (prev == kEmpty) {
-          tab[b].sig = sig;
-          placed = true;
-          break;
-        }
-      }
-      b = (b + 1) & msk;
-    }
-    if (!placed) atomicOr(flags, kFlagTableFull);
+    table_insert(tab, msk, sigR[v], len, row, flags);
   }
 }
+
+// The build fused into the signature kernel over R (as_join_build without
+// given signatures): after each group of 32 keys has its signatures, every
+// lane inserts its key.  The probe runs in a later kernel, so it never sees a
+// slot whose signature word is not yet written.
+struct BuildPost {
+  static constexpr size_t kScratch = 0;
+  Slot* slots;
+  uint64_t mask;
+  const uint64_t* offR;
+  uint32_t* flags;
+  __device__ __forceinline__ void init(uint8_t*, const uint4*) {}
+  __device__ __forceinline__ void group(uint64_t kq, uint64_t sig, bool valid) {
+    if (valid) table_insert(slots, mask, sig, __ldg(offR + kq + 1) - __ldg(offR + kq), kq, flags);
+  }
+  __device__ __forceinline__ void finish() {}
+};
 
 // ----------------------------------------------------------------------------
 // Probe: table walk + byte-exact verification + output compaction.  The S
@@ -1079,12 +1100,19 @@ static as_status ensure_device(DeviceState** out) {
       {
         constexpr LKShape k = kLKShapes[0];
         const int smem = (int)lk_smem_bytes(k.warps, k.depth, ProbePost::kScratch);
+        const int smem_b = (int)lk_smem_bytes(k.warps, k.depth, BuildPost::kScratch);
         if ((e = cudaFuncSetAttribute(
                  reinterpret_cast<const void*>(sig_key_kernel<true, 4, k.warps, k.depth, false, ProbePost>),
                  cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
             (e = cudaFuncSetAttribute(
                  reinterpret_cast<const void*>(sig_key_kernel<false, 4, k.warps, k.depth, false, ProbePost>),
-                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess)
+                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(
+                 reinterpret_cast<const void*>(sig_key_kernel<true, 4, k.warps, k.depth, false, BuildPost>),
+                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b)) != cudaSuccess ||
+            (e = cudaFuncSetAttribute(
+                 reinterpret_cast<const void*>(sig_key_kernel<false, 4, k.warps, k.depth, false, BuildPost>),
+                 cudaFuncAttributeMaxDynamicSharedMemorySize, smem_b)) != cudaSuccess)
           return cuda_fail(e, "kernel attribute");
       }
     }
@@ -1245,6 +1273,31 @@ static as_status launch_sig_probe(const DeviceState* d, const as_table* t, const
         <<<blocks, 32 * k.warps, smem, s>>>(arenaS, offS, n, sigS, nullptr, 0, 0, post);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(e, "signature and probe kernel launch");
+  return AS_OK;
+}
+
+// R's signatures with the build fused in (BuildPost): the signature kernel
+// (shape 0) inserts each group of keys into the cleared table slots[0..mask].
+static as_status launch_sig_build(const DeviceState* d, const uint8_t* arenaR, const uint64_t* offR, uint64_t m,
+                                  uint64_t* sigR, Slot* slots, uint64_t mask, uint32_t* flags, cudaStream_t s) {
+  if (m == 0) return AS_OK;
+  BuildPost post;
+  post.slots = slots;
+  post.mask = mask;
+  post.offR = offR;
+  post.flags = flags;
+  constexpr LKShape k = kLKShapes[0];
+  const uint64_t want = (m + 32ull * k.warps - 1) / (32ull * k.warps);
+  const unsigned blocks = (unsigned)(want < (uint64_t)d->sms ? (want < 1 ? 1 : want) : (uint64_t)d->sms);
+  const size_t smem = lk_smem_bytes(k.warps, k.depth, BuildPost::kScratch);
+  if (d->tables_at400)
+    sig_key_kernel<true, 4, k.warps, k.depth, false, BuildPost>
+        <<<blocks, 32 * k.warps, smem, s>>>(arenaR, offR, m, sigR, nullptr, 0, 0, post);
+  else
+    sig_key_kernel<false, 4, k.warps, k.depth, false, BuildPost>
+        <<<blocks, 32 * k.warps, smem, s>>>(arenaR, offR, m, sigR, nullptr, 0, 0, post);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(e, "signature and build kernel launch");
   return AS_OK;
 }
 
@@ -1470,12 +1523,11 @@ as_status as_join_build(void* d_ws, size_t ws_bytes, const uint8_t* d_arenaR, co
   if ((e = cudaMemsetAsync(slots, 0xFF, cap * 16, s)) != cudaSuccess) return cuda_fail(e, "table clear");
   if ((e = cudaMemsetAsync(flags, 0, 4, s)) != cudaSuccess) return cuda_fail(e, "flag clear");
   const uint64_t* sigR = d_sigR;
-  if (!sigR && m > 0) {
-    st = launch_sig(d_arenaR, d_offR, m, sig_ws, s);
+  if (!sigR && m > 0) {                              // R's signatures with the build in the same kernel
+    st = launch_sig_build(d, d_arenaR, d_offR, m, sig_ws, slots, cap - 1, flags, s);
     if (st != AS_OK) return st;
     sigR = sig_ws;
-  }
-  if (m > 0) {
+  } else if (m > 0) {
     uint64_t blocks = (m + 255) / 256;
     const uint64_t lim = (uint64_t)d->sms * 16;
     if (blocks > lim) blocks = lim;
