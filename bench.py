@@ -561,15 +561,23 @@ def run_gpu(args):
         flush_l2(stream)                                # between steps, outside the steps' events
     # ... then K joins as the four calls, with events between the kernels (the per-kernel split),
     # each followed (after an L2 flush) by the probe of the same table as one call, whose kernel
-    # computes S's signatures and probes in one pass (the whole join's pass over S)
+    # computes S's signatures and probes in one pass (the whole join's pass over S), and by the
+    # build without given signatures, whose kernel computes R's signatures and inserts them (the
+    # whole join's pass over R, the table clear included)
     fev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    bev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     fcount = torch.zeros(1, dtype=torch.int64, device="cuda")
+    table_cap = 0
     for k in range(args.steps):
         t_k = step(ev[k])
         flush_l2(stream)
         fev[k][0].record(stream)
         ag.join_probe(t_k, dS, pairs, fcount, sigS_out=sigS, sync=False, stream=stream)
         fev[k][1].record(stream)
+        flush_l2(stream)
+        bev[k][0].record(stream)
+        table_cap = int(ag.join_build(dR, ws[:tb], lf, stream=stream).cap)
+        bev[k][1].record(stream)
         flush_l2(stream)
     barrier()
     torch.cuda.synchronize()
@@ -817,11 +825,14 @@ def run_gpu(args):
                    + 2 * verified_bytes),                              # R and S key bytes compared
     }
     fused = n >= FUSED_PROBE_FROM                       # the whole join's S pass is one kernel
-    phases = PH
+    # the whole join's R pass: signatures and inserts in one kernel, after the table clear
+    phase_ms["sig_build_R"] = [a.elapsed_time(b) for a, b in bev]
+    alg["sig_build_R"] = wl.R.nbytes + 8 * (m + 1) + 8 * m + 16 * m + 16 * table_cap
+    phases = PH + ("sig_build_R",)
     if fused:                                          # its time from the probe calls after the split steps
         phase_ms["sig_probe_S"] = [a.elapsed_time(b) for a, b in fev]
         alg["sig_probe_S"] = alg["sig_S"] + alg["verify"]
-        phases = PH + ("sig_probe_S",)
+        phases = phases + ("sig_probe_S",)
     kernels = {}
     for ph in phases:
         avg = statistics.mean(phase_ms[ph])
@@ -881,7 +892,7 @@ def run_gpu(args):
                 "h2d_pinned_gbs": h2d_gbs,
                 "copy_bound_ms": (h2d + d2h) / (h2d_gbs * 1e9) * 1e3,
                 "path": "stream.HostStreamJoin: pinned host R and S, S copied in chunks under the kernels"},
-        "gpu_launches": (3 if fused else 4) * args.steps,
+        "gpu_launches": (2 if fused else 3) * args.steps,
         "roofline": {"bound": "hbm", "kernel": KERNEL_NAMES[dom], "achieved": kernels[dom]["gbps"], "peak": hbm,
                      "peak_kind": f"{peak_kind} (copy bandwidth, burst)", "unit": "GB/s",
                      "frac": kernels[dom]["frac_hbm"], "traffic": traffic,
@@ -910,9 +921,10 @@ def run_gpu(args):
 
 
 # revision of each kernel's code; profiles/traffic.json holds counters per revision
-KERNEL_REVS = {"sig_key_kernel": "v4", "build_kernel": "v8", "verify_kernel": "v17", "sig_key_kernel+probe": "v2"}
+KERNEL_REVS = {"sig_key_kernel": "v4", "build_kernel": "v8", "verify_kernel": "v17", "sig_key_kernel+probe": "v2",
+               "sig_key_kernel+build": "v1"}
 KERNEL_NAMES = {"sig_R": "sig_key_kernel", "sig_S": "sig_key_kernel", "build": "build_kernel",
-                "verify": "verify_kernel", "sig_probe_S": "sig_key_kernel+probe"}
+                "verify": "verify_kernel", "sig_probe_S": "sig_key_kernel+probe", "sig_build_R": "sig_key_kernel+build"}
 FUSED_PROBE_FROM = 1 << 19    # S keys from which the library's probe computes signatures and probes in one kernel
 
 

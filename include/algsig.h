@@ -212,7 +212,9 @@ size_t as_join_table_bytes(uint64_t m, float load_factor);
  *   d_ws, ws_bytes : device workspace of at least as_join_table_bytes(m, lf)
  *   d_arenaR, d_offR, d_idR, m : relation R (m < 2^32 - 1)
  *   d_sigR         : R's signatures if already computed (uint64[m], device),
- *                    or NULL: they are computed into the workspace
+ *                    or NULL: they are computed into the workspace by the
+ *                    kernel that inserts them (signatures and build in one
+ *                    pass over R's keys)
  *   load_factor    : table fill target in (0, 1]
  *   out            : host struct filled with the table description
  * Errors: AS_ERR_INVALID, AS_ERR_NOMEM (workspace too small), AS_ERR_CUDA.
@@ -329,10 +331,11 @@ size_t as_join_ws_bytes(uint64_t m, uint64_t n, float load_factor);
  * signatures of R, build, probe with S (signatures, verification, compaction).
  * Arguments as for as_join_build and as_join_probe; d_ws must hold
  * as_join_ws_bytes(m, load_factor) bytes.  d_count may be NULL (the counter
- * then lives in the workspace).  From 2^19 S keys it is as_join_build then
- * as_join_probe (whose signatures and probe then run as one kernel); below
- * that, S's signatures overlap R's on a side stream.  The result is the same
- * either way.
+ * then lives in the workspace).  R's signatures and the build are one kernel.
+ * From 2^19 S keys it is as_join_build then as_join_probe (whose signatures
+ * and probe then run as one kernel too: one pass over each relation's keys);
+ * below that, S's signatures overlap R's pass on a side stream.  The result is
+ * the same either way.
  */
 as_status as_join(const uint8_t* d_arenaR, const uint64_t* d_offR, const uint32_t* d_idR, uint64_t m,
                   const uint8_t* d_arenaS, const uint64_t* d_offS, const uint32_t* d_idS, uint64_t n,
