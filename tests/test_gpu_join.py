@@ -450,3 +450,47 @@ def test_fused_pass_capacity_and_split_probe(cuda):
     buf = torch.full((2 * exact + 64,), CANARY, dtype=torch.int32, device="cuda")   # S's signatures in a workspace
     cnt = ag.join_probe(t, S, buf[: 2 * exact], count, ws=ag.alloc_ws(ag.join_probe_ws_bytes(S.n)))
     check_buffer(buf, exact, ag.AS_OK, cnt)
+
+
+def test_fused_pass_rejects_signature_collisions(cuda):
+    """The fused signature-and-probe pass (from 2^19 S keys) with keys that
+    share all four signature components with an R key but differ from it in
+    five symbols (in the first 16 bytes, at both ends, on both sides of 512-
+    and 1024-byte comparison steps; 10 bytes to 4 KB, odd lengths too, every
+    start alignment), among ordinary candidates of similar length in the same
+    groups: every one is rejected, exact copies join, and the pairs equal the
+    oracle's."""
+    from packing import interleave_gaps
+    ag = cuda
+    rng = random.Random(77)
+    wl = workloads.generate(workloads.CONFIGS["plain"].scaled(20_000, (1 << 19) + 100))
+    shapes = [(5, (0, 1, 2, 3, 4)), (40, (0, 7, 8, 30, 39)), (64, (0, 63, 8, 9, 10)), (100, (1, 50, 64, 65, 99)),
+              (128, (0, 63, 64, 127, 100)), (300, (0, 255, 256, 299, 128)), (520, (0, 255, 256, 511, 519)),
+              (2048, (0, 511, 512, 1500, 2047))]
+    rkeys, skeys = [], []
+    for _ in range(6):
+        for n_sym, pos in shapes:
+            a, b = five_symbol_collision(n_sym, pos, seed=rng.randrange(1 << 30))
+            rkeys.append(a)
+            skeys += [b, a]
+            if max(pos) < n_sym - 1:                  # odd length: drop the last (equal) byte of both
+                rkeys.append(a[:-1])
+                skeys += [b[:-1], a[:-1]]
+    r_list = [wl.R.key(i) for i in range(wl.R.n)] + interleave_gaps(rkeys, seed=rng.randrange(1 << 30))
+    s_list = [wl.S.key(i) for i in range(wl.S.n)]
+    ins = interleave_gaps(skeys, seed=rng.randrange(1 << 30))      # (gap, key) pairs at random rows
+    for i in range(0, len(ins), 2):
+        p = rng.randrange(len(s_list) + 1)
+        s_list[p:p] = ins[i:i + 2]
+    R = relation_garbage_tail(r_list, seed=5)
+    S = relation_garbage_tail(s_list, seed=6)
+    assert S.n >= 1 << 19
+    want = oracle.join_grace(R, S, nthreads=8)
+    dR, dS = dev(ag, R), dev(ag, S)
+    ws = ag.alloc_ws(ag.join_ws_bytes(dR.n, dS.n, 0.5))
+    pairs = torch.empty(2 * (len(want) + 4096), dtype=torch.int32, device="cuda")
+    count = torch.zeros(1, dtype=torch.int64, device="cuda")
+    _, cnt = ag.join_into(dR, dS, ws, pairs, count, 0.5, sync=True)
+    assert cnt == len(want)
+    got = oracle.sort_pairs(pairs[: 2 * cnt].cpu().numpy().view(np.uint32))
+    assert np.array_equal(got, want)
