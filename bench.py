@@ -794,7 +794,7 @@ def run_gpu(args):
         rates.append(hprobe.numel() / (h0.elapsed_time(h1) * 1e-3) / 1e9)
     h2d_gbs = max(rates)
     del dprobe
-    e2e_steps = max(2, min(args.steps, 5))
+    e2e_steps = max(3, min(args.steps, 9))
     for _ in range(max(2, args.warmup)):                # warm-up runs (the first timed run after a single
         if sj.run(hR, hS, cuts, out_host) != expected:  # warm-up was seen to take several times the rest)
             raise SystemExit("end-to-end join: wrong pair count")
@@ -806,7 +806,10 @@ def run_gpu(args):
         cnt = sj.run(hR, hS, cuts, out_host)
         e2e_runs.append((time.perf_counter() - t_run) * 1e3)
     barrier()
-    e2e_s = ranks_max((time.perf_counter() - te) / e2e_steps)
+    e2e_mean_s = ranks_max((time.perf_counter() - te) / e2e_steps)
+    # the median run: single runs were seen to take 2-4x the others at times (the host's memory and link
+    # are shared with other jobs), so the mean of a few runs moves by that much from run to run; both kept
+    e2e_s = ranks_max(statistics.median(e2e_runs) / 1e3)
     e2e_value = replica_value(n, world, e2e_s * 1e3)
     d2h = 8 * cnt + 8 * (len(cuts) - 1)
     del sj
@@ -888,7 +891,8 @@ def run_gpu(args):
                                  "S's signatures, the pair buffer and the resident relations (keys, offsets, ids)"},
         "clocks": clk,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "ms_per_step": e2e_s * 1e3, "runs_ms": [round(x, 2) for x in e2e_runs], "chunks": len(cuts) - 1,
+                "ms_per_step": e2e_s * 1e3, "stat": f"median of {e2e_steps} timed runs (mean in mean_ms)",
+                "mean_ms": e2e_mean_s * 1e3, "runs_ms": [round(x, 2) for x in e2e_runs], "chunks": len(cuts) - 1,
                 "h2d_pinned_gbs": h2d_gbs,
                 "copy_bound_ms": (h2d + d2h) / (h2d_gbs * 1e9) * 1e3,
                 "path": "stream.HostStreamJoin: pinned host R and S, S copied in chunks under the kernels"},
